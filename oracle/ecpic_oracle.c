@@ -1,0 +1,1032 @@
+/*
+ * ecpic_oracle.c -- plain, slow, FP64 CPU oracle for the 1D3V EC-PIC hot
+ * path of Powis & Kaganovich (arXiv 2308.13092).
+ *
+ * TEST INFRASTRUCTURE ONLY.  It is loaded by the tests, the smoke check and
+ * the CPU-baseline leg of the benchmark; the GPU product never calls it.
+ *
+ * The time loop follows Sec. 2a (steps 1-7), rotated so that one call of
+ * step() does: gather + leapfrog push (Eq. 6-9) -> wall absorption ->
+ * Monte-Carlo collisions (step 6) -> CIC deposit (Eq. 2-3) -> Poisson (Eq. 4)
+ * -> field (Eq. 5, or the centred MC field).  The first deposit, solve and
+ * field are done at init.
+ *
+ * Readings of points the paper leaves open (node count, weights, boundary
+ * volumes, wall rule, collision details, random-number layout) are listed in
+ * the project design notes and repeated at the function that takes them.
+ *
+ * Parity status: every routine here is pinned by a CPU test against a closed
+ * form, an invariant, a library routine or a printed table of the paper,
+ * except the time-averaged profiles of a full RF-CCP run, whose parity with
+ * the paper is unpinned (no figure data and no Turner cross sections exist
+ * in this project; only GPU-vs-oracle agreement is tested there).
+ */
+#include "ecpic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 */
+#define OR_QE 1.602176634e-19
+#define OR_EPS0 8.8541878128e-12
+#define OR_KB 1.380649e-23
+
+#define OR_TWO_PI 6.283185307179586476925286766559
+
+typedef struct {
+  int kind;
+  double thr;    /* eV */
+  double dE;     /* eV */
+  int n;
+  double* sigma; /* m^2, copied from the caller's float table */
+  int product;   /* ion species of an ionisation, else -1 */
+} or_process;
+
+typedef struct {
+  double q, m, w;
+  int64_t cap, n;
+  double *X, *vx, *vy, *vz;
+  uint64_t* id;
+  int nproc;
+  or_process proc[OR_MAX_PROC];
+  int heavy;        /* has ion-neutral processes: sample the neutral */
+  double nu_max;    /* 1/s */
+  uint32_t thr24;   /* candidate iff (r0 >> 8) < thr24 */
+  /* counters */
+  int64_t absorbed[2], births, lost, clamps, candidates;
+  int64_t coll[OR_MAX_PROC];
+  double ke;
+  /* per-node deposit and moments at the current step */
+  double *D, *M1, *M2;
+  /* time averages */
+  double *acc_n, *acc_T, *acc_M0, *acc_M1, *acc_M2;
+} or_species;
+
+struct or_run {
+  int N;
+  double* x;  /* N+1 edges */
+  double* dx; /* N cell widths */
+  double* V;  /* N+1 node control volumes */
+  double L;
+  int bc;
+  double v0, freq, phase, vdc;
+  int scheme;
+  int grid_set;
+  int ns;
+  or_species sp[OR_MAX_SPECIES];
+  double ng, Tg, mg;
+  int gas_set;
+  uint64_t seed;
+  double dt;
+  int64_t step;
+  int initialized;
+  double *Q, *phi, *E;
+  double fe;
+  int sample_every;
+  int64_t n_samples;
+  double* acc_phi;
+};
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, written from its definition in Salmon, Moraes, Dror &
+ * Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds
+ * of two 32x32->64 multiplications with the Weyl-sequence key schedule.   */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                          uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014). */
+static uint64_t or_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+uint64_t oracle_child_id(uint64_t parent, int64_t step, uint64_t tag) {
+  return or_mix64(parent ^ or_mix64((uint64_t)step * 4u + tag));
+}
+
+/* 24-bit uniform in [0,1): (r >> 8) * 2^-24 */
+static double or_u24(uint32_t r) { return (double)(r >> 8) * (1.0 / 16777216.0); }
+/* 24-bit uniform in (0,1]: ((r >> 8) + 1) * 2^-24 */
+static double or_u24_open(uint32_t r) {
+  return (double)((r >> 8) + 1u) * (1.0 / 16777216.0);
+}
+
+/* Box-Muller: two standard normals from two uniforms (u1 in (0,1]). */
+static void or_box_muller(double u1, double u2, double* z0, double* z1) {
+  double rad = sqrt(-2.0 * log(u1));
+  *z0 = rad * cos(OR_TWO_PI * u2);
+  *z1 = rad * sin(OR_TWO_PI * u2);
+}
+
+/* isotropic unit vector from two uniforms: polar axis along x. */
+static void or_isotropic(double ua, double ub, double d[3]) {
+  double c = 1.0 - 2.0 * ua;
+  double s = sqrt(fmax(0.0, 1.0 - c * c));
+  double ph = OR_TWO_PI * ub;
+  d[0] = c;
+  d[1] = s * cos(ph);
+  d[2] = s * sin(ph);
+}
+
+static void or_draw(const or_run* r, uint64_t id, uint32_t step_word,
+                    uint32_t word3, uint32_t out[4]) {
+  uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), step_word, word3};
+  uint32_t key[2] = {(uint32_t)r->seed, (uint32_t)(r->seed >> 32)};
+  oracle_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* Deposit (Eq. 2-3) in fixed point.                                   */
+int oracle_deposit_fixed(int N, int64_t n, const int32_t* cell,
+                         const float* xi, uint64_t* S) {
+  if (N < 1 || n < 0 || (n > 0 && (!cell || !xi)) || !S) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int j = cell[i];
+    float f = xi[i];
+    if (j < 0 || j >= N || !(f >= 0.0f) || !(f < 1.0f)) return -1;
+    uint32_t rgt = (uint32_t)((double)f * 4294967296.0); /* floor, f < 1 */
+    uint64_t lft = 4294967296ull - (uint64_t)rgt;
+    S[j] += lft;
+    S[j + 1] += (uint64_t)rgt;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Poisson, Eq. 4 in finite-volume form (exact Eq. 4 times dx on a uniform
+ * grid).  Row n (1..N-1): a_n phi_{n-1} + b_n phi_n + c_n phi_{n+1} = d_n. */
+static void or_poisson_rows(int N, const double* x, const double* Q,
+                            double phi0, double phiN, double* a, double* b,
+                            double* c, double* d) {
+  for (int n = 1; n <= N - 1; ++n) {
+    double dl = x[n] - x[n - 1];
+    double dr = x[n + 1] - x[n];
+    a[n] = 1.0 / dl;
+    c[n] = 1.0 / dr;
+    b[n] = -(1.0 / dl + 1.0 / dr);
+    d[n] = -Q[n] / OR_EPS0;
+  }
+  d[1] -= a[1] * phi0;
+  d[N - 1] -= c[N - 1] * phiN;
+}
+
+int oracle_poisson_thomas(int N, const double* x, const double* Q,
+                          double phi0, double phiN, double* phi) {
+  if (N < 2 || !x || !Q || !phi) return -1;
+  double* a = malloc(sizeof(double) * (size_t)(N + 1));
+  double* b = malloc(sizeof(double) * (size_t)(N + 1));
+  double* c = malloc(sizeof(double) * (size_t)(N + 1));
+  double* d = malloc(sizeof(double) * (size_t)(N + 1));
+  if (!a || !b || !c || !d) {
+    free(a); free(b); free(c); free(d);
+    return -3;
+  }
+  or_poisson_rows(N, x, Q, phi0, phiN, a, b, c, d);
+  /* forward elimination (L of the tridiagonal LU) */
+  for (int n = 2; n <= N - 1; ++n) {
+    double m = a[n] / b[n - 1];
+    b[n] -= m * c[n - 1];
+    d[n] -= m * d[n - 1];
+  }
+  /* back substitution (U) */
+  phi[0] = phi0;
+  phi[N] = phiN;
+  phi[N - 1] = d[N - 1] / b[N - 1];
+  for (int n = N - 2; n >= 1; --n) phi[n] = (d[n] - c[n] * phi[n + 1]) / b[n];
+  free(a); free(b); free(c); free(d);
+  return 0;
+}
+
+int oracle_poisson_dense(int N, const double* x, const double* Q,
+                         double phi0, double phiN, double* phi) {
+  if (N < 2 || N > 256 || !x || !Q || !phi) return -1;
+  int m = N - 1;
+  double* A = calloc((size_t)m * (size_t)(m + 1), sizeof(double));
+  double* a = malloc(sizeof(double) * (size_t)(N + 1));
+  double* b = malloc(sizeof(double) * (size_t)(N + 1));
+  double* c = malloc(sizeof(double) * (size_t)(N + 1));
+  double* d = malloc(sizeof(double) * (size_t)(N + 1));
+  if (!A || !a || !b || !c || !d) {
+    free(A); free(a); free(b); free(c); free(d);
+    return -3;
+  }
+  or_poisson_rows(N, x, Q, phi0, phiN, a, b, c, d);
+  /* augmented matrix, unknown k <-> node k+1 */
+  for (int r = 0; r < m; ++r) {
+    int n = r + 1;
+    if (r > 0) A[r * (m + 1) + (r - 1)] = a[n];
+    A[r * (m + 1) + r] = b[n];
+    if (r < m - 1) A[r * (m + 1) + (r + 1)] = c[n];
+    A[r * (m + 1) + m] = d[n];
+  }
+  for (int col = 0; col < m; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < m; ++r)
+      if (fabs(A[r * (m + 1) + col]) > fabs(A[piv * (m + 1) + col])) piv = r;
+    if (piv != col)
+      for (int k = 0; k <= m; ++k) {
+        double t = A[col * (m + 1) + k];
+        A[col * (m + 1) + k] = A[piv * (m + 1) + k];
+        A[piv * (m + 1) + k] = t;
+      }
+    for (int r = col + 1; r < m; ++r) {
+      double f = A[r * (m + 1) + col] / A[col * (m + 1) + col];
+      for (int k = col; k <= m; ++k) A[r * (m + 1) + k] -= f * A[col * (m + 1) + k];
+    }
+  }
+  for (int r = m - 1; r >= 0; --r) {
+    double s = A[r * (m + 1) + m];
+    for (int k = r + 1; k < m; ++k) s -= A[r * (m + 1) + k] * phi[k + 1];
+    phi[r + 1] = s / A[r * (m + 1) + r];
+  }
+  phi[0] = phi0;
+  phi[N] = phiN;
+  free(A); free(a); free(b); free(c); free(d);
+  return 0;
+}
+
+/* Field.  EC: Eq. 5, one value per cell (face-centred on the staggered
+ * reading of Sec. 2a).  MC: centred difference at interior nodes,
+ * one-sided at Dirichlet end nodes, wrapped when periodic. */
+int oracle_field(int N, const double* x, const double* phi, int bc,
+                 int scheme, double* E) {
+  if (N < 2 || !x || !phi || !E) return -1;
+  if (scheme == OR_SCHEME_EC) {
+    for (int j = 0; j < N; ++j) E[j] = -(phi[j + 1] - phi[j]) / (x[j + 1] - x[j]);
+    return 0;
+  }
+  for (int n = 1; n <= N - 1; ++n)
+    E[n] = -(phi[n + 1] - phi[n - 1]) / (x[n + 1] - x[n - 1]);
+  if (bc == OR_PERIODIC) {
+    double dl = x[N] - x[N - 1], dr = x[1] - x[0];
+    E[0] = -(phi[1] - phi[N - 1]) / (dl + dr);
+    E[N] = E[0];
+  } else {
+    E[0] = -(phi[1] - phi[0]) / (x[1] - x[0]);
+    E[N] = -(phi[N] - phi[N - 1]) / (x[N] - x[N - 1]);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Doubling grid (Sec. 3c rules 1-4; L_buff = 5 cm for Table 2).
+ * Half-domain of H = n_ref/2 reference cells: ceil(L_buff/dx_min) cells of
+ * dx_min from the wall, then greedily the next cell is twice the previous one
+ * when that stays <= dx_max and the current position is a multiple of the
+ * doubled size; otherwise the previous size.  Mirrored about the centre. */
+int oracle_doubling_grid(int n_ref, double L, double L_buff, int dx_min,
+                         int dx_max, double* edges, int cap) {
+  if (n_ref < 2 || (n_ref & 1) || L <= 0 || L_buff < 0 || dx_min < 1 ||
+      dx_max < dx_min || !edges)
+    return -1;
+  double dx_ref = L / (double)n_ref;
+  int H = n_ref / 2;
+  int* size = malloc(sizeof(int) * (size_t)H);
+  if (!size) return -3;
+  int nh = 0, pos = 0;
+  int nb = (int)ceil(L_buff / (dx_min * dx_ref) - 1e-9);
+  for (int i = 0; i < nb && pos < H; ++i) {
+    int s = dx_min;
+    if (pos + s > H) s = H - pos;
+    size[nh++] = s;
+    pos += s;
+  }
+  int prev = dx_min;
+  while (pos < H) {
+    int s = prev;
+    if (2 * prev <= dx_max && pos % (2 * prev) == 0) s = 2 * prev;
+    while (pos + s > H && s > dx_min) s /= 2;
+    if (pos + s > H) s = H - pos;
+    size[nh++] = s;
+    pos += s;
+    prev = s;
+  }
+  int ncell = 2 * nh;
+  if (ncell + 1 > cap) {
+    free(size);
+    return -1;
+  }
+  int u = 0;
+  edges[0] = 0.0;
+  for (int i = 0; i < nh; ++i) {
+    u += size[i];
+    edges[i + 1] = u * dx_ref;
+  }
+  for (int i = nh - 1; i >= 0; --i) {
+    u += size[i];
+    edges[ncell - i] = u * dx_ref;
+  }
+  edges[ncell] = L;
+  free(size);
+  return ncell;
+}
+
+/* ------------------------------------------------------------------ */
+static void or_free_species(or_species* s) {
+  free(s->X); free(s->vx); free(s->vy); free(s->vz); free(s->id);
+  free(s->D); free(s->M1); free(s->M2);
+  free(s->acc_n); free(s->acc_T); free(s->acc_M0); free(s->acc_M1);
+  free(s->acc_M2);
+  for (int k = 0; k < s->nproc; ++k) free(s->proc[k].sigma);
+  memset(s, 0, sizeof(*s));
+}
+
+int oracle_create(or_run** out) {
+  if (!out) return -1;
+  or_run* r = calloc(1, sizeof(or_run));
+  if (!r) return -3;
+  *out = r;
+  return 0;
+}
+
+void oracle_destroy(or_run* r) {
+  if (!r) return;
+  for (int s = 0; s < r->ns; ++s) or_free_species(&r->sp[s]);
+  free(r->x); free(r->dx); free(r->V); free(r->Q); free(r->phi); free(r->E);
+  free(r->acc_phi);
+  free(r);
+}
+
+static int or_alloc_node_arrays(or_run* r, or_species* s) {
+  size_t nn = (size_t)r->N + 1;
+  s->D = calloc(nn, sizeof(double));
+  s->M1 = calloc(nn, sizeof(double));
+  s->M2 = calloc(nn, sizeof(double));
+  s->acc_n = calloc(nn, sizeof(double));
+  s->acc_T = calloc(nn, sizeof(double));
+  s->acc_M0 = calloc(nn, sizeof(double));
+  s->acc_M1 = calloc(nn, sizeof(double));
+  s->acc_M2 = calloc(nn, sizeof(double));
+  if (!s->D || !s->M1 || !s->M2 || !s->acc_n || !s->acc_T || !s->acc_M0 ||
+      !s->acc_M1 || !s->acc_M2)
+    return -3;
+  return 0;
+}
+
+int oracle_set_grid(or_run* r, const double* edges, int n_edges, int bc,
+                    double v0, double freq_hz, double phase_rad, double v_dc) {
+  if (!r || !edges || n_edges < 3 || (bc != OR_DIRICHLET && bc != OR_PERIODIC))
+    return -1;
+  if (r->ns > 0) return -2; /* grid before species */
+  if (edges[0] != 0.0) return -1;
+  for (int i = 1; i < n_edges; ++i)
+    if (!(edges[i] > edges[i - 1])) return -1;
+  free(r->x); free(r->dx); free(r->V); free(r->Q); free(r->phi); free(r->E);
+  free(r->acc_phi);
+  int N = n_edges - 1;
+  r->N = N;
+  r->x = malloc(sizeof(double) * (size_t)(N + 1));
+  r->dx = malloc(sizeof(double) * (size_t)N);
+  r->V = malloc(sizeof(double) * (size_t)(N + 1));
+  r->Q = calloc((size_t)N + 1, sizeof(double));
+  r->phi = calloc((size_t)N + 1, sizeof(double));
+  r->E = calloc((size_t)N + 1, sizeof(double));
+  r->acc_phi = calloc((size_t)N + 1, sizeof(double));
+  if (!r->x || !r->dx || !r->V || !r->Q || !r->phi || !r->E || !r->acc_phi)
+    return -3;
+  memcpy(r->x, edges, sizeof(double) * (size_t)(N + 1));
+  for (int j = 0; j < N; ++j) r->dx[j] = r->x[j + 1] - r->x[j];
+  r->L = r->x[N];
+  /* node control volumes: half cells at Dirichlet end nodes; the two end
+   * nodes are one node when periodic */
+  for (int n = 1; n < N; ++n) r->V[n] = 0.5 * (r->dx[n - 1] + r->dx[n]);
+  if (bc == OR_PERIODIC) {
+    r->V[0] = r->V[N] = 0.5 * (r->dx[N - 1] + r->dx[0]);
+  } else {
+    r->V[0] = 0.5 * r->dx[0];
+    r->V[N] = 0.5 * r->dx[N - 1];
+  }
+  r->bc = bc;
+  r->v0 = v0; r->freq = freq_hz; r->phase = phase_rad; r->vdc = v_dc;
+  r->grid_set = 1;
+  return 0;
+}
+
+int oracle_set_scheme(or_run* r, int scheme) {
+  if (!r || (scheme != OR_SCHEME_EC && scheme != OR_SCHEME_MC)) return -1;
+  r->scheme = scheme;
+  return 0;
+}
+
+int oracle_add_species(or_run* r, double q, double m, double w,
+                       int64_t capacity, int* species_out) {
+  if (!r || m <= 0 || w < 0 || capacity < 1) return -1;
+  if (!r->grid_set || r->initialized) return -2;
+  if (r->ns >= OR_MAX_SPECIES) return -1;
+  or_species* s = &r->sp[r->ns];
+  memset(s, 0, sizeof(*s));
+  s->q = q; s->m = m; s->w = w; s->cap = capacity;
+  size_t c = (size_t)capacity;
+  s->X = malloc(sizeof(double) * c);
+  s->vx = malloc(sizeof(double) * c);
+  s->vy = malloc(sizeof(double) * c);
+  s->vz = malloc(sizeof(double) * c);
+  s->id = malloc(sizeof(uint64_t) * c);
+  if (!s->X || !s->vx || !s->vy || !s->vz || !s->id) return -3;
+  if (or_alloc_node_arrays(r, s)) return -3;
+  if (species_out) *species_out = r->ns;
+  r->ns++;
+  return 0;
+}
+
+int oracle_set_gas(or_run* r, double n_g, double T_g, double m_g) {
+  if (!r || n_g < 0 || T_g < 0 || m_g <= 0) return -1;
+  if (r->initialized) return -2;
+  r->ng = n_g; r->Tg = T_g; r->mg = m_g;
+  r->gas_set = 1;
+  return 0;
+}
+
+int oracle_add_process(or_run* r, int species, int kind, double threshold_eV,
+                       double dE_eV, int n, const float* sigma,
+                       int product_species) {
+  if (!r || species < 0 || species >= r->ns || kind < OR_ELASTIC ||
+      kind > OR_CX || dE_eV <= 0 || n < 2 || !sigma || threshold_eV < 0)
+    return -1;
+  if (r->initialized) return -2;
+  or_species* s = &r->sp[species];
+  if (s->nproc >= OR_MAX_PROC) return -1;
+  /* all processes of one species share one energy grid */
+  if (s->nproc > 0 && (s->proc[0].dE != dE_eV || s->proc[0].n != n)) return -1;
+  int heavy = (kind == OR_ION_ELASTIC || kind == OR_CX);
+  if (s->nproc > 0 && heavy != s->heavy) return -1;
+  if (kind == OR_IONIZATION &&
+      (product_species < 0 || product_species >= r->ns || product_species == species))
+    return -1;
+  for (int i = 0; i < n; ++i)
+    if (!(sigma[i] >= 0.0f) || !isfinite(sigma[i])) return -1;
+  or_process* p = &s->proc[s->nproc];
+  p->kind = kind;
+  p->thr = threshold_eV;
+  p->dE = dE_eV;
+  p->n = n;
+  p->product = (kind == OR_IONIZATION) ? product_species : -1;
+  p->sigma = malloc(sizeof(double) * (size_t)n);
+  if (!p->sigma) return -3;
+  for (int i = 0; i < n; ++i) p->sigma[i] = (double)sigma[i];
+  s->heavy = heavy;
+  s->nproc++;
+  return 0;
+}
+
+/* sigma(E): linear interpolation in the uniform-energy table, held at the
+ * last entry above the table, zero below the threshold. */
+static double or_sigma(const or_process* p, double E) {
+  if (E < p->thr) return 0.0;
+  double u = E / p->dE;
+  double fi = floor(u);
+  if (fi >= (double)(p->n - 1)) return p->sigma[p->n - 1];
+  int i = (int)fi;
+  double t = u - fi;
+  return p->sigma[i] + t * (p->sigma[i + 1] - p->sigma[i]);
+}
+
+/* Null-collision frequency bound: on every table segment [E_i, E_{i+1}],
+ * n_g * max(sigma_tot(E_i), sigma_tot(E_{i+1})) * speed(E_{i+1}); the max over
+ * segments.  Candidate probability P = 1 - exp(-nu_max dt) becomes the
+ * 24-bit integer threshold ceil(P * 2^24). */
+static void or_null_rate(or_run* r, or_species* s) {
+  s->nu_max = 0.0;
+  s->thr24 = 0;
+  if (s->nproc == 0 || !r->gas_set || r->ng <= 0) return;
+  int n = s->proc[0].n;
+  double dE = s->proc[0].dE;
+  double best = 0.0;
+  for (int i = 0; i + 1 < n; ++i) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < s->nproc; ++k) {
+      a += s->proc[k].sigma[i];
+      b += s->proc[k].sigma[i + 1];
+    }
+    double sig = a > b ? a : b;
+    double v = sqrt(2.0 * (double)(i + 1) * dE * OR_QE / s->m);
+    if (sig * v > best) best = sig * v;
+  }
+  s->nu_max = r->ng * best;
+  double P = 1.0 - exp(-s->nu_max * r->dt);
+  double t = ceil(P * 16777216.0);
+  if (t > 16777216.0) t = 16777216.0;
+  s->thr24 = (uint32_t)t;
+}
+
+int oracle_nu_max(const or_run* r, int species, double* nu_max,
+                  uint32_t* threshold24) {
+  if (!r || species < 0 || species >= r->ns) return -1;
+  if (nu_max) *nu_max = r->sp[species].nu_max;
+  if (threshold24) *threshold24 = r->sp[species].thr24;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+static int or_locate(const or_run* r, double X) {
+  int lo = 0, hi = r->N; /* x[lo] <= X < x[hi] */
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (r->x[mid] <= X) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+static double or_rf(const or_run* r, int64_t k) {
+  double t = (double)k * r->dt;
+  return r->vdc + r->v0 * sin(OR_TWO_PI * r->freq * t + r->phase);
+}
+
+/* Step 1 (Eq. 2-3): per-species CIC shares D_s,n, and the first and second
+ * vx moments.  Periodic: node N is node 0. */
+static void or_deposit(or_run* r) {
+  int N = r->N;
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    memset(s->D, 0, sizeof(double) * (size_t)(N + 1));
+    memset(s->M1, 0, sizeof(double) * (size_t)(N + 1));
+    memset(s->M2, 0, sizeof(double) * (size_t)(N + 1));
+    for (int64_t i = 0; i < s->n; ++i) {
+      int j = or_locate(r, s->X[i]);
+      double xi = (s->X[i] - r->x[j]) / r->dx[j];
+      double v = s->vx[i];
+      s->D[j] += 1.0 - xi;
+      s->D[j + 1] += xi;
+      s->M1[j] += (1.0 - xi) * v;
+      s->M1[j + 1] += xi * v;
+      s->M2[j] += (1.0 - xi) * v * v;
+      s->M2[j + 1] += xi * v * v;
+    }
+    if (r->bc == OR_PERIODIC) {
+      s->D[0] += s->D[N]; s->D[N] = s->D[0];
+      s->M1[0] += s->M1[N]; s->M1[N] = s->M1[0];
+      s->M2[0] += s->M2[N]; s->M2[N] = s->M2[0];
+    }
+  }
+  for (int n = 0; n <= N; ++n) {
+    double q = 0.0;
+    for (int si = 0; si < r->ns; ++si) q += r->sp[si].q * r->sp[si].w * r->sp[si].D[n];
+    r->Q[n] = q;
+  }
+}
+
+/* Steps 2-3: Poisson (Eq. 4) and field (Eq. 5 or centred) at step k.
+ * Periodic: a uniform neutralising background (Q_n -= V_n * sum Q / L),
+ * phi_0 = phi_N = 0. */
+static int or_solve(or_run* r, int64_t k) {
+  int N = r->N;
+  double* Qs = malloc(sizeof(double) * (size_t)(N + 1));
+  if (!Qs) return -3;
+  double phi0, phiN;
+  if (r->bc == OR_PERIODIC) {
+    double tot = 0.0;
+    for (int n = 0; n < N; ++n) tot += r->Q[n];
+    for (int n = 0; n <= N; ++n) Qs[n] = r->Q[n] - r->V[n] * tot / r->L;
+    phi0 = phiN = 0.0;
+  } else {
+    memcpy(Qs, r->Q, sizeof(double) * (size_t)(N + 1));
+    phi0 = or_rf(r, k);
+    phiN = 0.0;
+  }
+  int rc = oracle_poisson_thomas(N, r->x, Qs, phi0, phiN, r->phi);
+  free(Qs);
+  if (rc) return rc;
+  return oracle_field(N, r->x, r->phi, r->bc, r->scheme, r->E);
+}
+
+static void or_sample(or_run* r) {
+  int N = r->N;
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    for (int n = 0; n <= N; ++n) {
+      double D = s->D[n];
+      s->acc_n[n] += s->w * D / r->V[n];
+      double T = 0.0;
+      if (D > 0.0) {
+        double m1 = s->M1[n] / D, m2 = s->M2[n] / D;
+        T = s->m * (m2 - m1 * m1) / OR_QE;
+      }
+      s->acc_T[n] += T;
+      s->acc_M0[n] += D;
+      s->acc_M1[n] += s->M1[n];
+      s->acc_M2[n] += s->M2[n];
+    }
+  }
+  for (int n = 0; n <= N; ++n) r->acc_phi[n] += r->phi[n];
+  r->n_samples++;
+}
+
+static int or_refresh(or_run* r) {
+  or_deposit(r);
+  return or_solve(r, r->step);
+}
+
+/* ------------------------------------------------------------------ */
+int oracle_init(or_run* r, uint64_t seed, double dt,
+                const int64_t* n_per_species, const double* T_eV) {
+  if (!r || !n_per_species || !T_eV || !(dt > 0)) return -1;
+  if (!r->grid_set || r->ns == 0) return -2;
+  for (int si = 0; si < r->ns; ++si)
+    if (n_per_species[si] < 0 || n_per_species[si] > r->sp[si].cap || T_eV[si] < 0)
+      return -1;
+  r->seed = seed;
+  r->dt = dt;
+  r->step = 0;
+  /* Sec. 2b: uniform density, Maxwellian temperature.  Position from
+   * 32-bit word 0 of the block with word3 = (s<<8)|0x80; velocities from
+   * the block with word3 = (s<<8)|0x81 (Box-Muller on 32-bit uniforms). */
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    double sd = sqrt(OR_QE * T_eV[si] / s->m);
+    s->n = n_per_species[si];
+    for (int64_t i = 0; i < s->n; ++i) {
+      uint32_t a[4], b[4];
+      or_draw(r, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)si << 8) | 0x80u, a);
+      or_draw(r, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)si << 8) | 0x81u, b);
+      double u = (double)a[0] * (1.0 / 4294967296.0);
+      s->X[i] = u * r->L;
+      double z0, z1, z2, z3;
+      or_box_muller(((double)b[0] + 1.0) * (1.0 / 4294967296.0),
+                    (double)b[1] * (1.0 / 4294967296.0), &z0, &z1);
+      or_box_muller(((double)b[2] + 1.0) * (1.0 / 4294967296.0),
+                    (double)b[3] * (1.0 / 4294967296.0), &z2, &z3);
+      s->vx[i] = sd * z0;
+      s->vy[i] = sd * z1;
+      s->vz[i] = sd * z2;
+      s->id[i] = (uint64_t)i;
+    }
+    memset(s->absorbed, 0, sizeof(s->absorbed));
+    memset(s->coll, 0, sizeof(s->coll));
+    s->births = s->lost = s->clamps = s->candidates = 0;
+    s->ke = 0.0;
+  }
+  for (int si = 0; si < r->ns; ++si) or_null_rate(r, &r->sp[si]);
+  r->initialized = 1;
+  r->fe = 0.0;
+  return or_refresh(r);
+}
+
+int oracle_set_particles(or_run* r, int species, const double* X,
+                         const double* vx, const double* vy, const double* vz,
+                         const uint64_t* id, int64_t n) {
+  if (!r || species < 0 || species >= r->ns || n < 0) return -1;
+  if (!r->initialized) return -2;
+  or_species* s = &r->sp[species];
+  if (n > s->cap) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(X[i] >= 0.0) || !(X[i] < r->L)) return -1;
+    s->X[i] = X[i];
+    s->vx[i] = vx[i];
+    s->vy[i] = vy[i];
+    s->vz[i] = vz[i];
+    s->id[i] = id[i];
+  }
+  s->n = n;
+  return or_refresh(r);
+}
+
+int oracle_get_particles(or_run* r, int species, double* X, double* vx,
+                         double* vy, double* vz, uint64_t* id, int64_t cap,
+                         int64_t* n) {
+  if (!r || species < 0 || species >= r->ns || !n) return -1;
+  or_species* s = &r->sp[species];
+  *n = s->n;
+  if (cap < s->n) return -1;
+  for (int64_t i = 0; i < s->n; ++i) {
+    if (X) X[i] = s->X[i];
+    if (vx) vx[i] = s->vx[i];
+    if (vy) vy[i] = s->vy[i];
+    if (vz) vz[i] = s->vz[i];
+    if (id) id[i] = s->id[i];
+  }
+  return 0;
+}
+
+int oracle_set_particles_cell(or_run* r, int species, const int32_t* cell,
+                              const float* xi, const float* vx,
+                              const float* vy, const float* vz,
+                              const uint64_t* id, int64_t n) {
+  if (!r || species < 0 || species >= r->ns || n < 0) return -1;
+  if (!r->initialized) return -2;
+  or_species* s = &r->sp[species];
+  if (n > s->cap) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int j = cell[i];
+    if (j < 0 || j >= r->N || !(xi[i] >= 0.0f) || !(xi[i] < 1.0f)) return -1;
+    double X = r->x[j] + (double)xi[i] * r->dx[j];
+    if (X >= r->L) X = r->x[j];
+    s->X[i] = X;
+    s->vx[i] = (double)vx[i];
+    s->vy[i] = (double)vy[i];
+    s->vz[i] = (double)vz[i];
+    s->id[i] = id[i];
+  }
+  s->n = n;
+  return or_refresh(r);
+}
+
+int oracle_get_particles_cell(or_run* r, int species, int32_t* cell,
+                              double* xi, int64_t cap, int64_t* n) {
+  if (!r || species < 0 || species >= r->ns || !n) return -1;
+  or_species* s = &r->sp[species];
+  *n = s->n;
+  if (cap < s->n) return -1;
+  for (int64_t i = 0; i < s->n; ++i) {
+    int j = or_locate(r, s->X[i]);
+    if (cell) cell[i] = j;
+    if (xi) xi[i] = (s->X[i] - r->x[j]) / r->dx[j];
+  }
+  return 0;
+}
+
+static int or_append(or_species* s, double X, double vx, double vy, double vz,
+                     uint64_t id) {
+  if (s->n >= s->cap) {
+    s->lost++;
+    return -4;
+  }
+  s->X[s->n] = X; s->vx[s->n] = vx; s->vy[s->n] = vy; s->vz[s->n] = vz;
+  s->id[s->n] = id;
+  s->n++;
+  return 0;
+}
+
+/* Step 6: null-collision Monte Carlo (Vahedi & Surendra) for one particle.
+ * Draws: block A = Philox(ctr = (id, step, (s<<8)|0)): r0 candidate,
+ * r1 process, r2/r3 scattering direction.  Heavy species: block B (|1) gives
+ * the target neutral's Maxwellian velocity.  Electron ionisation: block B
+ * gives the energy split (s0) and the secondary's direction (s1, s2), and
+ * block C (|2) the new ion's Maxwellian velocity. */
+static int or_collide(or_run* r, int si, int64_t i, int64_t k) {
+  or_species* s = &r->sp[si];
+  if (s->nproc == 0 || s->thr24 == 0) return 0;
+  uint64_t id = s->id[i];
+  uint32_t A[4];
+  or_draw(r, id, (uint32_t)k, (uint32_t)si << 8, A);
+  if ((A[0] >> 8) >= s->thr24) return 0;
+  s->candidates++;
+  double v[3] = {s->vx[i], s->vy[i], s->vz[i]};
+  double vn[3] = {0.0, 0.0, 0.0};
+  uint32_t B[4];
+  int haveB = 0;
+  if (s->heavy) {
+    or_draw(r, id, (uint32_t)k, ((uint32_t)si << 8) | 1u, B);
+    haveB = 1;
+    double z0, z1, z2, z3;
+    or_box_muller(or_u24_open(B[0]), or_u24(B[1]), &z0, &z1);
+    or_box_muller(or_u24_open(B[2]), or_u24(B[3]), &z2, &z3);
+    double sd = sqrt(OR_KB * r->Tg / r->mg);
+    vn[0] = sd * z0; vn[1] = sd * z1; vn[2] = sd * z2;
+  }
+  double g[3] = {v[0] - vn[0], v[1] - vn[1], v[2] - vn[2]};
+  double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  double gm = sqrt(g2);
+  double E = 0.5 * s->m * g2 / OR_QE;
+  double nu[OR_MAX_PROC];
+  double tot = 0.0;
+  for (int p = 0; p < s->nproc; ++p) {
+    nu[p] = r->ng * or_sigma(&s->proc[p], E) * gm;
+    tot += nu[p];
+  }
+  if (tot > s->nu_max) s->clamps++;
+  double R = or_u24(A[1]) * s->nu_max;
+  int chosen = -1;
+  double cum = 0.0;
+  for (int p = 0; p < s->nproc; ++p) {
+    cum += nu[p];
+    if (R < cum) {
+      chosen = p;
+      break;
+    }
+  }
+  if (chosen < 0) return 0; /* null collision */
+  s->coll[chosen]++;
+  const or_process* pr = &s->proc[chosen];
+  double d[3];
+  or_isotropic(or_u24(A[2]), or_u24(A[3]), d);
+  int rc = 0;
+  switch (pr->kind) {
+    case OR_ELASTIC: {
+      /* neutral at rest; energy loss (2m/M)(1 - cos chi) E */
+      double cchi = (gm > 0.0) ? (g[0] * d[0] + g[1] * d[1] + g[2] * d[2]) / gm : 1.0;
+      double E1 = E * (1.0 - 2.0 * s->m / r->mg * (1.0 - cchi));
+      double sp = sqrt(2.0 * E1 * OR_QE / s->m);
+      v[0] = sp * d[0]; v[1] = sp * d[1]; v[2] = sp * d[2];
+      break;
+    }
+    case OR_EXCITATION: {
+      double E1 = E - pr->thr;
+      double sp = sqrt(2.0 * E1 * OR_QE / s->m);
+      v[0] = sp * d[0]; v[1] = sp * d[1]; v[2] = sp * d[2];
+      break;
+    }
+    case OR_IONIZATION: {
+      if (!haveB) or_draw(r, id, (uint32_t)k, ((uint32_t)si << 8) | 1u, B);
+      double Erem = E - pr->thr;
+      double f = or_u24(B[0]);
+      double E1 = f * Erem, E2 = (1.0 - f) * Erem;
+      double sp1 = sqrt(2.0 * E1 * OR_QE / s->m);
+      double sp2 = sqrt(2.0 * E2 * OR_QE / s->m);
+      v[0] = sp1 * d[0]; v[1] = sp1 * d[1]; v[2] = sp1 * d[2];
+      double d2[3];
+      or_isotropic(or_u24(B[1]), or_u24(B[2]), d2);
+      uint32_t C[4];
+      or_draw(r, id, (uint32_t)k, ((uint32_t)si << 8) | 2u, C);
+      double z0, z1, z2, z3;
+      or_box_muller(or_u24_open(C[0]), or_u24(C[1]), &z0, &z1);
+      or_box_muller(or_u24_open(C[2]), or_u24(C[3]), &z2, &z3);
+      double sd = sqrt(OR_KB * r->Tg / r->mg);
+      double X = s->X[i];
+      s->births++;
+      if (or_append(s, X, sp2 * d2[0], sp2 * d2[1], sp2 * d2[2],
+                    oracle_child_id(id, k, 1)))
+        rc = -4;
+      if (or_append(&r->sp[pr->product], X, sd * z0, sd * z1, sd * z2,
+                    oracle_child_id(id, k, 2)))
+        rc = -4;
+      break;
+    }
+    case OR_ION_ELASTIC: {
+      /* isotropic in the centre-of-mass frame */
+      double M = s->m + r->mg;
+      double gm_new = gm;
+      for (int c = 0; c < 3; ++c) {
+        double vcm = (s->m * v[c] + r->mg * vn[c]) / M;
+        v[c] = vcm + (r->mg / M) * gm_new * d[c];
+      }
+      break;
+    }
+    case OR_CX: {
+      v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
+      break;
+    }
+  }
+  s->vx[i] = v[0]; s->vy[i] = v[1]; s->vz[i] = v[2];
+  return rc;
+}
+
+static int or_step_once(or_run* r) {
+  int64_t k = r->step;
+  int N = r->N;
+  int rc = 0;
+  /* field energy at time level k: face fields from phi^k */
+  double fe = 0.0;
+  for (int j = 0; j < N; ++j) {
+    double Ej = -(r->phi[j + 1] - r->phi[j]) / r->dx[j];
+    fe += 0.5 * OR_EPS0 * Ej * Ej * r->dx[j];
+  }
+  r->fe = fe;
+  /* steps 4-5 (Eq. 6-9), then the walls */
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    double qm = s->q / s->m;
+    double ke = 0.0;
+    int64_t keep = 0;
+    for (int64_t i = 0; i < s->n; ++i) {
+      double X = s->X[i];
+      int j = or_locate(r, X);
+      double xi = (X - r->x[j]) / r->dx[j];
+      double Ei = (r->scheme == OR_SCHEME_EC) ? r->E[j]
+                                               : (1.0 - xi) * r->E[j] + xi * r->E[j + 1];
+      double vold = s->vx[i];
+      double vnew = vold + qm * Ei * r->dt;
+      ke += 0.5 * s->m * s->w * (vold * vnew + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+      double Xn = X + vnew * r->dt;
+      if (r->bc == OR_DIRICHLET) {
+        if (Xn <= 0.0) { s->absorbed[0]++; continue; }
+        if (Xn >= r->L) { s->absorbed[1]++; continue; }
+      } else {
+        Xn = Xn - r->L * floor(Xn / r->L);
+        if (Xn >= r->L || Xn < 0.0) Xn = 0.0;
+      }
+      s->X[keep] = Xn;
+      s->vx[keep] = vnew;
+      s->vy[keep] = s->vy[i];
+      s->vz[keep] = s->vz[i];
+      s->id[keep] = s->id[i];
+      keep++;
+    }
+    s->n = keep;
+    s->ke = ke;
+  }
+  /* step 6 on the survivors; particles born now are not collided now */
+  int64_t n0[OR_MAX_SPECIES];
+  for (int si = 0; si < r->ns; ++si) n0[si] = r->sp[si].n;
+  for (int si = 0; si < r->ns; ++si)
+    for (int64_t i = 0; i < n0[si]; ++i)
+      if (or_collide(r, si, i, k)) rc = -4;
+  /* steps 1-3 at k+1 */
+  r->step = k + 1;
+  int e = or_refresh(r);
+  if (e) return e;
+  if (r->sample_every > 0 && r->step % r->sample_every == 0) or_sample(r);
+  return rc;
+}
+
+int oracle_step(or_run* r, int64_t n_steps) {
+  if (!r || n_steps < 0) return -1;
+  if (!r->initialized) return -2;
+  int rc = 0;
+  for (int64_t t = 0; t < n_steps; ++t) {
+    int e = or_step_once(r);
+    if (e == -4) rc = -4;
+    else if (e) return e;
+  }
+  return rc;
+}
+
+int oracle_reset_averages(or_run* r, int sample_every) {
+  if (!r || sample_every < 0) return -1;
+  if (!r->grid_set) return -2;
+  r->sample_every = sample_every;
+  r->n_samples = 0;
+  size_t nn = (size_t)r->N + 1;
+  memset(r->acc_phi, 0, sizeof(double) * nn);
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    memset(s->acc_n, 0, sizeof(double) * nn);
+    memset(s->acc_T, 0, sizeof(double) * nn);
+    memset(s->acc_M0, 0, sizeof(double) * nn);
+    memset(s->acc_M1, 0, sizeof(double) * nn);
+    memset(s->acc_M2, 0, sizeof(double) * nn);
+  }
+  return 0;
+}
+
+int oracle_get_counters(const or_run* r, int64_t* out, int cap) {
+  if (!r || !out || cap < 1 + 16 * OR_MAX_SPECIES) return -1;
+  memset(out, 0, sizeof(int64_t) * (size_t)cap);
+  out[0] = r->step;
+  for (int si = 0; si < r->ns; ++si) {
+    const or_species* s = &r->sp[si];
+    int64_t* o = out + 1 + 16 * si;
+    o[0] = s->n;
+    o[1] = s->absorbed[0];
+    o[2] = s->absorbed[1];
+    o[3] = s->births;
+    o[4] = s->lost;
+    o[5] = s->clamps;
+    o[6] = s->candidates;
+    for (int p = 0; p < OR_MAX_PROC; ++p) o[7 + p] = s->coll[p];
+  }
+  return 0;
+}
+
+int oracle_get_fields(const or_run* r, double* phi, double* E, double* Q) {
+  if (!r || !r->grid_set) return -1;
+  int N = r->N;
+  if (phi) memcpy(phi, r->phi, sizeof(double) * (size_t)(N + 1));
+  if (E) memcpy(E, r->E, sizeof(double) * (size_t)(r->scheme == OR_SCHEME_EC ? N : N + 1));
+  if (Q) memcpy(Q, r->Q, sizeof(double) * (size_t)(N + 1));
+  return 0;
+}
+
+int oracle_get_energy(const or_run* r, double* ke, double* fe) {
+  if (!r) return -1;
+  if (ke)
+    for (int si = 0; si < r->ns; ++si) ke[si] = r->sp[si].ke;
+  if (fe) *fe = r->fe;
+  return 0;
+}
+
+int64_t oracle_get_averages(const or_run* r, double* density, double* phi,
+                            double* Tx, double* Tx_mom) {
+  if (!r || !r->grid_set) return -1;
+  int64_t ns = r->n_samples;
+  int N = r->N;
+  double inv = ns > 0 ? 1.0 / (double)ns : 0.0;
+  for (int si = 0; si < r->ns; ++si) {
+    const or_species* s = &r->sp[si];
+    for (int n = 0; n <= N; ++n) {
+      size_t o = (size_t)si * (size_t)(N + 1) + (size_t)n;
+      if (density) density[o] = s->acc_n[n] * inv;
+      if (Tx) Tx[o] = s->acc_T[n] * inv;
+      if (Tx_mom) {
+        double M0 = s->acc_M0[n];
+        double T = 0.0;
+        if (M0 > 0.0) {
+          double m1 = s->acc_M1[n] / M0, m2 = s->acc_M2[n] / M0;
+          T = s->m * (m2 - m1 * m1) / OR_QE;
+        }
+        Tx_mom[o] = T;
+      }
+    }
+  }
+  if (phi)
+    for (int n = 0; n <= N; ++n) phi[n] = r->acc_phi[n] * inv;
+  return ns;
+}
