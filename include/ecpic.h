@@ -1,0 +1,190 @@
+/*
+ * ecpic.h -- C ABI of libecpic, a GB300 (sm_103a) implementation of the
+ * explicit energy-conserving particle-in-cell method (EC-PIC) for 1D3V
+ * radio-frequency capacitively coupled discharges, after Powis & Kaganovich,
+ * "Accuracy of the Explicit Energy-Conserving Particle-in-Cell Method for
+ * Under-resolved Simulations of Capacitively Coupled Plasma Discharges"
+ * (arXiv 2308.13092).  Section, equation and table numbers below refer to
+ * that paper.
+ *
+ * Conventions
+ *  - Every call returns an ecpic_status (0 = ECPIC_OK, negative = error);
+ *    no C++ exception crosses this boundary.  ecpic_last_error() gives a
+ *    human-readable message for the last failing call on a handle.
+ *  - Host input arrays are copied; the caller keeps ownership.  Output
+ *    buffers are allocated by the caller.  All device memory is owned by the
+ *    handle that allocated it and released by its destroy call.
+ *  - Pointers documented as "device" must point to memory of the handle's
+ *    CUDA device; every other pointer is host memory.
+ *  - Work is queued on the stream given at creation (NULL = the legacy
+ *    default stream); calls marked "async" return before the GPU finishes and
+ *    report device-side errors at the next ecpic_sync().
+ *  - One handle must not be used from two host threads at once.
+ *  - Calling out of order (for example step before init) returns
+ *    ECPIC_ERR_STATE.
+ *
+ * Units are SI; energies in eV where noted.  Positions are cell-relative:
+ * particle p lies at X = x[cell] + xi * (x[cell+1] - x[cell]), xi in [0,1).
+ */
+#ifndef ECPIC_H
+#define ECPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ECPIC_OK = 0,
+  ECPIC_ERR_ARG = -1,      /* invalid argument */
+  ECPIC_ERR_STATE = -2,    /* call out of order */
+  ECPIC_ERR_NOMEM = -3,    /* device allocation or memory budget */
+  ECPIC_ERR_CAPACITY = -4, /* particle births exceeded a species capacity */
+  ECPIC_ERR_CUDA = -5,     /* CUDA runtime error */
+  ECPIC_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
+  ECPIC_ERR_NAN = -7       /* non-finite particle state detected */
+} ecpic_status;
+
+#define ECPIC_MAX_SPECIES 4
+#define ECPIC_MAX_PROC 8
+#define ECPIC_MAX_CELLS 2048
+
+/* boundary conditions */
+#define ECPIC_DIRICHLET_RF 0 /* phi_0 = RF waveform at x = 0, phi_N = 0 */
+#define ECPIC_PERIODIC 1     /* periodic, uniform neutralising background */
+/* field/gather scheme (Sec. 2a steps 3-4) */
+#define ECPIC_SCHEME_EC 0 /* face field Eq. 5, shifted NGP gather Eq. 6-7 */
+#define ECPIC_SCHEME_MC 1 /* centred node field, CIC gather */
+/* collision processes (Sec. 2b) */
+#define ECPIC_ELASTIC 0     /* electron-neutral elastic, neutral at rest */
+#define ECPIC_EXCITATION 1  /* electron-impact excitation */
+#define ECPIC_IONIZATION 2  /* electron-impact ionisation: births e + ion */
+#define ECPIC_ION_ELASTIC 3 /* ion-neutral elastic, isotropic in CM frame */
+#define ECPIC_CX 4          /* ion-neutral charge exchange */
+
+typedef struct ecpic_run ecpic_run;
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics (Sec. 3a: moments averaged at intervals; temperature is
+ * the standard deviation of the x velocity distribution).  Scalars are
+ * always filled; each array pointer may be NULL, else it must hold
+ * n_species * (N+1) (per-species arrays) or N+1 (phi) doubles. */
+typedef struct {
+  int64_t step;                                /* time level reached */
+  double time;                                 /* step * dt */
+  int n_species;
+  int n_cells;
+  int64_t n_live[ECPIC_MAX_SPECIES];           /* particles now */
+  int64_t absorbed[ECPIC_MAX_SPECIES][2];      /* at x=0 and x=L, total */
+  int64_t births[ECPIC_MAX_SPECIES];           /* ionisation events */
+  int64_t lost[ECPIC_MAX_SPECIES];             /* births dropped: capacity */
+  int64_t candidates[ECPIC_MAX_SPECIES];       /* null-collision candidates */
+  int64_t clamps[ECPIC_MAX_SPECIES];           /* nu_tot > nu_max seen */
+  int64_t collisions[ECPIC_MAX_SPECIES][ECPIC_MAX_PROC];
+  double ke[ECPIC_MAX_SPECIES]; /* sum 1/2 m w (vx^- vx^+ + vy^2 + vz^2), J/m^2,
+                                   at the last sampled push */
+  double fe;                    /* 1/2 eps0 sum_j E_j^2 dx_j at that level */
+  int64_t n_samples;            /* samples in the averages */
+  double* density;              /* [s][n] averaged density, m^-3 */
+  double* phi;                  /* [n] averaged potential, V */
+  double* temp_x;               /* [s][n] mean of per-sample T_x, eV */
+  double* temp_x_mom;           /* [s][n] T_x of the averaged moments, eV */
+} ecpic_diag;
+
+/* ------------------------------------------------------------------ */
+/* Single run.  Order: create -> set_grid -> set_scheme? -> add_species+
+ * -> set_gas? -> add_process* -> init -> step / diagnostics / particles.
+ * `device` is the CUDA ordinal; `cuda_stream` a cudaStream_t or NULL. */
+int ecpic_create(ecpic_run** out, int device, void* cuda_stream);
+void ecpic_destroy(ecpic_run* run);
+const char* ecpic_last_error(const ecpic_run* run);
+
+/* Grid and electrode bias (Sec. 2a step 2, Sec. 2b, Sec. 3c).  edges: N+1
+ * strictly increasing node positions, edges[0] == 0, 2 <= N <=
+ * ECPIC_MAX_CELLS; copied.  phi_0(t) = v_dc + v0 sin(2 pi f t + phase) at
+ * x = 0 and phi_N = 0 (Dirichlet), or periodic. */
+int ecpic_set_grid(ecpic_run* run, const double* edges, int n_edges, int bc,
+                   double v0, double freq_hz, double phase_rad, double v_dc);
+int ecpic_set_scheme(ecpic_run* run, int scheme);
+/* Species (Eq. 2 charge q, mass m, macro-particle weight w in m^-2) with a
+ * particle capacity (births beyond it are dropped and counted). */
+int ecpic_add_species(ecpic_run* run, double q_C, double m_kg,
+                      double weight_per_m2, int64_t capacity, int* species_out);
+/* Background gas (Table 1: density, temperature) and its particle mass. */
+int ecpic_set_gas(ecpic_run* run, double n_g_m3, double T_g_K, double m_g_kg);
+/* Cross section sigma(E) tabulated at E = i*dE (eV), i < n, linear in
+ * between, held at sigma[n-1] above, zero below threshold_eV.  All
+ * processes of one species share (dE, n).  product_species: the species
+ * receiving the ion of an ionisation (else ignored).  Copied. */
+int ecpic_add_process(ecpic_run* run, int species, int kind, double threshold_eV,
+                      double dE_eV, int n, const float* sigma_m2, int product_species);
+/* Load n_per_species[s] particles uniformly in [0, L) with Maxwellian
+ * velocities of T_eV[s] (Sec. 2b), ids 0..n-1, from the counter-based
+ * Philox4x32-10 stream keyed on `seed`; time step dt; then deposit and
+ * solve the field of step 0.  Allocates all device memory. */
+int ecpic_init(ecpic_run* run, uint64_t seed, double dt_s,
+               const int64_t* n_per_species, const double* T_eV);
+/* Advance n_steps (async).  One step: EC (or MC) gather and leapfrog push
+ * (Eq. 6-9), wall absorption, null-collision MCC, CIC deposit (Eq. 2-3),
+ * Poisson (Eq. 4) and field (Eq. 5) of the next time level. */
+int ecpic_step(ecpic_run* run, int64_t n_steps);
+/* Wait for queued work; return the first device-side error of the run. */
+int ecpic_sync(ecpic_run* run);
+/* Restart the time averages; sample every `sample_every` steps (0 = off). */
+int ecpic_reset_averages(ecpic_run* run, int sample_every);
+int ecpic_diagnostics(ecpic_run* run, ecpic_diag* out);
+/* Live particles of a species (synchronises).  Returns ECPIC_ERR_ARG with
+ * *n set if cap is too small.  Any pointer may be NULL. */
+int ecpic_get_particles(ecpic_run* run, int species, int32_t* cell, float* xi,
+                        float* vx, float* vy, float* vz, uint64_t* id,
+                        int64_t cap, int64_t* n);
+/* Replace a species' particles (after init); recomputes the current field. */
+int ecpic_set_particles(ecpic_run* run, int species, const int32_t* cell,
+                        const float* xi, const float* vx, const float* vy,
+                        const float* vz, const uint64_t* id, int64_t n);
+/* Fields of the current time level: phi[N+1] (FP64), E[N] for EC or [N+1]
+ * for MC (the FP32 values the push uses).  Either may be NULL. */
+int ecpic_get_fields(ecpic_run* run, double* phi, float* E);
+/* Null-collision bound of a species: nu_max (1/s) and the 24-bit candidate
+ * threshold ceil((1 - exp(-nu_max dt)) 2^24). */
+int ecpic_nu_max(ecpic_run* run, int species, double* nu_max, uint32_t* threshold24);
+/* Counting-sort cadence in steps (>= 1; default 16). */
+int ecpic_set_sort_every(ecpic_run* run, int sort_every);
+/* Force a counting sort by cell now (compacts absorbed particles). */
+int ecpic_sort_now(ecpic_run* run);
+/* Measurement: advance n_steps with plain launches (no graph), bracketing
+ * each kernel phase with CUDA events on the run's stream; synchronises.
+ * ms[0..2] = summed device time of the particle pass, the field solve and the
+ * counting sort; launches[0..2] = their launch counts.  Same physics as
+ * ecpic_step. */
+int ecpic_profile_step(ecpic_run* run, int64_t n_steps, double* ms, int64_t* launches);
+/* Pass-kernel grid size override (0 = automatic); for tuning. */
+int ecpic_set_pass_grid(ecpic_run* run, int ctas);
+
+/* ------------------------------------------------------------------ */
+/* Doubling non-uniform grid (Sec. 3c rules 1-4): buffers of dx_min cells of
+ * total length >= L_buff at both electrodes, then cell sizes doubling up to
+ * dx_max (sizes in units of dx_ref = L/n_ref).  Writes the N+1 edges (m) into
+ * edges[cap] and returns N (> 0), or a negative ecpic_status. */
+int ecpic_doubling_grid(int n_ref, double L, double L_buff, int dx_min, int dx_max,
+                        double* edges, int cap);
+
+/* ------------------------------------------------------------------ */
+/* Kernel-level entry points on caller-owned device memory (tests, tools).
+ * Fixed-point CIC deposit (Eq. 2-3 in units of 2^-32 particle): for each
+ * particle r = floor(xi*2^32), S[cell] += 2^32 - r, S[cell+1] += r.
+ * d_cell/d_xi: device, n entries; d_S: device, N+1 uint64, accumulated.
+ * Particles with cell < 0 are skipped.  Async on cuda_stream. */
+int ecpic_deposit_device(int N, int64_t n, const int32_t* d_cell, const float* d_xi,
+                         uint64_t* d_S, void* cuda_stream);
+/* Philox4x32-10 on the device: out[4i..4i+3] = Philox(counter = ctr[4i..],
+ * key = key[2i..]) for i < n.  All pointers device.  Async. */
+int ecpic_philox_device(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key,
+                        uint32_t* d_out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

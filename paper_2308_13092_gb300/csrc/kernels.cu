@@ -1,0 +1,1037 @@
+// kernels.cu -- the sm_103a kernels of libecpic.
+//
+// One time step of every resident run is two launches:
+//   k_pass   fused gather (Eq. 6-7, or CIC for the MC scheme) -> leapfrog
+//            push (Eq. 8-9) in cell-relative FP32 -> wall absorption ->
+//            null-collision MCC (Sec. 2a step 6) -> fixed-point CIC deposit
+//            (Eq. 2-3) of the new positions, over all (run, species)
+//            segments, load-balanced by particle count;
+//   k_field  per run: charge from the deposit, Poisson (Eq. 4) in its
+//            two-scan form, field (Eq. 5 or centred), potential, sampling.
+// Every K steps a counting sort by cell (k_hist, k_scan, k_scatter,
+// k_finalize) restores cell order and drops absorbed particles.
+#include <cfloat>
+#include <climits>
+
+#include "kernels.h"
+
+namespace ecpic {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// ----------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// exclusive scan over the block (blockDim a multiple of 32); wsm >= 32 entries
+template <typename T>
+__device__ T block_excl_scan(T v, T* wsm, T* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T inc = warp_incl_scan(v);
+  if (lane == 31) wsm[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T t = lane < nw ? wsm[lane] : T(0);
+    t = warp_incl_scan(t);
+    if (lane < nw) wsm[lane] = t;
+  }
+  __syncthreads();
+  const T off = w > 0 ? wsm[w - 1] : T(0);
+  *total = wsm[nw - 1];
+  __syncthreads();
+  return off + inc - v;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* wsm) {
+  T total;
+  block_excl_scan(v, wsm, &total);
+  return total;
+}
+
+// in-place inclusive scan of a[0..n) held in shared memory (fixed partition,
+// so the FP64 rounding is deterministic)
+template <typename T>
+__device__ void block_incl_scan_array(T* a, int n, T* wsm) {
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
+  T loc = T(0);
+  for (int i = beg; i < end; ++i) loc += a[i];
+  T total;
+  T run = block_excl_scan(loc, wsm, &total);
+  for (int i = beg; i < end; ++i) {
+    run += a[i];
+    a[i] = run;
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------- segments
+__device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int mode, int only,
+                                         int slot) {
+  if (!R.active) return false;
+  if (mode == MODE_REFRESH) return slot == only;
+  if (S.status != 0) return false;
+  if (mode == MODE_STEP) return S.step < S.step_end;
+  return true;
+}
+
+// exclusive prefix of the particle counts of all segments: pre[0..nseg]
+__device__ long long seg_prefix(const BatchView& b, int mode, int only, long long* pre,
+                                long long* wsm) {
+  const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per;
+  long long loc = 0;
+  for (int k = 0; k < per; ++k) {
+    const int s = s0 + k;
+    if (s < b.nseg) {
+      const int slot = b.segs[s].run;
+      const long long c =
+          run_live(b.runs[slot], b.rst[slot], mode, only, slot) ? b.sst[s].n_proc : 0;
+      pre[s] = c;
+      loc += c;
+    }
+  }
+  long long total;
+  long long run = block_excl_scan(loc, wsm, &total);
+  for (int k = 0; k < per; ++k) {
+    const int s = s0 + k;
+    if (s < b.nseg) {
+      const long long c = pre[s];
+      pre[s] = run;
+      run += c;
+    }
+  }
+  if (threadIdx.x == 0) pre[b.nseg] = total;
+  __syncthreads();
+  return total;
+}
+
+// first segment s with pre[s] <= v < pre[s+1]
+__device__ __forceinline__ int seg_find(const long long* pre, int nseg, long long v) {
+  int lo = 0, hi = nseg;  // pre[lo] <= v, answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ----------------------------------------------------------------- deposit
+// Warp-aggregated fixed-point CIC deposit into shared memory: lanes that hold
+// the same cell add their shares once.  S[c] += 2^32 - r, S[c+1] += r with
+// r = floor(xi * 2^32) (xi * 2^32 is exact in FP32; rz truncation = floor).
+__device__ __forceinline__ void deposit_warp(unsigned long long* Ssm, bool valid, int c, float f) {
+  const unsigned key = valid ? (unsigned)c : 0xFFFFFFFFu;
+  const unsigned grp = __match_any_sync(kFull, key);
+  if (!valid) return;
+  const unsigned r = __float2uint_rz(f * 4294967296.0f);
+  const unsigned lo16 = __reduce_add_sync(grp, r & 0xFFFFu);
+  const unsigned hi16 = __reduce_add_sync(grp, r >> 16);
+  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+    const unsigned long long sr = ((unsigned long long)hi16 << 16) + (unsigned long long)lo16;
+    const unsigned long long cnt = (unsigned long long)__popc(grp);
+    atomicAdd(Ssm + c, (cnt << 32) - sr);
+    atomicAdd(Ssm + c + 1, sr);
+  }
+}
+
+__device__ __forceinline__ void deposit_one(unsigned long long* S, int c, float f) {
+  const unsigned r = __float2uint_rz(f * 4294967296.0f);
+  atomicAdd(S + c, 4294967296ull - (unsigned long long)r);
+  atomicAdd(S + c + 1, (unsigned long long)r);
+}
+
+// ----------------------------------------------------------------- MCC helpers
+__device__ __forceinline__ float sigma_at(const float* tab, float thr, float E, float dE_inv, int n) {
+  if (E < thr) return 0.f;
+  const float u = E * dE_inv;
+  const float fi = floorf(u);
+  if (fi >= (float)(n - 1)) return __ldg(tab + n - 1);
+  const int i = (int)fi;
+  const float t = u - fi;
+  const float s0 = __ldg(tab + i), s1 = __ldg(tab + i + 1);
+  return s0 + t * (s1 - s0);
+}
+
+__device__ __forceinline__ void box_muller(float u1, float u2, float& z0, float& z1) {
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// unit vector uniform on the sphere, polar axis along x
+__device__ __forceinline__ void isotropic(float ua, float ub, float& d0, float& d1, float& d2) {
+  const float c = 1.0f - 2.0f * ua;
+  const float s = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+  float sp, cp;
+  sincospif(2.0f * ub, &sp, &cp);
+  d0 = c;
+  d1 = s * cp;
+  d2 = s * sp;
+}
+
+__device__ __forceinline__ void set_status(RunState* st, int code) {
+  atomicCAS(&st->status, 0, code);
+}
+
+// append a particle to a segment (births); false if the capacity is full
+__device__ __forceinline__ bool append_particle(const SegDev& G, SegState* ss, int c, float f,
+                                                float vx, float vy, float vz, uint64_t id) {
+  const long long idx = (long long)atomicAdd((unsigned long long*)&ss->n_alloc, 1ull);
+  if (idx >= G.cap) return false;
+  const int cur = ss->cur;
+  G.cell[cur][idx] = c;
+  G.xi[cur][idx] = f;
+  G.vx[cur][idx] = vx;
+  G.vy[cur][idx] = vy;
+  G.vz[cur][idx] = vz;
+  G.id[cur][idx] = id;
+  return true;
+}
+
+// cell walk on a non-uniform grid: g = xi + vx dt/dx_c, carried into the
+// neighbours with their width ratios; FP32 rounding to 1.0f puts the particle
+// on the next face (xi = 0)
+__device__ __forceinline__ void walk_nonuniform(int& c, float& f, float g, int N, int bc,
+                                                const float* rp, const float* rm) {
+  int guard = 0;
+  while (g >= 1.0f) {
+    if (c == N - 1 && bc != ECPIC_PERIODIC) { c = N; g = 0.0f; break; }
+    g = (g - 1.0f) * __ldg(rp + c);
+    c = (c == N - 1) ? 0 : c + 1;
+    if (++guard > N) { g = 0.0f; break; }
+  }
+  while (g < 0.0f) {
+    if (c == 0 && bc != ECPIC_PERIODIC) { c = -1; g = 0.0f; break; }
+    g = 1.0f + g * __ldg(rm + c);
+    c = (c == 0) ? N - 1 : c - 1;
+    if (g >= 1.0f) {
+      c = (c == N - 1) ? 0 : c + 1;
+      g = 0.0f;
+    }
+    if (++guard > N) { g = 0.0f; break; }
+  }
+  f = g;
+}
+
+struct PassShared {
+  unsigned long long ctr[kNumCtr];
+  long long wsm[32];
+  double dsm[32];
+  int lohi[2];
+};
+
+// one piece [beg, end) of segment s
+__device__ void pass_piece(const BatchView& b, int s, long long beg, long long end, int mode,
+                           unsigned long long* Ssm, float* Msm, PassShared& sh) {
+  const SegDev& G = b.segs[s];
+  const int slot = G.run, sp = G.species;
+  const RunDev* R = b.runs + slot;
+  RunState* st = b.rst + slot;
+  SegState* ss = b.sst + s;
+  const int N = R->N, scheme = R->scheme, bc = R->bc, uniform = R->uniform;
+  const int cur = ss->cur;
+  int32_t* __restrict__ pc = G.cell[cur];
+  float* __restrict__ pxi = G.xi[cur];
+  float* __restrict__ pvx = G.vx[cur];
+  float* __restrict__ pvy = G.vy[cur];
+  float* __restrict__ pvz = G.vz[cur];
+  const uint64_t* __restrict__ pid = G.id[cur];
+  const long long k = st->step;
+  const bool stepping = (mode == MODE_STEP);
+  const bool sample = stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0;
+  const SpeciesDev* SP = &R->sp[sp];
+  const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
+  const float* __restrict__ E = R->E;
+  const float* __restrict__ dtdx = R->dtdx;
+  const uint32_t thr24 = SP->thr24;
+  const int nproc = SP->nproc;
+  const uint64_t seed = R->seed;
+  const int Nm = b.nmax + 1;
+  const int lane = threadIdx.x & 31;
+
+  int my_lo = INT_MAX, my_hi = -1;
+  float ke = 0.0f;
+  unsigned cand = 0;
+
+  for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
+    const long long i = base + lane;
+    bool valid = i < end;
+    int c = valid ? pc[i] : -1;
+    valid = valid && c >= 0;
+    float f = 0.0f, vx = 0.0f;
+    if (valid) {
+      f = pxi[i];
+      vx = pvx[i];
+    }
+    if (valid && stepping) {
+      float vy = pvy[i], vz = pvz[i];
+      // gather: EC face field of the particle's cell (Eq. 6-7) or CIC (MC)
+      float Ei;
+      if (scheme == ECPIC_SCHEME_EC) {
+        Ei = __ldg(E + c);
+      } else {
+        const float e0 = __ldg(E + c), e1 = __ldg(E + c + 1);
+        Ei = e0 + f * (e1 - e0);
+      }
+      // leapfrog (Eq. 8)
+      const float vnew = vx + qm_dt * Ei;
+      if (sample) ke += vx * vnew + vy * vy + vz * vz;
+      vx = vnew;
+      if (!(fabsf(vx) < 3.0e8f)) {
+        // non-finite or superluminal: drop the particle, flag the run
+        pc[i] = -1;
+        atomicAdd(&sh.ctr[C_NAN], 1ull);
+        set_status(st, ECPIC_ERR_NAN);
+        valid = false;
+      } else {
+        // Eq. 9 in cell units
+        if (uniform) {
+          float g = f + vx * dtdx_u;
+          if (!(g >= 0.0f && g < 1.0f)) {
+            const float fl = floorf(g);
+            c += (int)fl;
+            g -= fl;
+            if (g >= 1.0f) {
+              c += 1;
+              g = 0.0f;
+            }
+            if (bc == ECPIC_PERIODIC) {
+              c %= N;
+              if (c < 0) c += N;
+            }
+          }
+          f = g;
+        } else {
+          walk_nonuniform(c, f, f + vx * __ldg(dtdx + c), N, bc, R->rp, R->rm);
+        }
+        // walls: X <= 0 or X >= L
+        if (bc != ECPIC_PERIODIC && (c < 0 || c >= N || (c == 0 && f == 0.0f))) {
+          pc[i] = -1;
+          atomicAdd(&sh.ctr[c >= N ? C_ABS_R : C_ABS_L], 1ull);
+          valid = false;
+        } else {
+          bool yz = false;
+          if (nproc > 0) {
+            const uint64_t id = pid[i];
+            const uint4 A = draw(seed, id, (uint32_t)k, (uint32_t)sp << 8);
+            if ((A.x >> 8) < thr24) {
+              ++cand;
+              float gx = vx, gy = vy, gz = vz, vnx = 0.f, vny = 0.f, vnz = 0.f;
+              if (SP->heavy) {
+                const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+                float z0, z1, z2, z3;
+                box_muller(u24_open(B.x), u24(B.y), z0, z1);
+                box_muller(u24_open(B.z), u24(B.w), z2, z3);
+                const float sd = R->vth_gas;
+                vnx = sd * z0;
+                vny = sd * z1;
+                vnz = sd * z2;
+                gx -= vnx;
+                gy -= vny;
+                gz -= vnz;
+              }
+              const float g2 = gx * gx + gy * gy + gz * gz;
+              const float gm = sqrtf(g2);
+              const float En = SP->half_m_over_e * g2;
+              const float ng = R->ng;
+              float nu[kMaxProc];
+              float tot = 0.0f;
+#pragma unroll
+              for (int p = 0; p < kMaxProc; ++p) {
+                nu[p] = 0.0f;
+                if (p < nproc) {
+                  nu[p] = ng * sigma_at(SP->proc[p].sigma, SP->proc[p].thr, En, SP->dE_inv, SP->ntab) * gm;
+                  tot += nu[p];
+                }
+              }
+              if (tot > SP->nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
+              const float Rr = u24(A.y) * SP->nu_max;
+              int chosen = -1;
+              float cum = 0.0f;
+#pragma unroll
+              for (int p = 0; p < kMaxProc; ++p) {
+                if (p < nproc && chosen < 0) {
+                  cum += nu[p];
+                  if (Rr < cum) chosen = p;
+                }
+              }
+              if (chosen >= 0) {
+                atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
+                float d0, d1, d2;
+                isotropic(u24(A.z), u24(A.w), d0, d1, d2);
+                const int kind = SP->proc[chosen].kind;
+                const float thr = SP->proc[chosen].thr;
+                yz = true;
+                if (kind == ECPIC_ELASTIC) {
+                  const float cchi = gm > 0.0f ? (gx * d0 + gy * d1 + gz * d2) / gm : 1.0f;
+                  const float E1 = En * (1.0f - SP->two_m_over_M * (1.0f - cchi));
+                  const float v1 = sqrtf(SP->two_e_over_m * E1);
+                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+                } else if (kind == ECPIC_EXCITATION) {
+                  const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
+                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+                } else if (kind == ECPIC_IONIZATION) {
+                  const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+                  const float Erem = En - thr;
+                  const float fr = u24(B.x);
+                  const float v1 = sqrtf(SP->two_e_over_m * (fr * Erem));
+                  const float v2 = sqrtf(SP->two_e_over_m * ((1.0f - fr) * Erem));
+                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+                  float e0, e1, e2;
+                  isotropic(u24(B.y), u24(B.z), e0, e1, e2);
+                  const uint4 Cw = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 2u);
+                  float z0, z1, z2, z3;
+                  box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
+                  box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
+                  const float sd = R->vth_gas;
+                  atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
+                  // secondary electron: same segment, deposited here
+                  if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
+                    deposit_one(Ssm, c, f);
+                    if (sample) {
+                      const float vb = v2 * e0;
+                      atomicAdd(Msm + c, (1.0f - f) * vb);
+                      atomicAdd(Msm + c + 1, f * vb);
+                      atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
+                      atomicAdd(Msm + Nm + c + 1, f * vb * vb);
+                    }
+                  } else {
+                    atomicAdd(&sh.ctr[C_LOST], 1ull);
+                    set_status(st, ECPIC_ERR_CAPACITY);
+                  }
+                  // ion: product species' segment, deposited straight to HBM
+                  const int ps = SP->proc[chosen].product_seg;
+                  const int pspec = SP->proc[chosen].product_species;
+                  const float ivx = sd * z0;
+                  if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2,
+                                      child_id(id, k, 2))) {
+                    deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
+                    if (sample) {
+                      double* md = R->momd + (size_t)pspec * 2 * (N + 1);
+                      atomicAdd(md + c, (double)((1.0f - f) * ivx));
+                      atomicAdd(md + c + 1, (double)(f * ivx));
+                      atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
+                      atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
+                    }
+                  } else {
+                    atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
+                    set_status(st, ECPIC_ERR_CAPACITY);
+                  }
+                } else if (kind == ECPIC_ION_ELASTIC) {
+                  const float h = SP->m_frac * gm;
+                  vx = SP->mass_frac * vx + SP->m_frac * vnx + h * d0;
+                  vy = SP->mass_frac * vy + SP->m_frac * vny + h * d1;
+                  vz = SP->mass_frac * vz + SP->m_frac * vnz + h * d2;
+                } else {  // ECPIC_CX
+                  vx = vnx; vy = vny; vz = vnz;
+                }
+              }
+            }
+          }
+          pc[i] = c;
+          pxi[i] = f;
+          pvx[i] = vx;
+          if (yz) {
+            pvy[i] = vy;
+            pvz[i] = vz;
+          }
+        }
+      }
+    }
+    // fixed-point CIC deposit of X^{k+1} (Eq. 2-3)
+    deposit_warp(Ssm, valid, c, f);
+    if (valid) {
+      my_lo = min(my_lo, c);
+      my_hi = max(my_hi, c + 1);
+      if (sample) {
+        atomicAdd(Msm + c, (1.0f - f) * vx);
+        atomicAdd(Msm + c + 1, f * vx);
+        atomicAdd(Msm + Nm + c, (1.0f - f) * vx * vx);
+        atomicAdd(Msm + Nm + c + 1, f * vx * vx);
+      }
+    }
+  }
+
+  // piece epilogue: node range, energy, counters, flush to HBM
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_lo = min(my_lo, __shfl_xor_sync(kFull, my_lo, o));
+    my_hi = max(my_hi, __shfl_xor_sync(kFull, my_hi, o));
+  }
+  cand = warp_sum(cand);
+  if (lane == 0) {
+    if (my_hi >= 0) {
+      atomicMin(&sh.lohi[0], my_lo);
+      atomicMax(&sh.lohi[1], my_hi);
+    }
+    if (cand) atomicAdd(&sh.ctr[C_CAND], (unsigned long long)cand);
+  }
+  if (sample) {
+    const double kes = block_sum((double)ke, sh.dsm);
+    if (threadIdx.x == 0) atomicAdd(&st->ke_acc[sp], 0.5 * SP->m * SP->w * kes);
+  }
+  __syncthreads();
+  const int flo = sh.lohi[0], fhi = sh.lohi[1];
+  unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
+  double* md = R->momd + (size_t)sp * 2 * (N + 1);
+  for (int n = flo + (int)threadIdx.x; n <= fhi; n += kPassBlock) {
+    const unsigned long long v = Ssm[n];
+    if (v) {
+      atomicAdd(Sg + n, v);
+      Ssm[n] = 0ull;
+    }
+    if (sample) {
+      const float m1 = Msm[n], m2 = Msm[Nm + n];
+      if (m1 != 0.0f) atomicAdd(md + n, (double)m1);
+      if (m2 != 0.0f) atomicAdd(md + (N + 1) + n, (double)m2);
+      Msm[n] = 0.0f;
+      Msm[Nm + n] = 0.0f;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long dead = sh.ctr[C_ABS_L] + sh.ctr[C_ABS_R] + sh.ctr[C_NAN];
+    if (dead) atomicAdd((unsigned long long*)&ss->n_dead, dead);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumCtr) {
+    const unsigned long long v = sh.ctr[threadIdx.x];
+    if (v) {
+      atomicAdd(&st->ctr[sp][threadIdx.x], v);
+      sh.ctr[threadIdx.x] = 0ull;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sh.lohi[0] = INT_MAX;
+    sh.lohi[1] = -1;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPassBlock) k_pass(BatchView b, int mode, int only) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* pre = reinterpret_cast<long long*>(smem_raw);
+  unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
+  float* Msm = reinterpret_cast<float*>(Ssm + b.nmax + 1);
+  __shared__ PassShared sh;
+  for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
+    Ssm[i] = 0ull;
+    Msm[i] = 0.0f;
+    Msm[b.nmax + 1 + i] = 0.0f;
+  }
+  if (threadIdx.x < kNumCtr) sh.ctr[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) {
+    sh.lohi[0] = INT_MAX;
+    sh.lohi[1] = -1;
+  }
+  const long long T = seg_prefix(b, mode, only, pre, sh.wsm);
+  if (T == 0) return;
+  const long long lo = T * (long long)blockIdx.x / gridDim.x;
+  const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  for (int s = seg_find(pre, b.nseg, lo); s < b.nseg && pre[s] < hi; ++s) {
+    const long long beg = max(lo, pre[s]) - pre[s];
+    const long long end = min(hi, pre[s + 1]) - pre[s];
+    if (beg >= end) continue;
+    pass_piece(b, s, beg, end, mode, Ssm, Msm, sh);
+  }
+}
+
+// ----------------------------------------------------------------- field
+// Poisson (Eq. 4 in finite-volume form) solved through Gauss's law: with
+// g_n = (phi_{n+1}-phi_n)/dx_n, Eq. 4 reads g_n - g_{n-1} = -Q_n/eps0, so
+// g_n = g_0 - C_n/eps0 with C_n = sum_{m=1..n} Q_m, and the boundary values
+// fix g_0 = (phi_N - phi_0 + sum_n dx_n C_n / eps0) / L.  This is the exact
+// solution of the same tridiagonal system that a Thomas sweep solves, in two
+// parallel scans.  EC field E_j = -g_j (Eq. 5).
+__global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance, int only) {
+  const int slot = blockIdx.x;
+  if (slot >= b.max_slots) return;
+  const RunDev* R = b.runs + slot;
+  if (!R->active) return;
+  RunState* st = b.rst + slot;
+  if (advance) {
+    if (st->status != 0 || st->step >= st->step_end) return;
+  } else if (only >= 0 && slot != only) {
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Q = reinterpret_cast<double*>(smem_raw);  // N+1
+  double* g = Q + (b.nmax + 1);                     // N+1
+  __shared__ double dsm[32];
+  const int N = R->N, ns = R->ns;
+  const int tid = threadIdx.x;
+  const long long kn = advance ? st->step + 1 : st->step;
+  const bool sample = advance && R->sample_every > 0 && (kn % R->sample_every) == 0;
+  const bool periodic = (R->bc == ECPIC_PERIODIC);
+  const double* V = R->V;
+  const double* dx = R->dx;
+
+  // sampled moments (Sec. 3a: density and x temperature per node)
+  if (sample) {
+    double* acc = R->acc;
+    for (int n = tid; n <= N; n += kFieldBlock) {
+      for (int s = 0; s < ns; ++s) {
+        const unsigned long long* S = R->S + (size_t)s * (N + 1);
+        const double* md = R->momd + (size_t)s * 2 * (N + 1);
+        double D, M1, M2;
+        if (periodic && (n == 0 || n == N)) {
+          D = (double)S[0] + (double)S[N];
+          M1 = md[0] + md[N];
+          M2 = md[N + 1] + md[N + 1 + N];
+        } else {
+          D = (double)S[n];
+          M1 = md[n];
+          M2 = md[N + 1 + n];
+        }
+        D *= 2.3283064365386963e-10;  // 2^-32
+        const double m = R->sp[s].m;
+        double T = 0.0;
+        if (D > 0.0) {
+          const double a = M1 / D, c2 = M2 / D;
+          T = m * (c2 - a * a) / 1.602176634e-19;
+        }
+        acc[(size_t)s * (N + 1) + n] += R->sp[s].w * D / V[n];
+        acc[(size_t)(ns + s) * (N + 1) + n] += T;
+        acc[(size_t)(2 * ns + s) * (N + 1) + n] += D;
+        acc[(size_t)(3 * ns + s) * (N + 1) + n] += M1;
+        acc[(size_t)(4 * ns + s) * (N + 1) + n] += M2;
+      }
+    }
+    __syncthreads();
+    for (int n = tid; n <= N; n += kFieldBlock)
+      for (int s = 0; s < ns; ++s) {
+        double* md = R->momd + (size_t)s * 2 * (N + 1);
+        md[n] = 0.0;
+        md[N + 1 + n] = 0.0;
+      }
+  }
+
+  // charge per node control volume from the fixed-point deposit; clear it
+  for (int n = tid; n <= N; n += kFieldBlock) {
+    double q = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      unsigned long long* S = R->S + (size_t)s * (N + 1);
+      const double cw = R->sp[s].q * R->sp[s].w * 2.3283064365386963e-10;
+      q += cw * (double)S[n];
+      S[n] = 0ull;
+    }
+    Q[n] = q;
+  }
+  __syncthreads();
+  double phi0 = 0.0;
+  if (periodic) {
+    if (tid == 0) Q[0] += Q[N];
+    __syncthreads();
+    double loc = 0.0;
+    for (int n = tid; n < N; n += kFieldBlock) loc += Q[n];
+    const double tot = block_sum(loc, dsm);
+    for (int n = tid; n < N; n += kFieldBlock) Q[n] -= V[n] * tot / R->L;
+    __syncthreads();
+  } else {
+    const double t = (double)kn * R->dt;
+    const double arg = __dadd_rn(__dmul_rn(__dmul_rn(kTwoPi, R->freq), t), R->phase);
+    phi0 = R->vdc + R->v0 * sin(arg);
+  }
+  // C_n = sum_{m=1..n} Q_m for n = 0..N-1 (C_0 = 0)
+  if (tid == 0) Q[0] = 0.0;
+  __syncthreads();
+  block_incl_scan_array(Q, N, dsm);
+  double loc = 0.0;
+  for (int n = tid; n < N; n += kFieldBlock) loc += dx[n] * Q[n];
+  const double A = block_sum(loc, dsm);
+  const double g0 = (0.0 - phi0 + A / kEps0) / R->L;
+  double fe = 0.0;
+  for (int n = tid; n < N; n += kFieldBlock) {
+    const double gn = g0 - Q[n] / kEps0;
+    g[n] = gn;
+    fe += 0.5 * kEps0 * gn * gn * dx[n];
+  }
+  __syncthreads();
+  float* E = R->E;
+  if (R->scheme == ECPIC_SCHEME_EC) {
+    for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-g[n]);
+  } else {
+    for (int n = tid; n <= N; n += kFieldBlock) {
+      double e;
+      if (n > 0 && n < N) {
+        e = -(g[n] * dx[n] + g[n - 1] * dx[n - 1]) / (dx[n] + dx[n - 1]);
+      } else if (periodic) {
+        e = -(g[0] * dx[0] + g[N - 1] * dx[N - 1]) / (dx[0] + dx[N - 1]);
+      } else {
+        e = (n == 0) ? -g[0] : -g[N - 1];
+      }
+      E[n] = (float)e;
+    }
+  }
+  const double fe_tot = block_sum(fe, dsm);
+  // potential: phi_n = phi_0 + sum_{m<n} g_m dx_m
+  for (int n = tid; n < N; n += kFieldBlock) g[n] *= dx[n];
+  __syncthreads();
+  block_incl_scan_array(g, N, dsm);
+  double* phi = R->phi;
+  for (int n = tid; n <= N; n += kFieldBlock) {
+    double p;
+    if (n == 0) p = phi0;
+    else if (n == N) p = 0.0;
+    else p = phi0 + g[n - 1];
+    phi[n] = p;
+    if (sample) R->acc[(size_t)(5 * ns) * (N + 1) + n] += p;
+  }
+  if (tid == 0) {
+    if (sample) {
+      st->fe = st->fe_field;
+      for (int s = 0; s < ns; ++s) {
+        st->ke[s] = st->ke_acc[s];
+        st->ke_acc[s] = 0.0;
+      }
+      st->n_samples += 1;
+    }
+    st->fe_field = fe_tot;
+    if (advance) {
+      st->step = kn;
+      for (int s = 0; s < ns; ++s) {
+        SegState* ss = b.sst + R->seg0 + s;
+        const long long cap = b.segs[R->seg0 + s].cap;
+        const long long n = ss->n_alloc < cap ? ss->n_alloc : cap;
+        ss->n_proc = n;
+        ss->n_alloc = n;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- sort
+__global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* pre = reinterpret_cast<long long*>(smem_raw);
+  int* H = reinterpret_cast<int*>(pre + b.nseg + 1);
+  __shared__ long long wsm[32];
+  __shared__ int lohi[2];
+  for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) H[i] = 0;
+  if (threadIdx.x == 0) {
+    lohi[0] = INT_MAX;
+    lohi[1] = -1;
+  }
+  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm);
+  if (T == 0) return;
+  const long long lo = T * (long long)blockIdx.x / gridDim.x;
+  const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  const int lane = threadIdx.x & 31;
+  for (int s = seg_find(pre, b.nseg, lo); s < b.nseg && pre[s] < hi; ++s) {
+    const long long beg = max(lo, pre[s]) - pre[s];
+    const long long end = min(hi, pre[s + 1]) - pre[s];
+    if (beg >= end) continue;
+    const SegDev& G = b.segs[s];
+    const int32_t* pc = G.cell[b.sst[s].cur];
+    const int Nr = b.runs[G.run].N;
+    int my_lo = INT_MAX, my_hi = -1;
+    for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
+      const long long i = base + lane;
+      int c = i < end ? pc[i] : -1;
+      if (c >= Nr) c = -1;
+      const unsigned grp = __match_any_sync(kFull, c >= 0 ? (unsigned)c : 0xFFFFFFFFu);
+      if (c >= 0) {
+        if (lane == __ffs(grp) - 1) atomicAdd(H + c, __popc(grp));
+        my_lo = min(my_lo, c);
+        my_hi = max(my_hi, c);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      my_lo = min(my_lo, __shfl_xor_sync(kFull, my_lo, o));
+      my_hi = max(my_hi, __shfl_xor_sync(kFull, my_hi, o));
+    }
+    if (lane == 0 && my_hi >= 0) {
+      atomicMin(&lohi[0], my_lo);
+      atomicMax(&lohi[1], my_hi);
+    }
+    __syncthreads();
+    const int flo = lohi[0], fhi = lohi[1];
+    for (int n = flo + (int)threadIdx.x; n <= fhi; n += kPassBlock) {
+      const int v = H[n];
+      if (v) {
+        atomicAdd(b.hist + G.hoff + n, v);
+        H[n] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      lohi[0] = INT_MAX;
+      lohi[1] = -1;
+    }
+    __syncthreads();
+  }
+}
+
+// per segment: counts -> exclusive cursors; live total
+__global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b) {
+  const int s = blockIdx.x;
+  if (s >= b.nseg) return;
+  const SegDev& G = b.segs[s];
+  const int slot = G.run;
+  if (!run_live(b.runs[slot], b.rst[slot], MODE_SORT, -1, slot)) return;
+  __shared__ long long wsm[32];
+  const int N = b.runs[slot].N;
+  int* h = b.hist + G.hoff;
+  const int per = (N + kPassBlock - 1) / kPassBlock;
+  const int beg = min(N, (int)threadIdx.x * per), end = min(N, beg + per);
+  long long loc = 0;
+  for (int i = beg; i < end; ++i) loc += h[i];
+  long long total;
+  long long run = block_excl_scan(loc, wsm, &total);
+  for (int i = beg; i < end; ++i) {
+    const int c = h[i];
+    h[i] = (int)run;
+    run += c;
+  }
+  if (threadIdx.x == 0) b.sst[s].n_live = total;
+}
+
+__global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* pre = reinterpret_cast<long long*>(smem_raw);
+  __shared__ long long wsm[32];
+  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm);
+  if (T == 0) return;
+  const long long lo = T * (long long)blockIdx.x / gridDim.x;
+  const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int s = seg_find(pre, b.nseg, lo); s < b.nseg && pre[s] < hi; ++s) {
+    const long long beg = max(lo, pre[s]) - pre[s];
+    const long long end = min(hi, pre[s + 1]) - pre[s];
+    if (beg >= end) continue;
+    const SegDev& G = b.segs[s];
+    const int src = b.sst[s].cur, dst = src ^ 1;
+    int* cursor = b.hist + G.hoff;
+    const int Nr = b.runs[G.run].N;
+    for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
+      const long long i = base + lane;
+      int c = i < end ? G.cell[src][i] : -1;
+      if (c >= Nr) c = -1;
+      const unsigned grp = __match_any_sync(kFull, c >= 0 ? (unsigned)c : 0xFFFFFFFFu);
+      if (c >= 0) {
+        const int leader = __ffs(grp) - 1;
+        int basepos = 0;
+        if (lane == leader) basepos = atomicAdd(cursor + c, __popc(grp));
+        basepos = __shfl_sync(grp, basepos, leader);
+        const long long j = (long long)basepos + __popc(grp & lt);
+        G.cell[dst][j] = c;
+        G.xi[dst][j] = G.xi[src][i];
+        G.vx[dst][j] = G.vx[src][i];
+        G.vy[dst][j] = G.vy[src][i];
+        G.vz[dst][j] = G.vz[src][i];
+        G.id[dst][j] = G.id[src][i];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPassBlock) k_finalize(BatchView b) {
+  const int s = blockIdx.x;
+  if (s >= b.nseg) return;
+  const SegDev& G = b.segs[s];
+  const int slot = G.run;
+  if (!run_live(b.runs[slot], b.rst[slot], MODE_SORT, -1, slot)) return;
+  const int N = b.runs[slot].N;
+  for (int i = threadIdx.x; i < N; i += kPassBlock) b.hist[G.hoff + i] = 0;
+  if (threadIdx.x == 0) {
+    SegState* ss = b.sst + s;
+    ss->cur ^= 1;
+    ss->n_proc = ss->n_live;
+    ss->n_alloc = ss->n_live;
+    ss->n_dead = 0;
+  }
+}
+
+// ----------------------------------------------------------------- loader
+// Uniform positions and Maxwellian velocities (Sec. 2b) from Philox blocks
+// (id = i, step word 0xFFFFFFFF, word3 = (s<<8)|0x80 for X, |0x81 for v),
+// in FP64 so that the cell index matches the FP64 definition exactly.
+__global__ void k_init(BatchView b, int slot, InitParams p) {
+  const RunDev* R = b.runs + slot;
+  const int sp = blockIdx.y;
+  if (sp >= R->ns) return;
+  const int s = R->seg0 + sp;
+  const SegDev& G = b.segs[s];
+  const int cur = b.sst[s].cur;
+  const int N = R->N;
+  const double L = R->L;
+  const double* x = R->x;
+  const double* dx = R->dx;
+  const double sd = p.sd[sp];
+  const long long n = p.n[sp];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4 A = draw(R->seed, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)sp << 8) | 0x80u);
+    const uint4 B = draw(R->seed, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)sp << 8) | 0x81u);
+    const double u = (double)A.x * 2.3283064365386963e-10;
+    const double X = __dmul_rn(u, L);
+    int lo = 0, hi = N;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (x[mid] <= X) lo = mid; else hi = mid;
+    }
+    int c = lo;
+    float f = __double2float_rn(__ddiv_rn(__dsub_rn(X, x[c]), dx[c]));
+    if (f >= 1.0f) {
+      if (c + 1 < N) {
+        c += 1;
+        f = 0.0f;
+      } else {
+        f = 0.99999994f;
+      }
+    }
+    const double u1a = __dmul_rn((double)B.x + 1.0, 2.3283064365386963e-10);
+    const double u2a = __dmul_rn((double)B.y, 2.3283064365386963e-10);
+    const double u1b = __dmul_rn((double)B.z + 1.0, 2.3283064365386963e-10);
+    const double u2b = __dmul_rn((double)B.w, 2.3283064365386963e-10);
+    const double ra = sqrt(__dmul_rn(-2.0, log(u1a)));
+    const double rb = sqrt(__dmul_rn(-2.0, log(u1b)));
+    const double aa = __dmul_rn(kTwoPi, u2a), ab = __dmul_rn(kTwoPi, u2b);
+    const double z0 = __dmul_rn(ra, cos(aa)), z1 = __dmul_rn(ra, sin(aa));
+    const double z2 = __dmul_rn(rb, cos(ab));
+    G.cell[cur][i] = c;
+    G.xi[cur][i] = f;
+    G.vx[cur][i] = __double2float_rn(__dmul_rn(sd, z0));
+    G.vy[cur][i] = __double2float_rn(__dmul_rn(sd, z1));
+    G.vz[cur][i] = __double2float_rn(__dmul_rn(sd, z2));
+    G.id[cur][i] = (uint64_t)i;
+  }
+}
+
+// ----------------------------------------------------------------- test kernels
+__global__ void __launch_bounds__(kPassBlock) k_deposit_device(int N, long long n, const int* cell,
+                                                               const float* xi,
+                                                               unsigned long long* S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(smem_raw);
+  for (int i = threadIdx.x; i <= N; i += kPassBlock) Ssm[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * kPassBlock + (threadIdx.x & ~31); base < n;
+       base += (long long)gridDim.x * kPassBlock) {
+    const long long i = base + lane;
+    int c = i < n ? cell[i] : -1;
+    const bool valid = c >= 0 && c < N;
+    const float f = valid ? xi[i] : 0.0f;
+    deposit_warp(Ssm, valid, c, f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= N; i += kPassBlock) {
+    const unsigned long long v = Ssm[i];
+    if (v) atomicAdd(S + i, v);
+  }
+}
+
+__global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t* key,
+                                uint32_t* out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, make_uint2(key[2 * i], key[2 * i + 1]));
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+size_t pass_smem_bytes(const BatchView& b) {
+  return sizeof(long long) * (size_t)(b.nseg + 1) +
+         sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1);
+}
+
+size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }
+
+static void set_smem_attr(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int pass_max_ctas_per_sm(const BatchView& b) {
+  const size_t sm = pass_smem_bytes(b);
+  set_smem_attr((const void*)k_pass, sm);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass, kPassBlock, sm);
+  return n > 0 ? n : 1;
+}
+
+void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s) {
+  const size_t sm = pass_smem_bytes(b);
+  set_smem_attr((const void*)k_pass, sm);
+  k_pass<<<grid, kPassBlock, sm, s>>>(b, mode, only);
+}
+
+void launch_field(const BatchView& b, int advance, int only, cudaStream_t s) {
+  const size_t sm = field_smem_bytes(b);
+  set_smem_attr((const void*)k_field, sm);
+  k_field<<<b.max_slots, kFieldBlock, sm, s>>>(b, advance, only);
+}
+
+void launch_sort(const BatchView& b, int grid, cudaStream_t s) {
+  const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
+  set_smem_attr((const void*)k_hist, smh);
+  k_hist<<<grid, kPassBlock, smh, s>>>(b);
+  k_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
+  const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
+  k_scatter<<<grid, kPassBlock, sms, s>>>(b);
+  k_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
+}
+
+void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s) {
+  long long nmax = 0;
+  for (int i = 0; i < kMaxSpecies; ++i) nmax = p.n[i] > nmax ? p.n[i] : nmax;
+  long long blocks = (nmax + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  k_init<<<dim3((unsigned)blocks, kMaxSpecies), 256, 0, s>>>(b, slot, p);
+}
+
+void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
+                           unsigned long long* S, cudaStream_t s) {
+  long long blocks = (n + kPassBlock * 8 - 1) / (kPassBlock * 8);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  const size_t sm = sizeof(unsigned long long) * (size_t)(N + 1);
+  set_smem_attr((const void*)k_deposit_device, sm);
+  k_deposit_device<<<(unsigned)blocks, kPassBlock, sm, s>>>(N, n, cell, xi, S);
+}
+
+void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  k_philox_device<<<(unsigned)blocks, 256, 0, s>>>(n, ctr, key, out);
+}
+
+}  // namespace ecpic

@@ -1,0 +1,42 @@
+// kernels.h -- host-side launch wrappers of the libecpic kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ecpic_dev.cuh"
+
+namespace ecpic {
+
+constexpr int kPassBlock = 256;
+constexpr int kFieldBlock = 256;
+
+struct BatchView {
+  const RunDev* runs;   // device, max_slots
+  RunState* rst;        // device, max_slots
+  const SegDev* segs;   // device, nseg
+  SegState* sst;        // device, nseg
+  int* hist;            // device, sum of N over segments
+  int max_slots;
+  int nseg;
+  int nmax;             // largest N in the batch
+};
+
+struct InitParams {
+  long long n[kMaxSpecies];
+  double sd[kMaxSpecies];  // sqrt(e T / m)
+};
+
+size_t pass_smem_bytes(const BatchView& b);
+size_t field_smem_bytes(const BatchView& b);
+int pass_max_ctas_per_sm(const BatchView& b);
+
+void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s);
+void launch_field(const BatchView& b, int advance, int only, cudaStream_t s);
+void launch_sort(const BatchView& b, int grid, cudaStream_t s);
+void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s);
+
+void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
+                           unsigned long long* S, cudaStream_t s);
+void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          cudaStream_t s);
+
+}  // namespace ecpic

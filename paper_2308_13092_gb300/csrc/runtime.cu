@@ -1,0 +1,723 @@
+// runtime.cu -- host runtime of libecpic (device memory, uploads, graphs).
+#include "runtime.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace ecpic {
+
+namespace {
+constexpr double kQe = 1.602176634e-19;
+constexpr double kKb = 1.380649e-23;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off += align_up(sizeof(T) * (count ? count : 1));
+    return p;
+  }
+};
+
+size_t layout_bytes(const RunSpec& s) {
+  const size_t N = s.edges.size() - 1, ns = s.species.size();
+  size_t b = 0;
+  auto add = [&](size_t bytes) { b += align_up(bytes ? bytes : 1); };
+  add(8 * (N + 1));       // x
+  add(8 * N);             // dx
+  add(8 * (N + 1));       // V
+  add(4 * N);             // dtdx
+  add(4 * N);             // rp
+  add(4 * N);             // rm
+  add(4 * (N + 1));       // E
+  add(8 * (N + 1));       // phi
+  add(8 * ns * (N + 1));  // S
+  add(8 * ns * 2 * (N + 1));  // momd
+  add(8 * (size_t)acc_size((int)ns) * (N + 1));
+  for (const auto& sp : s.species)
+    for (const auto& p : sp.procs) add(4 * p.sigma.size());
+  for (const auto& sp : s.species)
+    for (int buf = 0; buf < 2; ++buf) {
+      const size_t c = (size_t)sp.cap;
+      add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(8 * c);
+    }
+  return b;
+}
+}  // namespace
+
+std::string validate_grid(const std::vector<double>& e, int bc) {
+  if (e.size() < 3) return "need at least 2 cells";
+  if (e.size() - 1 > (size_t)kMaxCells) return "too many cells (max ECPIC_MAX_CELLS)";
+  if (e[0] != 0.0) return "edges[0] must be 0";
+  for (size_t i = 1; i < e.size(); ++i)
+    if (!(e[i] > e[i - 1]) || !std::isfinite(e[i])) return "edges must be finite and strictly increasing";
+  if (bc != ECPIC_DIRICHLET_RF && bc != ECPIC_PERIODIC) return "unknown boundary condition";
+  return "";
+}
+
+std::string validate_spec(const RunSpec& s) {
+  std::string e = validate_grid(s.edges, s.bc);
+  if (!e.empty()) return e;
+  if (s.scheme != ECPIC_SCHEME_EC && s.scheme != ECPIC_SCHEME_MC) return "unknown scheme";
+  if (s.species.empty() || s.species.size() > (size_t)kMaxSpecies) return "1..4 species required";
+  if (!(s.dt > 0) || !std::isfinite(s.dt)) return "dt must be positive";
+  if (s.n_init.size() != s.species.size() || s.T_eV.size() != s.species.size())
+    return "n_per_species/T_eV size mismatch";
+  for (size_t i = 0; i < s.species.size(); ++i) {
+    const auto& sp = s.species[i];
+    if (!(sp.m > 0) || !(sp.w >= 0) || sp.cap < 1 || sp.cap > (long long)INT32_MAX)
+      return "bad species parameters";
+    if (s.n_init[i] < 0 || s.n_init[i] > sp.cap) return "initial particles exceed capacity";
+    if (!(s.T_eV[i] >= 0)) return "negative temperature";
+    if (sp.procs.size() > (size_t)kMaxProc) return "too many processes";
+    for (const auto& p : sp.procs) {
+      if (p.kind < ECPIC_ELASTIC || p.kind > ECPIC_CX) return "unknown process kind";
+      if (p.sigma.size() < 2 || !(p.dE > 0) || !(p.thr >= 0)) return "bad cross-section table";
+      if (p.dE != sp.procs[0].dE || p.sigma.size() != sp.procs[0].sigma.size())
+        return "processes of one species must share the energy grid";
+      const bool heavy = p.kind == ECPIC_ION_ELASTIC || p.kind == ECPIC_CX;
+      const bool heavy0 = sp.procs[0].kind == ECPIC_ION_ELASTIC || sp.procs[0].kind == ECPIC_CX;
+      if (heavy != heavy0) return "electron and ion processes mixed in one species";
+      if (p.kind == ECPIC_IONIZATION &&
+          (p.product < 0 || p.product >= (int)s.species.size() || p.product == (int)i))
+        return "ionisation needs a product ion species";
+      for (float v : p.sigma)
+        if (!(v >= 0.0f) || !std::isfinite(v)) return "cross sections must be finite and >= 0";
+    }
+    if (!sp.procs.empty() && !(s.gas && s.mg > 0)) return "collisions need a gas";
+  }
+  return "";
+}
+
+void null_rate(const HostSpecies& sp, const RunSpec& s, double* nu_max, uint32_t* thr24) {
+  *nu_max = 0.0;
+  *thr24 = 0;
+  if (sp.procs.empty() || !s.gas || !(s.ng > 0)) return;
+  // per table segment: n_g * max(sigma_tot at both ends) * speed at the upper end
+  const size_t n = sp.procs[0].sigma.size();
+  const double dE = sp.procs[0].dE;
+  double best = 0.0;
+  for (size_t i = 0; i + 1 < n; ++i) {
+    double a = 0.0, b = 0.0;
+    for (const auto& p : sp.procs) {
+      a += (double)p.sigma[i];
+      b += (double)p.sigma[i + 1];
+    }
+    const double sig = a > b ? a : b;
+    const double v = std::sqrt(2.0 * (double)(i + 1) * dE * kQe / sp.m);
+    if (sig * v > best) best = sig * v;
+  }
+  *nu_max = s.ng * best;
+  const double P = 1.0 - std::exp(-(*nu_max) * s.dt);
+  double t = std::ceil(P * 16777216.0);
+  if (t > 16777216.0) t = 16777216.0;
+  *thr24 = (uint32_t)t;
+}
+
+size_t run_bytes(const RunSpec& s) { return layout_bytes(s); }
+
+// ------------------------------------------------------------------ Batch
+Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
+    : device_(device), stream_(stream), max_slots_(max_slots), spc_(spc), nmax_(nmax) {
+  nseg_ = max_slots_ * spc_;
+  cudaSetDevice(device_);
+  if (!stream_) {
+    cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
+    own_stream_ = true;
+  }
+  cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, device_);
+  cudaMalloc(&d_runs_, sizeof(RunDev) * max_slots_);
+  cudaMalloc(&d_rst_, sizeof(RunState) * max_slots_);
+  cudaMalloc(&d_segs_, sizeof(SegDev) * nseg_);
+  cudaMalloc(&d_sst_, sizeof(SegState) * nseg_);
+  cudaMalloc(&d_hist_, sizeof(int) * (size_t)nseg_ * nmax_);
+  h_runs_.assign(max_slots_, RunDev{});
+  h_segs_.assign(nseg_, SegDev{});
+  for (int s = 0; s < nseg_; ++s) {
+    h_segs_[s].run = s / spc_;
+    h_segs_[s].species = s % spc_;
+    h_segs_[s].hoff = s * nmax_;
+  }
+  cudaMemsetAsync(d_runs_, 0, sizeof(RunDev) * max_slots_, stream_);
+  cudaMemsetAsync(d_rst_, 0, sizeof(RunState) * max_slots_, stream_);
+  cudaMemsetAsync(d_sst_, 0, sizeof(SegState) * nseg_, stream_);
+  cudaMemsetAsync(d_hist_, 0, sizeof(int) * (size_t)nseg_ * nmax_, stream_);
+  cudaMemcpyAsync(d_segs_, h_segs_.data(), sizeof(SegDev) * nseg_, cudaMemcpyHostToDevice, stream_);
+  slot_mem_.assign(max_slots_, nullptr);
+  slot_bytes_.assign(max_slots_, 0);
+  active_.assign(max_slots_, 0);
+  specs_.assign(max_slots_, RunSpec{});
+  cudaStreamSynchronize(stream_);
+}
+
+Batch::~Batch() {
+  cudaSetDevice(device_);
+  cudaStreamSynchronize(stream_);
+  invalidate_graphs();
+  for (int s = 0; s < max_slots_; ++s)
+    if (slot_mem_[s]) cudaFree(slot_mem_[s]);
+  cudaFree(d_runs_);
+  cudaFree(d_rst_);
+  cudaFree(d_segs_);
+  cudaFree(d_sst_);
+  cudaFree(d_hist_);
+  if (own_stream_) cudaStreamDestroy(stream_);
+}
+
+int Batch::check(cudaError_t e, const char* what, std::string* err) {
+  if (e == cudaSuccess) return ECPIC_OK;
+  if (err) *err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? ECPIC_ERR_NOMEM : ECPIC_ERR_CUDA;
+}
+
+BatchView Batch::view() const {
+  BatchView v;
+  v.runs = d_runs_;
+  v.rst = d_rst_;
+  v.segs = d_segs_;
+  v.sst = d_sst_;
+  v.hist = d_hist_;
+  v.max_slots = max_slots_;
+  v.nseg = nseg_;
+  v.nmax = nmax_;
+  return v;
+}
+
+void Batch::upload_run(int slot) {
+  cudaMemcpyAsync(d_runs_ + slot, &h_runs_[slot], sizeof(RunDev), cudaMemcpyHostToDevice, stream_);
+}
+
+int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
+  if (slot < 0 || slot >= max_slots_ || active_[slot]) {
+    if (err) *err = "slot unavailable";
+    return ECPIC_ERR_STATE;
+  }
+  const std::string v = validate_spec(spec);
+  if (!v.empty()) {
+    if (err) *err = v;
+    return ECPIC_ERR_ARG;
+  }
+  const int N = (int)spec.edges.size() - 1, ns = (int)spec.species.size();
+  if (N > nmax_ || ns > spc_) {
+    if (err) *err = "run exceeds the batch's cell or species limits";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  const size_t bytes = layout_bytes(spec);
+  void* mem = nullptr;
+  int rc = check(cudaMallocAsync(&mem, bytes, stream_), "device allocation", err);
+  if (rc) return rc;
+  Carve cv{static_cast<char*>(mem)};
+  RunDev R{};
+  R.active = 1;
+  R.N = N;
+  R.bc = spec.bc;
+  R.scheme = spec.scheme;
+  R.ns = ns;
+  R.seg0 = slot * spc_;
+  R.sample_every = spec.sample_every;
+  R.L = spec.edges[N];
+  R.dt = spec.dt;
+  R.v0 = spec.v0;
+  R.freq = spec.freq;
+  R.phase = spec.phase;
+  R.vdc = spec.vdc;
+  R.seed = spec.seed;
+  R.ng = (float)(spec.gas ? spec.ng : 0.0);
+  R.vth_gas = (float)(spec.gas && spec.mg > 0 ? std::sqrt(kKb * spec.Tg / spec.mg) : 0.0);
+  // grid arrays
+  std::vector<double> dx(N), V(N + 1);
+  std::vector<float> dtdx(N), rp(N), rm(N);
+  for (int j = 0; j < N; ++j) dx[j] = spec.edges[j + 1] - spec.edges[j];
+  for (int n = 1; n < N; ++n) V[n] = 0.5 * (dx[n - 1] + dx[n]);
+  if (spec.bc == ECPIC_PERIODIC) {
+    V[0] = V[N] = 0.5 * (dx[N - 1] + dx[0]);
+  } else {
+    V[0] = 0.5 * dx[0];
+    V[N] = 0.5 * dx[N - 1];
+  }
+  const double dxu = R.L / N;
+  bool uniform = true;
+  for (int j = 0; j < N; ++j) {
+    if (std::fabs(dx[j] - dxu) > 1e-12 * dxu) uniform = false;
+    dtdx[j] = (float)(spec.dt / dx[j]);
+    const int jp = (j + 1 < N) ? j + 1 : (spec.bc == ECPIC_PERIODIC ? 0 : j);
+    const int jm = (j > 0) ? j - 1 : (spec.bc == ECPIC_PERIODIC ? N - 1 : j);
+    rp[j] = (float)(dx[j] / dx[jp]);
+    rm[j] = (float)(dx[j] / dx[jm]);
+  }
+  R.uniform = uniform ? 1 : 0;
+  R.dtdx_u = (float)(spec.dt / dxu);
+  double* d_x = cv.take<double>(N + 1);
+  double* d_dx = cv.take<double>(N);
+  double* d_V = cv.take<double>(N + 1);
+  float* d_dtdx = cv.take<float>(N);
+  float* d_rp = cv.take<float>(N);
+  float* d_rm = cv.take<float>(N);
+  R.E = cv.take<float>(N + 1);
+  R.phi = cv.take<double>(N + 1);
+  R.S = cv.take<unsigned long long>((size_t)ns * (N + 1));
+  R.momd = cv.take<double>((size_t)ns * 2 * (N + 1));
+  R.acc = cv.take<double>((size_t)acc_size(ns) * (N + 1));
+  R.mom = nullptr;
+  R.x = d_x;
+  R.dx = d_dx;
+  R.V = d_V;
+  R.dtdx = d_dtdx;
+  R.rp = d_rp;
+  R.rm = d_rm;
+  cudaMemcpyAsync(d_x, spec.edges.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_dx, dx.data(), 8 * N, cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_V, V.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_dtdx, dtdx.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_rp, rp.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_rm, rm.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
+  cudaMemsetAsync(R.E, 0, 4 * (N + 1), stream_);
+  cudaMemsetAsync(R.phi, 0, 8 * (N + 1), stream_);
+  cudaMemsetAsync(R.S, 0, 8 * (size_t)ns * (N + 1), stream_);
+  cudaMemsetAsync(R.momd, 0, 8 * (size_t)ns * 2 * (N + 1), stream_);
+  cudaMemsetAsync(R.acc, 0, 8 * (size_t)acc_size(ns) * (N + 1), stream_);
+  // species
+  for (int s = 0; s < ns; ++s) {
+    const HostSpecies& hs = spec.species[s];
+    SpeciesDev& D = R.sp[s];
+    D.q = hs.q;
+    D.m = hs.m;
+    D.w = hs.w;
+    D.qm_dt = (float)(hs.q / hs.m * spec.dt);
+    D.half_m_over_e = (float)(0.5 * hs.m / kQe);
+    D.two_e_over_m = (float)(2.0 * kQe / hs.m);
+    const double mg = spec.gas && spec.mg > 0 ? spec.mg : 1.0;
+    D.two_m_over_M = (float)(2.0 * hs.m / mg);
+    D.m_frac = (float)(mg / (hs.m + mg));
+    D.mass_frac = (float)(hs.m / (hs.m + mg));
+    double nu;
+    uint32_t thr;
+    null_rate(hs, spec, &nu, &thr);
+    D.nu_max = (float)nu;
+    D.thr24 = thr;
+    D.nproc = (int)hs.procs.size();
+    D.heavy = 0;
+    D.ntab = hs.procs.empty() ? 2 : (int)hs.procs[0].sigma.size();
+    D.dE_inv = hs.procs.empty() ? 1.0f : (float)(1.0 / hs.procs[0].dE);
+    for (int p = 0; p < D.nproc; ++p) {
+      const HostProc& hp = hs.procs[p];
+      ProcDev& P = D.proc[p];
+      P.kind = hp.kind;
+      P.thr = (float)hp.thr;
+      float* tab = cv.take<float>(hp.sigma.size());
+      cudaMemcpyAsync(tab, hp.sigma.data(), 4 * hp.sigma.size(), cudaMemcpyHostToDevice, stream_);
+      P.sigma = tab;
+      P.product_species = hp.kind == ECPIC_IONIZATION ? hp.product : -1;
+      P.product_seg = hp.kind == ECPIC_IONIZATION ? R.seg0 + hp.product : -1;
+      if (hp.kind == ECPIC_ION_ELASTIC || hp.kind == ECPIC_CX) D.heavy = 1;
+    }
+  }
+  // particle segments
+  std::vector<SegState> sst(spc_);
+  for (int s = 0; s < spc_; ++s) {
+    SegDev& G = h_segs_[R.seg0 + s];
+    std::memset(sst.data() + s, 0, sizeof(SegState));
+    if (s < ns) {
+      const size_t c = (size_t)spec.species[s].cap;
+      for (int buf = 0; buf < 2; ++buf) {
+        G.cell[buf] = cv.take<int32_t>(c);
+        G.xi[buf] = cv.take<float>(c);
+        G.vx[buf] = cv.take<float>(c);
+        G.vy[buf] = cv.take<float>(c);
+        G.vz[buf] = cv.take<float>(c);
+        G.id[buf] = cv.take<uint64_t>(c);
+      }
+      G.cap = (long long)c;
+      sst[s].n_proc = sst[s].n_alloc = spec.n_init[s];
+    } else {
+      std::memset(G.cell, 0, sizeof(G.cell));
+      G.cap = 0;
+    }
+  }
+  cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
+                  stream_);
+  cudaMemcpyAsync(d_sst_ + R.seg0, sst.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
+                  stream_);
+  RunState st{};
+  st.step = 0;
+  st.step_end = spec.step_end;
+  cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
+  h_runs_[slot] = R;
+  upload_run(slot);
+  slot_mem_[slot] = mem;
+  slot_bytes_[slot] = bytes;
+  bytes_in_use_ += bytes;
+  active_[slot] = 1;
+  specs_[slot] = spec;
+  // particles and the field of step 0
+  InitParams ip{};
+  for (int s = 0; s < ns; ++s) {
+    ip.n[s] = spec.n_init[s];
+    ip.sd[s] = std::sqrt(kQe * spec.T_eV[s] / spec.species[s].m);
+  }
+  launch_init(view(), slot, ip, stream_);
+  refresh(slot);
+  return check(cudaGetLastError(), "admit", err);
+}
+
+void Batch::refresh(int slot) {
+  const BatchView b = view();
+  launch_pass(b, std::max(1, std::min(choose_grid(), sm_count_ * 2)), MODE_REFRESH, slot, stream_);
+  launch_field(b, 0, slot, stream_);
+}
+
+void Batch::release(int slot) {
+  if (!slot_active(slot)) return;
+  cudaSetDevice(device_);
+  h_runs_[slot].active = 0;
+  upload_run(slot);
+  std::vector<SegState> z(spc_);
+  std::memset(z.data(), 0, sizeof(SegState) * spc_);
+  cudaMemcpyAsync(d_sst_ + slot * spc_, z.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
+                  stream_);
+  cudaFreeAsync(slot_mem_[slot], stream_);
+  slot_mem_[slot] = nullptr;
+  bytes_in_use_ -= slot_bytes_[slot];
+  slot_bytes_[slot] = 0;
+  active_[slot] = 0;
+  cudaStreamSynchronize(stream_);
+}
+
+long long Batch::live_estimate() const {
+  long long t = 0;
+  for (int s = 0; s < max_slots_; ++s)
+    if (active_[s])
+      for (long long n : specs_[s].n_init) t += n;
+  return t;
+}
+
+int Batch::choose_grid() const {
+  if (pass_grid_override_ > 0) return pass_grid_override_;
+  const int occ = pass_max_ctas_per_sm(view());
+  const long long cap = (long long)occ * sm_count_;
+  long long want = (live_estimate() * 5 / 4 + kPassBlock * 2 - 1) / (kPassBlock * 2);
+  if (max_slots_ > 1) want = cap;  // a batch's population changes: fill the GPU
+  if (want < 1) want = 1;
+  return (int)std::min(cap, want);
+}
+
+void Batch::invalidate_graphs() {
+  if (graph_k_) cudaGraphExecDestroy(graph_k_);
+  if (graph_1_) cudaGraphExecDestroy(graph_1_);
+  graph_k_ = graph_1_ = nullptr;
+}
+
+int Batch::ensure_graphs(std::string* err) {
+  if (!use_graphs_) return ECPIC_OK;
+  const int g = choose_grid();
+  if (graph_k_ && graph_1_ && g == pass_grid_) return ECPIC_OK;
+  invalidate_graphs();
+  pass_grid_ = g;
+  const BatchView b = view();
+  for (int which = 0; which < 2; ++which) {
+    cudaGraph_t graph = nullptr;
+    int rc = check(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "capture", err);
+    if (rc) return rc;
+    const int steps = which == 0 ? sort_every_ : 1;
+    for (int t = 0; t < steps; ++t) {
+      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_field(b, 1, -1, stream_);
+    }
+    if (which == 0) launch_sort(b, pass_grid_, stream_);
+    rc = check(cudaStreamEndCapture(stream_, &graph), "capture end", err);
+    if (rc) return rc;
+    cudaGraphExec_t exec = nullptr;
+    rc = check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate", err);
+    cudaGraphDestroy(graph);
+    if (rc) return rc;
+    (which == 0 ? graph_k_ : graph_1_) = exec;
+  }
+  return ECPIC_OK;
+}
+
+int Batch::step(long long n, std::string* err) {
+  if (n < 0) {
+    if (err) *err = "negative step count";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = ensure_graphs(err);
+  if (rc) return rc;
+  const BatchView b = view();
+  if (!use_graphs_) pass_grid_ = choose_grid();
+  while (n > 0) {
+    if (use_graphs_ && since_sort_ == 0 && n >= sort_every_) {
+      rc = check(cudaGraphLaunch(graph_k_, stream_), "graph launch", err);
+      if (rc) return rc;
+      n -= sort_every_;
+      continue;
+    }
+    if (use_graphs_) {
+      rc = check(cudaGraphLaunch(graph_1_, stream_), "graph launch", err);
+      if (rc) return rc;
+    } else {
+      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_field(b, 1, -1, stream_);
+    }
+    --n;
+    if (++since_sort_ >= sort_every_) {
+      launch_sort(b, pass_grid_, stream_);
+      since_sort_ = 0;
+    }
+  }
+  return check(cudaGetLastError(), "step", err);
+}
+
+int Batch::profile_step(long long n, double* ms, long long* launches, std::string* err) {
+  cudaSetDevice(device_);
+  if (pass_grid_ <= 0) pass_grid_ = choose_grid();
+  const BatchView b = view();
+  cudaEvent_t ev[4];
+  for (auto& e : ev) cudaEventCreate(&e);
+  double acc[3] = {0, 0, 0};
+  long long cnt[3] = {0, 0, 0};
+  int rc = ECPIC_OK;
+  for (long long t = 0; t < n && rc == ECPIC_OK; ++t) {
+    cudaEventRecord(ev[0], stream_);
+    launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+    cudaEventRecord(ev[1], stream_);
+    launch_field(b, 1, -1, stream_);
+    cudaEventRecord(ev[2], stream_);
+    const bool sort = ++since_sort_ >= sort_every_;
+    if (sort) {
+      launch_sort(b, pass_grid_, stream_);
+      since_sort_ = 0;
+    }
+    cudaEventRecord(ev[3], stream_);
+    rc = check(cudaEventSynchronize(ev[3]), "profile step", err);
+    float a = 0, f = 0, c = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&f, ev[1], ev[2]);
+    cudaEventElapsedTime(&c, ev[2], ev[3]);
+    acc[0] += a;
+    acc[1] += f;
+    cnt[0] += 1;
+    cnt[1] += 1;
+    if (sort) {
+      acc[2] += c;
+      cnt[2] += 4;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (int i = 0; i < 3; ++i) {
+    if (ms) ms[i] = acc[i];
+    if (launches) launches[i] = cnt[i];
+  }
+  return rc;
+}
+
+int Batch::sort_now(std::string* err) {
+  cudaSetDevice(device_);
+  const int g = pass_grid_ > 0 ? pass_grid_ : choose_grid();
+  launch_sort(view(), g, stream_);
+  since_sort_ = 0;
+  return check(cudaGetLastError(), "sort", err);
+}
+
+int Batch::set_sort_every(int k) {
+  if (k < 1) return ECPIC_ERR_ARG;
+  sort_every_ = k;
+  since_sort_ = 0;
+  invalidate_graphs();
+  return ECPIC_OK;
+}
+
+int Batch::sync(std::string* err) {
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  std::vector<RunState> st(max_slots_);
+  rc = check(cudaMemcpy(st.data(), d_rst_, sizeof(RunState) * max_slots_, cudaMemcpyDeviceToHost),
+             "status read", err);
+  if (rc) return rc;
+  for (int s = 0; s < max_slots_; ++s)
+    if (active_[s] && st[s].status != 0) {
+      if (err) *err = "device reported status " + std::to_string(st[s].status) + " in slot " +
+                      std::to_string(s);
+      return st[s].status;
+    }
+  return ECPIC_OK;
+}
+
+int Batch::slot_status(int slot) {
+  cudaSetDevice(device_);
+  cudaStreamSynchronize(stream_);
+  RunState st;
+  cudaMemcpy(&st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
+  return st.status;
+}
+
+int Batch::get_particles(int slot, int species, int32_t* cell, float* xi, float* vx, float* vy,
+                         float* vz, uint64_t* id, long long cap, long long* n, std::string* err) {
+  if (!slot_active(slot) || species < 0 || species >= (int)specs_[slot].species.size() || !n) {
+    if (err) *err = "bad slot or species";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  const int seg = slot * spc_ + species;
+  SegState ss;
+  cudaMemcpy(&ss, d_sst_ + seg, sizeof(SegState), cudaMemcpyDeviceToHost);
+  const SegDev& G = h_segs_[seg];
+  const size_t m = (size_t)ss.n_proc;
+  std::vector<int32_t> c(m);
+  std::vector<float> a(m), bx(m), by(m), bz(m);
+  std::vector<uint64_t> ids(m);
+  const int u = ss.cur;
+  cudaMemcpy(c.data(), G.cell[u], 4 * m, cudaMemcpyDeviceToHost);
+  cudaMemcpy(a.data(), G.xi[u], 4 * m, cudaMemcpyDeviceToHost);
+  cudaMemcpy(bx.data(), G.vx[u], 4 * m, cudaMemcpyDeviceToHost);
+  cudaMemcpy(by.data(), G.vy[u], 4 * m, cudaMemcpyDeviceToHost);
+  cudaMemcpy(bz.data(), G.vz[u], 4 * m, cudaMemcpyDeviceToHost);
+  rc = check(cudaMemcpy(ids.data(), G.id[u], 8 * m, cudaMemcpyDeviceToHost), "particle read", err);
+  if (rc) return rc;
+  long long live = 0;
+  for (size_t i = 0; i < m; ++i) live += c[i] >= 0;
+  *n = live;
+  if (live > cap) {
+    if (err) *err = "output capacity too small";
+    return ECPIC_ERR_ARG;
+  }
+  long long k = 0;
+  for (size_t i = 0; i < m; ++i) {
+    if (c[i] < 0) continue;
+    if (cell) cell[k] = c[i];
+    if (xi) xi[k] = a[i];
+    if (vx) vx[k] = bx[i];
+    if (vy) vy[k] = by[i];
+    if (vz) vz[k] = bz[i];
+    if (id) id[k] = ids[i];
+    ++k;
+  }
+  return ECPIC_OK;
+}
+
+int Batch::set_particles(int slot, int species, const int32_t* cell, const float* xi,
+                         const float* vx, const float* vy, const float* vz, const uint64_t* id,
+                         long long n, std::string* err) {
+  if (!slot_active(slot) || species < 0 || species >= (int)specs_[slot].species.size() || n < 0) {
+    if (err) *err = "bad slot or species";
+    return ECPIC_ERR_ARG;
+  }
+  const int seg = slot * spc_ + species;
+  const SegDev& G = h_segs_[seg];
+  const int N = (int)specs_[slot].edges.size() - 1;
+  if (n > G.cap) {
+    if (err) *err = "more particles than the species capacity";
+    return ECPIC_ERR_ARG;
+  }
+  if (n > 0 && (!cell || !xi || !vx || !vy || !vz || !id)) {
+    if (err) *err = "null particle array";
+    return ECPIC_ERR_ARG;
+  }
+  for (long long i = 0; i < n; ++i)
+    if (cell[i] < 0 || cell[i] >= N || !(xi[i] >= 0.0f) || !(xi[i] < 1.0f)) {
+      if (err) *err = "cell or xi out of range at index " + std::to_string(i);
+      return ECPIC_ERR_ARG;
+    }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  SegState ss;
+  cudaMemcpy(&ss, d_sst_ + seg, sizeof(SegState), cudaMemcpyDeviceToHost);
+  const int u = ss.cur;
+  const size_t m = (size_t)n;
+  cudaMemcpy(G.cell[u], cell, 4 * m, cudaMemcpyHostToDevice);
+  cudaMemcpy(G.xi[u], xi, 4 * m, cudaMemcpyHostToDevice);
+  cudaMemcpy(G.vx[u], vx, 4 * m, cudaMemcpyHostToDevice);
+  cudaMemcpy(G.vy[u], vy, 4 * m, cudaMemcpyHostToDevice);
+  cudaMemcpy(G.vz[u], vz, 4 * m, cudaMemcpyHostToDevice);
+  cudaMemcpy(G.id[u], id, 8 * m, cudaMemcpyHostToDevice);
+  ss.n_proc = ss.n_alloc = n;
+  ss.n_dead = 0;
+  cudaMemcpy(d_sst_ + seg, &ss, sizeof(SegState), cudaMemcpyHostToDevice);
+  refresh(slot);
+  return check(cudaGetLastError(), "set_particles", err);
+}
+
+int Batch::get_fields(int slot, double* phi, float* E, std::string* err) {
+  if (!slot_active(slot)) {
+    if (err) *err = "bad slot";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  const RunDev& R = h_runs_[slot];
+  if (phi) cudaMemcpy(phi, R.phi, 8 * (size_t)(R.N + 1), cudaMemcpyDeviceToHost);
+  if (E)
+    cudaMemcpy(E, R.E, 4 * (size_t)(R.scheme == ECPIC_SCHEME_EC ? R.N : R.N + 1),
+               cudaMemcpyDeviceToHost);
+  return check(cudaGetLastError(), "get_fields", err);
+}
+
+int Batch::diag(int slot, Diag* out, std::string* err) {
+  if (!slot_active(slot)) {
+    if (err) *err = "bad slot";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  const RunDev& R = h_runs_[slot];
+  out->N = R.N;
+  out->ns = R.ns;
+  cudaMemcpy(&out->st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
+  std::vector<SegState> ss(spc_);
+  cudaMemcpy(ss.data(), d_sst_ + slot * spc_, sizeof(SegState) * spc_, cudaMemcpyDeviceToHost);
+  for (int s = 0; s < R.ns; ++s) out->n_live[s] = ss[s].n_proc - ss[s].n_dead;
+  out->acc.resize((size_t)acc_size(R.ns) * (R.N + 1));
+  return check(cudaMemcpy(out->acc.data(), R.acc, 8 * out->acc.size(), cudaMemcpyDeviceToHost),
+               "diagnostics read", err);
+}
+
+int Batch::reset_averages(int slot, int sample_every, std::string* err) {
+  if (!slot_active(slot) || sample_every < 0) {
+    if (err) *err = "bad slot or sample_every";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  RunDev& R = h_runs_[slot];
+  R.sample_every = sample_every;
+  specs_[slot].sample_every = sample_every;
+  upload_run(slot);
+  cudaMemsetAsync(R.acc, 0, 8 * (size_t)acc_size(R.ns) * (R.N + 1), stream_);
+  cudaMemsetAsync(R.momd, 0, 8 * (size_t)R.ns * 2 * (R.N + 1), stream_);
+  RunState st;
+  cudaMemcpy(&st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
+  st.n_samples = 0;
+  for (int s = 0; s < kMaxSpecies; ++s) st.ke_acc[s] = 0.0;
+  cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
+  return check(cudaStreamSynchronize(stream_), "reset_averages", err);
+}
+
+int Batch::set_step_end(int slot, long long step_end, std::string* err) {
+  if (!slot_active(slot)) {
+    if (err) *err = "bad slot";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  cudaStreamSynchronize(stream_);
+  RunState st;
+  cudaMemcpy(&st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
+  st.step_end = step_end;
+  return check(cudaMemcpy(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice),
+               "set_step_end", err);
+}
+
+}  // namespace ecpic

@@ -1,0 +1,132 @@
+// runtime.h -- host runtime of libecpic: a Batch owns the device state of up
+// to max_slots independent runs and steps them together (one launch per
+// phase for all runs, replayed from CUDA graphs).
+#pragma once
+#include <climits>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace ecpic {
+
+struct HostProc {
+  int kind = 0;
+  double thr = 0, dE = 0;
+  std::vector<float> sigma;
+  int product = -1;
+};
+
+struct HostSpecies {
+  double q = 0, m = 0, w = 0;
+  long long cap = 0;
+  std::vector<HostProc> procs;
+};
+
+struct RunSpec {
+  std::vector<double> edges;
+  int bc = ECPIC_DIRICHLET_RF;
+  double v0 = 0, freq = 0, phase = 0, vdc = 0;
+  int scheme = ECPIC_SCHEME_EC;
+  std::vector<HostSpecies> species;
+  bool gas = false;
+  double ng = 0, Tg = 0, mg = 0;
+  uint64_t seed = 0;
+  double dt = 0;
+  std::vector<long long> n_init;
+  std::vector<double> T_eV;
+  int sample_every = 0;
+  long long step_end = LLONG_MAX;
+};
+
+// argument checks of a complete run description; "" when valid
+std::string validate_grid(const std::vector<double>& edges, int bc);
+std::string validate_spec(const RunSpec& s);
+// null-collision bound of a species (FP64, host): nu_max and the 24-bit
+// candidate threshold
+void null_rate(const HostSpecies& sp, const RunSpec& s, double* nu_max, uint32_t* thr24);
+// bytes of device memory a run needs
+size_t run_bytes(const RunSpec& s);
+
+struct Diag {
+  RunState st;
+  std::vector<double> acc;
+  long long n_live[kMaxSpecies] = {0, 0, 0, 0};
+  int N = 0, ns = 0;
+};
+
+class Batch {
+ public:
+  Batch(int device, cudaStream_t stream, int max_slots, int species_per_slot, int nmax);
+  ~Batch();
+  Batch(const Batch&) = delete;
+  Batch& operator=(const Batch&) = delete;
+
+  // allocate, upload, load particles (Philox), first deposit and field
+  int admit(int slot, const RunSpec& spec, std::string* err);
+  void release(int slot);
+  bool slot_active(int slot) const { return slot >= 0 && slot < max_slots_ && active_[slot]; }
+
+  int step(long long n, std::string* err);  // async
+  int profile_step(long long n, double* ms, long long* launches, std::string* err);
+  int sort_now(std::string* err);
+  int sync(std::string* err);
+  int slot_status(int slot);  // synchronises
+
+  int get_particles(int slot, int species, int32_t* cell, float* xi, float* vx, float* vy,
+                    float* vz, uint64_t* id, long long cap, long long* n, std::string* err);
+  int set_particles(int slot, int species, const int32_t* cell, const float* xi, const float* vx,
+                    const float* vy, const float* vz, const uint64_t* id, long long n,
+                    std::string* err);
+  int get_fields(int slot, double* phi, float* E, std::string* err);
+  int diag(int slot, Diag* out, std::string* err);
+  int reset_averages(int slot, int sample_every, std::string* err);
+  int set_step_end(int slot, long long step_end, std::string* err);
+  int set_sort_every(int k);
+  void set_pass_grid(int g) { pass_grid_override_ = g; invalidate_graphs(); }
+  int pass_grid() const { return pass_grid_; }
+  int sort_every() const { return sort_every_; }
+  void set_use_graphs(bool on) { use_graphs_ = on; }
+  long long live_estimate() const;
+  cudaStream_t stream() const { return stream_; }
+  int device() const { return device_; }
+  size_t bytes_in_use() const { return bytes_in_use_; }
+  const RunSpec& spec(int slot) const { return specs_[slot]; }
+
+ private:
+  BatchView view() const;
+  void upload_run(int slot);
+  void refresh(int slot);
+  void invalidate_graphs();
+  int ensure_graphs(std::string* err);
+  int choose_grid() const;
+  int check(cudaError_t e, const char* what, std::string* err);
+
+  int device_;
+  cudaStream_t stream_;
+  bool own_stream_ = false;
+  int max_slots_, spc_, nmax_, nseg_;
+  int sm_count_ = 1;
+  RunDev* d_runs_ = nullptr;
+  RunState* d_rst_ = nullptr;
+  SegDev* d_segs_ = nullptr;
+  SegState* d_sst_ = nullptr;
+  int* d_hist_ = nullptr;
+  std::vector<RunDev> h_runs_;
+  std::vector<SegDev> h_segs_;
+  std::vector<void*> slot_mem_;
+  std::vector<size_t> slot_bytes_;
+  std::vector<char> active_;
+  std::vector<RunSpec> specs_;
+  size_t bytes_in_use_ = 0;
+  int sort_every_ = 16;
+  int since_sort_ = 0;
+  bool use_graphs_ = true;
+  int pass_grid_ = 0;
+  int pass_grid_override_ = 0;
+  cudaGraphExec_t graph_k_ = nullptr;
+  cudaGraphExec_t graph_1_ = nullptr;
+};
+
+}  // namespace ecpic

@@ -1,0 +1,301 @@
+"""ctypes binding of libecpic (``include/ecpic.h``): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays to pointers and status codes to exceptions.  There is no fallback: if
+``libecpic.so`` cannot be built or loaded the import of ``lib()`` raises.
+The module-level functions carry the C names (``ecpic_create`` ...); ``Run``
+is a convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libecpic.so")
+
+ECPIC_OK = 0
+ECPIC_ERR_ARG, ECPIC_ERR_STATE, ECPIC_ERR_NOMEM = -1, -2, -3
+ECPIC_ERR_CAPACITY, ECPIC_ERR_CUDA, ECPIC_ERR_TIMEOUT, ECPIC_ERR_NAN = -4, -5, -6, -7
+ECPIC_MAX_SPECIES, ECPIC_MAX_PROC, ECPIC_MAX_CELLS = 4, 8, 2048
+ECPIC_DIRICHLET_RF, ECPIC_PERIODIC = 0, 1
+ECPIC_SCHEME_EC, ECPIC_SCHEME_MC = 0, 1
+ECPIC_ELASTIC, ECPIC_EXCITATION, ECPIC_IONIZATION, ECPIC_ION_ELASTIC, ECPIC_CX = 0, 1, 2, 3, 4
+
+_STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_STATE", -3: "ERR_NOMEM", -4: "ERR_CAPACITY",
+           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_NAN"}
+
+
+class EcpicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ecpic_diag(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("time", C.c_double), ("n_species", C.c_int), ("n_cells", C.c_int),
+        ("n_live", C.c_int64 * 4), ("absorbed", (C.c_int64 * 2) * 4), ("births", C.c_int64 * 4),
+        ("lost", C.c_int64 * 4), ("candidates", C.c_int64 * 4), ("clamps", C.c_int64 * 4),
+        ("collisions", (C.c_int64 * 8) * 4), ("ke", C.c_double * 4), ("fe", C.c_double),
+        ("n_samples", C.c_int64), ("density", C.c_void_p), ("phi", C.c_void_p),
+        ("temp_x", C.c_void_p), ("temp_x_mom", C.c_void_p),
+    ]
+
+
+# name -> (restype, argtypes); the exported symbols of include/ecpic.h
+vp, i32, i64, u32, u64, d = C.c_void_p, C.c_int, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+SIGNATURES = {
+    "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
+    "ecpic_destroy": (None, [vp]),
+    "ecpic_last_error": (C.c_char_p, [vp]),
+    "ecpic_set_grid": (i32, [vp, vp, i32, i32, d, d, d, d]),
+    "ecpic_set_scheme": (i32, [vp, i32]),
+    "ecpic_add_species": (i32, [vp, d, d, d, i64, C.POINTER(i32)]),
+    "ecpic_set_gas": (i32, [vp, d, d, d]),
+    "ecpic_add_process": (i32, [vp, i32, i32, d, d, i32, vp, i32]),
+    "ecpic_init": (i32, [vp, u64, d, vp, vp]),
+    "ecpic_step": (i32, [vp, i64]),
+    "ecpic_sync": (i32, [vp]),
+    "ecpic_reset_averages": (i32, [vp, i32]),
+    "ecpic_diagnostics": (i32, [vp, C.POINTER(ecpic_diag)]),
+    "ecpic_get_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64, C.POINTER(i64)]),
+    "ecpic_set_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64]),
+    "ecpic_get_fields": (i32, [vp, vp, vp]),
+    "ecpic_nu_max": (i32, [vp, i32, C.POINTER(d), C.POINTER(u32)]),
+    "ecpic_set_sort_every": (i32, [vp, i32]),
+    "ecpic_sort_now": (i32, [vp]),
+    "ecpic_profile_step": (i32, [vp, i64, vp, vp]),
+    "ecpic_set_pass_grid": (i32, [vp, i32]),
+    "ecpic_doubling_grid": (i32, [i32, d, d, i32, i32, vp, i32]),
+    "ecpic_deposit_device": (i32, [i32, i64, vp, vp, vp, vp]),
+    "ecpic_philox_device": (i32, [i64, vp, vp, vp, vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libecpic.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                from . import build as _build
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libecpic.so not found at {LIB_PATH}; run build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _chk(h, rc, what):
+    if rc != ECPIC_OK:
+        msg = lib().ecpic_last_error(h).decode() if h else ""
+        raise EcpicError(rc, f"{what}: {msg}")
+    return rc
+
+
+# ---------------------------------------------------------------- C names
+def ecpic_create(device=0, stream=None):
+    h = C.c_void_p()
+    rc = lib().ecpic_create(C.byref(h), device, stream)
+    if rc != ECPIC_OK:
+        raise EcpicError(rc, "ecpic_create (no CUDA device?)")
+    return h
+
+
+def ecpic_destroy(h):
+    lib().ecpic_destroy(h)
+
+
+def ecpic_doubling_grid(n_ref, L, L_buff, dx_min, dx_max):
+    e = np.zeros(n_ref + 1)
+    n = lib().ecpic_doubling_grid(n_ref, L, L_buff, dx_min, dx_max, _p(e), e.size)
+    if n < 0:
+        raise EcpicError(n, "ecpic_doubling_grid")
+    return e[: n + 1].copy()
+
+
+def ecpic_deposit_device(N, n, d_cell, d_xi, d_S, stream=None):
+    rc = lib().ecpic_deposit_device(N, n, d_cell, d_xi, d_S, stream)
+    if rc != ECPIC_OK:
+        raise EcpicError(rc, "ecpic_deposit_device")
+
+
+def ecpic_philox_device(n, d_ctr, d_key, d_out, stream=None):
+    rc = lib().ecpic_philox_device(n, d_ctr, d_key, d_out, stream)
+    if rc != ECPIC_OK:
+        raise EcpicError(rc, "ecpic_philox_device")
+
+
+class Run:
+    """One discharge on the GPU, driven through the C ABI."""
+
+    def __init__(self, device=0, stream=None):
+        self._L = lib()
+        self.h = ecpic_create(device, stream)
+        self.ns = 0
+        self.N = 0
+        self.scheme = ECPIC_SCHEME_EC
+
+    @classmethod
+    def from_config(cls, cfg, device=0, stream=None, sort_every=None, init=True):
+        r = cls(device, stream)
+        r.set_grid(cfg.edges, cfg.bc, cfg.v0, cfg.freq, cfg.phase, cfg.vdc)
+        r.set_scheme(cfg.scheme)
+        for s in cfg.species:
+            r.add_species(s.q, s.m, s.w, s.capacity)
+        if cfg.processes or cfg.n_gas:
+            r.set_gas(cfg.n_gas, cfg.T_gas, cfg.m_gas)
+        for p in cfg.processes:
+            r.add_process(p.species, p.kind, p.threshold, p.dE, p.sigma, p.product)
+        if sort_every:
+            r.set_sort_every(sort_every)
+        if init:
+            r.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
+            if cfg.sample_every:
+                r.reset_averages(cfg.sample_every)
+        return r
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ecpic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_grid(self, edges, bc=ECPIC_DIRICHLET_RF, v0=0.0, freq=0.0, phase=0.0, vdc=0.0):
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        _chk(self.h, self._L.ecpic_set_grid(self.h, _p(e), e.size, bc, v0, freq, phase, vdc),
+             "ecpic_set_grid")
+        self.N = e.size - 1
+
+    def set_scheme(self, scheme):
+        _chk(self.h, self._L.ecpic_set_scheme(self.h, scheme), "ecpic_set_scheme")
+        self.scheme = scheme
+
+    def add_species(self, q, m, w, capacity):
+        out = C.c_int()
+        _chk(self.h, self._L.ecpic_add_species(self.h, q, m, w, int(capacity), C.byref(out)),
+             "ecpic_add_species")
+        self.ns += 1
+        return out.value
+
+    def set_gas(self, n_g, T_g, m_g):
+        _chk(self.h, self._L.ecpic_set_gas(self.h, n_g, T_g, m_g), "ecpic_set_gas")
+
+    def add_process(self, species, kind, threshold, dE, sigma, product=-1):
+        s = np.ascontiguousarray(sigma, dtype=np.float32)
+        _chk(self.h, self._L.ecpic_add_process(self.h, species, kind, threshold, dE, s.size,
+                                               _p(s), product), "ecpic_add_process")
+
+    def init(self, seed, dt, n_per_species, T_eV):
+        n = np.ascontiguousarray(n_per_species, dtype=np.int64)
+        T = np.ascontiguousarray(T_eV, dtype=np.float64)
+        _chk(self.h, self._L.ecpic_init(self.h, int(seed), dt, _p(n), _p(T)), "ecpic_init")
+
+    def step(self, n=1):
+        _chk(self.h, self._L.ecpic_step(self.h, int(n)), "ecpic_step")
+
+    def sync(self, allow=()):
+        rc = self._L.ecpic_sync(self.h)
+        if rc in allow:
+            return rc
+        return _chk(self.h, rc, "ecpic_sync")
+
+    def reset_averages(self, sample_every):
+        _chk(self.h, self._L.ecpic_reset_averages(self.h, sample_every), "ecpic_reset_averages")
+
+    def set_sort_every(self, k):
+        _chk(self.h, self._L.ecpic_set_sort_every(self.h, k), "ecpic_set_sort_every")
+
+    def sort_now(self):
+        _chk(self.h, self._L.ecpic_sort_now(self.h), "ecpic_sort_now")
+
+    def profile_step(self, n):
+        ms = np.zeros(3)
+        cnt = np.zeros(3, np.int64)
+        _chk(self.h, self._L.ecpic_profile_step(self.h, int(n), _p(ms), _p(cnt)),
+             "ecpic_profile_step")
+        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], launches=cnt.tolist())
+
+    def set_pass_grid(self, ctas):
+        _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
+
+    def nu_max(self, species):
+        nu = C.c_double()
+        t = C.c_uint32()
+        _chk(self.h, self._L.ecpic_nu_max(self.h, species, C.byref(nu), C.byref(t)), "ecpic_nu_max")
+        return nu.value, int(t.value)
+
+    def get_particles(self, species):
+        n = C.c_int64()
+        rc = self._L.ecpic_get_particles(self.h, species, None, None, None, None, None, None, 0,
+                                         C.byref(n))
+        if rc not in (ECPIC_OK, ECPIC_ERR_ARG):
+            _chk(self.h, rc, "ecpic_get_particles")
+        m = n.value
+        cell = np.zeros(m, np.int32)
+        xi, vx, vy, vz = (np.zeros(m, np.float32) for _ in range(4))
+        ids = np.zeros(m, np.uint64)
+        _chk(self.h, self._L.ecpic_get_particles(self.h, species, _p(cell), _p(xi), _p(vx),
+                                                 _p(vy), _p(vz), _p(ids), m, C.byref(n)),
+             "ecpic_get_particles")
+        return dict(cell=cell, xi=xi, vx=vx, vy=vy, vz=vz, id=ids)
+
+    def set_particles(self, species, cell, xi, vx, vy, vz, ids):
+        c = np.ascontiguousarray(cell, dtype=np.int32)
+        f = [np.ascontiguousarray(a, dtype=np.float32) for a in (xi, vx, vy, vz)]
+        i = np.ascontiguousarray(ids, dtype=np.uint64)
+        _chk(self.h, self._L.ecpic_set_particles(self.h, species, _p(c), *[_p(a) for a in f], _p(i),
+                                                 c.size), "ecpic_set_particles")
+
+    def fields(self):
+        phi = np.zeros(self.N + 1)
+        E = np.zeros(self.N if self.scheme == ECPIC_SCHEME_EC else self.N + 1, np.float32)
+        _chk(self.h, self._L.ecpic_get_fields(self.h, _p(phi), _p(E)), "ecpic_get_fields")
+        return dict(phi=phi, E=E)
+
+    def diagnostics(self, profiles=True):
+        dg = ecpic_diag()
+        arrs = {}
+        if profiles:
+            M = self.N + 1
+            arrs = dict(density=np.zeros(self.ns * M), phi=np.zeros(M),
+                        temp_x=np.zeros(self.ns * M), temp_x_mom=np.zeros(self.ns * M))
+            for k, a in arrs.items():
+                setattr(dg, k, _p(a))
+        _chk(self.h, self._L.ecpic_diagnostics(self.h, C.byref(dg)), "ecpic_diagnostics")
+        ns = self.ns
+        out = dict(step=dg.step, time=dg.time, n_samples=dg.n_samples, fe=dg.fe,
+                   ke=np.array(dg.ke[:ns]), species=[])
+        for s in range(ns):
+            out["species"].append(dict(
+                n=dg.n_live[s], absorbed_left=dg.absorbed[s][0], absorbed_right=dg.absorbed[s][1],
+                births=dg.births[s], lost=dg.lost[s], candidates=dg.candidates[s],
+                clamps=dg.clamps[s], collisions=list(dg.collisions[s])))
+        if profiles:
+            M = self.N + 1
+            out["density"] = arrs["density"].reshape(ns, M)
+            out["phi"] = arrs["phi"]
+            out["Tx"] = arrs["temp_x"].reshape(ns, M)
+            out["Tx_mom"] = arrs["temp_x_mom"].reshape(ns, M)
+        return out

@@ -286,3 +286,23 @@ def random_state(rng: np.random.Generator, N: int, n: int, vth: float, cells_per
                                                 + np.uint64(11))).astype(np.uint64)
     return dict(cell=cell, xi=xi, vx=v[0].astype(np.float32), vy=v[1].astype(np.float32),
                 vz=v[2].astype(np.float32), id=ids)
+
+
+def periodic_plasma(N: int = 64, dx_lambda: float = 4.0, ppc: int = 64, dt_wpe: float = 0.1,
+                    n_steps: int = 1000, seed: int = 0, scheme: int = EC, ions: bool = False,
+                    n0: float = 1e14, Te: float = 2.0, Ti: float = 0.5) -> RunConfig:
+    """Collisionless periodic Maxwellian of App. B: electrons (and optionally
+    mobile ions) on a uniform neutralising background, dx = dx_lambda * lambda_De,
+    dt = dt_wpe / w_pe."""
+    lam = math.sqrt(EPS0 * Te / (n0 * QE))
+    wpe = math.sqrt(n0 * QE ** 2 / (EPS0 * ME))
+    L = N * dx_lambda * lam
+    npart = N * ppc
+    w = n0 * L / npart
+    sp = [Species(-QE, ME, w, npart, npart, Te)]
+    if ions:
+        sp.append(Species(QE, M_ION, w, npart, npart, Ti))
+    return RunConfig(name=f"periodic-{N}", edges=uniform_edges(N, L), bc=PERIODIC, v0=0.0,
+                     freq=0.0, phase=0.0, vdc=0.0, scheme=scheme, species=sp, n_gas=0.0,
+                     T_gas=T_GAS, m_gas=M_ION, processes=[], seed=seed, dt=dt_wpe / wpe,
+                     n_steps=n_steps)

@@ -27,3 +27,15 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_from_config(cfg: I.RunConfig, **kw):
+    from paper_2308_13092_gb300 import ecpic
+    return ecpic.Run.from_config(cfg, **kw)
+
+
+def require_gpu():
+    import pytest
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")

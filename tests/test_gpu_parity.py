@@ -1,0 +1,247 @@
+"""GPU-vs-oracle parity of the whole step through the C ABI.
+
+* loader: cell indices bit-exact, xi and velocities within FP32 rounding of
+  the oracle's FP64 values;
+* field of a given state: E and phi within 1e-5 of the field scale;
+* one step from an identical state (EC and MC, uniform and non-uniform,
+  Dirichlet-RF and periodic, with and without collisions): cells bit-exact
+  except particles within 4 FP32 ulps of a face; positions and velocities to
+  relative 1e-5; collision candidates exactly equal (integer decision on the
+  same Philox stream); only near-ties of the process choice may differ;
+* run-to-run determinism of the GPU state (integer deposit: bit-identical
+  results for any launch shape).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_13092_gb300 import inputs as I
+from helpers import oracle_from_config, gpu_from_config, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+FACE = 4 * 2.0 ** -24
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _small(scheme=I.EC, edges=None, collisions=True, bc=I.DIRICHLET, n=4000, seed=3):
+    cfg = I.ccp("parity", N=64, n0=5e13, dt=1.0 / (400 * I.F_RF), ppc=0, v0=300.0, p_mtorr=60.0,
+                n_steps=1, seed=seed, scheme=scheme, edges=edges, L=0.05, collisions=collisions,
+                n_per_species=n)
+    cfg.bc = bc
+    return cfg
+
+
+def _set_same_state(cfg, g, o, seed=11, tail=0.05):
+    rng = np.random.default_rng(seed)
+    dx = np.diff(cfg.edges)
+    states = []
+    for s, sp in enumerate(cfg.species):
+        vth = np.sqrt(I.QE * (5.0 if s == 0 else 0.5) / sp.m)
+        st = I.random_state(rng, cfg.N, sp.n0, vth, cells_per_step=2.5, dt=cfg.dt,
+                            dx_min=dx.min(), tail=tail, id_base=1000000 * s)
+        g.set_particles(s, st["cell"], st["xi"], st["vx"], st["vy"], st["vz"], st["id"])
+        o.set_particles_cell(s, st["cell"], st["xi"], st["vx"], st["vy"], st["vz"], st["id"])
+        states.append(st)
+    return states
+
+
+def _pair(cfg):
+    g = gpu_from_config(cfg)
+    o = oracle_from_config(cfg)
+    return g, o
+
+
+def _compare(cfg, g, o, before, allow=0):
+    """Compare the species states by particle id; returns mismatch counts."""
+    e = cfg.edges
+    dx = np.diff(e)
+    report = {}
+    for s in range(len(cfg.species)):
+        gp = g.get_particles(s)
+        op = o.get_particles(s)
+        oc, oxi = o.get_particles_cell(s)
+        gi = np.argsort(gp["id"])
+        oi = np.argsort(op["id"])
+        gid, oid = gp["id"][gi], op["id"][oi]
+        common, ga, oa = np.intersect1d(gid, oid, return_indices=True)
+        only = (gid.size - common.size) + (oid.size - common.size)
+        gsel, osel = gi[ga], oi[oa]
+        cg, xg = gp["cell"][gsel], gp["xi"][gsel].astype(np.float64)
+        co, xo = oc[osel], oxi[osel]
+        near_face = (xo < FACE) | (xo > 1 - FACE) | (xg < FACE) | (xg > 1 - FACE)
+        bad_cell = (cg != co) & ~near_face
+        Xg = e[cg] + xg * dx[cg]
+        Xo = op["X"][osel]
+        bad_X = np.abs(Xg - Xo) > RTOL * np.maximum(np.abs(Xo), dx.min())
+        # velocity scale: the result and the value it came from
+        vb = {}
+        bid = before[s]["id"]
+        order = np.argsort(bid)
+        pos = np.searchsorted(bid[order], common)
+        pos = np.minimum(pos, bid.size - 1)
+        known = bid[order][pos] == common
+        bad_v = np.zeros(common.size, bool)
+        for comp in ("vx", "vy", "vz"):
+            vgc = gp[comp][gsel].astype(np.float64)
+            voc = op[comp][osel]
+            vbc = np.where(known, before[s][comp][order][pos].astype(np.float64), 0.0)
+            scale = np.abs(voc) + np.abs(vbc) + 1e-3 * np.sqrt(I.QE * 0.03 / cfg.species[s].m)
+            bad_v |= np.abs(vgc - voc) > RTOL * scale
+        bad = bad_cell | bad_X | bad_v
+        report[s] = dict(n=common.size, only=only, bad=int(bad.sum()), bad_cell=int(bad_cell.sum()),
+                         bad_X=int(bad_X.sum()), bad_v=int(bad_v.sum()))
+    return report
+
+
+def _counters_match(g, o, exact_keys=("candidates",)):
+    dg = g.diagnostics(profiles=False)["species"]
+    co = o.counters()["species"]
+    for s in range(len(co)):
+        for k in exact_keys:
+            assert dg[s][k] == co[s][k], (s, k, dg[s][k], co[s][k])
+    return dg, co
+
+
+def test_loader_parity():
+    for cfg in (I.config_small(seed=5), _small(edges=oracle.doubling_grid(128, 0.05, 0.01, 1, 8))):
+        g, o = _pair(cfg)
+        for s, sp in enumerate(cfg.species):
+            gp = g.get_particles(s)
+            oc, oxi = o.get_particles_cell(s)
+            op = o.get_particles(s)
+            assert np.array_equal(gp["id"], op["id"])
+            assert np.array_equal(gp["cell"], oc)
+            assert np.all(np.abs(gp["xi"].astype(np.float64) - oxi) <= 2.0 ** -24)
+            for comp in ("vx", "vy", "vz"):
+                d = np.abs(gp[comp].astype(np.float64) - op[comp])
+                assert np.all(d <= 2.0 ** -23 * np.abs(op[comp]) + 1e-30)
+
+
+@pytest.mark.parametrize("scheme", [I.EC, I.MC])
+@pytest.mark.parametrize("grid", ["uniform", "doubling", "tanh"])
+def test_field_parity(scheme, grid):
+    edges = {"uniform": None, "doubling": oracle.doubling_grid(128, 0.05, 0.01, 1, 8),
+             "tanh": I.tanh_edges(70, 0.05, 0.05 / 400)}[grid]
+    cfg = _small(scheme=scheme, edges=edges)
+    g, o = _pair(cfg)
+    _set_same_state(cfg, g, o)
+    fg, fo = g.fields(), o.fields()
+    Es = np.max(np.abs(fo["E"]))
+    assert np.max(np.abs(fg["E"] - fo["E"])) <= RTOL * Es
+    ps = np.max(np.abs(fo["phi"])) + 1.0
+    assert np.max(np.abs(fg["phi"] - fo["phi"])) <= RTOL * ps
+
+
+CASES = [
+    ("EC", "uniform", "dirichlet", False), ("MC", "uniform", "dirichlet", False),
+    ("EC", "doubling", "dirichlet", False), ("MC", "tanh", "dirichlet", False),
+    ("EC", "uniform", "periodic", False), ("MC", "uniform", "periodic", False),
+    ("EC", "doubling", "periodic", False),
+    ("EC", "uniform", "dirichlet", True), ("MC", "doubling", "dirichlet", True),
+    ("EC", "tanh", "dirichlet", True),
+]
+
+
+@pytest.mark.parametrize("scheme,grid,bc,coll", CASES)
+def test_one_step_parity(scheme, grid, bc, coll):
+    edges = {"uniform": None, "doubling": oracle.doubling_grid(128, 0.05, 0.01, 1, 8),
+             "tanh": I.tanh_edges(70, 0.05, 0.05 / 400)}[grid]
+    cfg = _small(scheme={"EC": I.EC, "MC": I.MC}[scheme], edges=edges, collisions=coll,
+                 bc={"dirichlet": I.DIRICHLET, "periodic": I.PERIODIC}[bc], n=6000)
+    g, o = _pair(cfg)
+    before = _set_same_state(cfg, g, o)
+    g.step(1)
+    g.sync()
+    o.step(1)
+    rep = _compare(cfg, g, o, before)
+    dg, co = _counters_match(g, o)
+    for s, r in rep.items():
+        n = r["n"]
+        assert n > 0.8 * cfg.species[s].n0
+        limit = 0 if not coll else max(2, int(2e-3 * max(1, co[s]["candidates"])))
+        assert r["bad"] <= limit, (s, r)
+        assert r["only"] <= (0 if not coll else limit) + 2, (s, r)
+    if coll:
+        for s in range(2):
+            assert dg[s]["candidates"] > 0
+            assert abs(sum(dg[s]["collisions"]) - sum(co[s]["collisions"])) <= 2
+    assert g.diagnostics(profiles=False)["step"] == 1
+
+
+def test_ten_steps_collisionless_stay_close():
+    cfg = _small(collisions=False, n=6000)
+    g, o = _pair(cfg)
+    before = _set_same_state(cfg, g, o, tail=0.0)
+    g.step(10)
+    o.step(10)
+    rep = _compare(cfg, g, o, before)
+    for s, r in rep.items():
+        assert r["bad_cell"] <= 2 and r["only"] <= 2, r
+
+
+def test_gpu_deterministic_across_launch_shapes():
+    """The fixed-point deposit makes the state independent of thread order:
+    two runs with different sort cadences give bit-identical particles."""
+    cfg = I.config_small(seed=9)
+    a = gpu_from_config(cfg, sort_every=16)
+    b = gpu_from_config(cfg, sort_every=5)
+    a.step(120)
+    b.step(120)
+    for s in range(2):
+        pa, pb = a.get_particles(s), b.get_particles(s)
+        ia, ib = np.argsort(pa["id"]), np.argsort(pb["id"])
+        for k in ("cell", "xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(pa[k][ia], pb[k][ib]), k
+    assert a.diagnostics(profiles=False)["species"] == b.diagnostics(profiles=False)["species"]
+
+
+def test_sort_orders_and_compacts():
+    cfg = I.config_small(seed=2)
+    g = gpu_from_config(cfg, sort_every=1000)
+    g.step(37)
+    before = [g.get_particles(s) for s in range(2)]
+    g.sort_now()
+    for s in range(2):
+        p = g.get_particles(s)
+        assert np.all(np.diff(p["cell"]) >= 0)
+        ia, ib = np.argsort(before[s]["id"]), np.argsort(p["id"])
+        for k in ("cell", "xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(before[s][k][ia], p[k][ib])
+
+
+def test_capacity_overflow_is_reported_not_fatal():
+    cfg = I.config_small(seed=4)
+    for sp in cfg.species:
+        sp.capacity = sp.n0 + 3
+    cfg.n_gas *= 30  # many ionisations
+    g = gpu_from_config(cfg)
+    g.step(200)
+    from paper_2308_13092_gb300 import ecpic
+    rc = g.sync(allow=(ecpic.ECPIC_ERR_CAPACITY,))
+    d = g.diagnostics(profiles=False)
+    assert rc == ecpic.ECPIC_ERR_CAPACITY
+    assert d["species"][0]["lost"] + d["species"][1]["lost"] > 0
+    assert d["species"][0]["n"] <= cfg.species[0].capacity
+
+
+def test_empty_species_and_single_particle():
+    cfg = _small(collisions=False, n=1)
+    g, o = _pair(cfg)
+    g.set_particles(1, [], [], [], [], [], np.array([], np.uint64))
+    o.set_particles_cell(1, [], [], [], [], [], np.array([], np.uint64))
+    g.set_particles(0, [31], [0.5], [1e5], [0.0], [0.0], np.array([42], np.uint64))
+    o.set_particles_cell(0, [31], [0.5], [1e5], [0.0], [0.0], np.array([42], np.uint64))
+    g.step(3)
+    o.step(3)
+    gp, op = g.get_particles(0), o.get_particles(0)
+    oc, oxi = o.get_particles_cell(0)
+    assert gp["cell"].tolist() == oc.tolist()
+    assert np.allclose(gp["xi"], oxi, rtol=0, atol=1e-5)
+    assert np.allclose(gp["vx"], op["vx"], rtol=1e-5)
+    assert g.get_particles(1)["id"].size == 0
