@@ -1,20 +1,30 @@
 """Throughput benchmark of the GB300 EC-PIC hot path (particle-steps/s).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload resolved]
 
-A "step" is one time step of the whole hot path (gather, push, walls, MCC,
-deposit, field; the counting sort every 16 steps) over every live particle of
-the workload.  Inputs are synthetic and seeded (``paper_2308_13092_gb300.inputs``).
+A "step" is one time step of the whole hot path -- gather, leapfrog push,
+walls, null-collision MCC, fixed-point deposit, Poisson and field, the counting
+sort every 16 steps -- for every live particle of the workload.  Inputs are
+synthetic and seeded (``paper_2308_13092_gb300.inputs``); no dataset exists.
 
-Workload "resolved": one 1D3V RF-CCP, 1024 uniform cells at dx = lambda_De,
-256 particles/cell/species (524,288 particles), 300 V, 30 mTorr, w_pe dt = 0.2.
-Its particle state (29 MB) fits in the 129 MB L2, so L2 is flushed (a 512 MB
-write) before every timed step and each step is timed alone with CUDA events.
+Headline workload ("batched"): 256 independent RF-CCP runs drawn from
+``default_rng(0)`` -- cells logU[64,1024], particles logU[1e4,1e6] split
+between electrons and 4 amu ions, V0 logU[100,500] V, p logU[10,100] mTorr,
+dx U[0.5,1] mm, n0 = 1e14, dt = 1/(400 f) -- all resident on the GPU and
+advanced together, one launch per kernel phase, replayed from CUDA graphs.
+About 5.5e7 particles (1.5 GB of particle state, far above the 129 MB L2).
 
-For N > 1 (torchrun) every rank steps an independent replica of the workload
-(different seed); value = all ranks' particle-steps / max over ranks of the
-time.  --impl reference times the FP64 CPU oracle on the host cores.
+Also reported (same JSON line):
+  single_run  the 1024-cell, 524,288-particle resolved discharge alone (its
+              29 MB state fits in L2, so L2 is flushed before every timed step);
+  one_by_one  the same batched manifest run one run at a time (a sample);
+  served      a Poisson stream of run requests admitted by device memory,
+              with p50/p99 completion latency, against one-at-a-time service;
+  e2e         the batched job through the public API from host configs to
+              host diagnostics.
+For N > 1 (torchrun) each rank runs its own manifest (seed = rank); value =
+all ranks' particle-steps / max over ranks of the time.  --impl reference
+times the FP64 CPU oracle on one host core on a sample of the same workload.
 """
 from __future__ import annotations
 
@@ -31,43 +41,48 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
 
 from paper_2308_13092_gb300 import inputs as I  # noqa: E402
 
-BYTES_PER_PARTICLE_STEP = 40  # 28 B read (cell, xi, vx, vy, vz, id) + 12 B written
+# Algorithmic HBM bytes per particle-step of the fused pass: read cell, xi,
+# vx, vy, vz (4 B each) and the 8 B id = 28 B, write cell, xi, vx = 12 B.
+BYTES_PER_PARTICLE_STEP = 40
 METRIC = "particle-steps/s"
+N_RUNS = 256
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=800)
+    ap.add_argument("--warmup", type=int, default=40)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="resolved", choices=["resolved"])
+    ap.add_argument("--runs", type=int, default=N_RUNS)
+    ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only (no single-run, one-by-one, served, e2e)")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
-def workload_config(name, rank):
-    if name == "resolved":
-        return I.config_resolved(seed=1000 + rank)
-    raise ValueError(name)
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), "measured"
+        return json.load(open(p)).get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def manifest(rank, args, steps):
+    runs = I.batched_manifest(args.runs, seed=rank, steps=steps, scale=args.scale)
+    for r in runs:
+        r.sample_every = 40  # 1/10 RF period at 400 steps per period
+    return runs
 
 
 class Clocks:
@@ -95,7 +110,7 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
@@ -104,6 +119,7 @@ class Clocks:
             try:
                 sm.append(float(parts[1]))
                 mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[5:9]):
@@ -111,59 +127,219 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(cfg, budget_s=12.0, max_steps=10_000):
-    """The FP64 C oracle, as it stands, on one host core: particle-steps/s over
-    a bounded number of steps of the same workload."""
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(cfgs, budget_s=12.0):
+    """The FP64 C oracle as it stands, one host core, over a bounded sample:
+    the first runs of the manifest for a few steps each, particle-steps/s."""
     from helpers import oracle_from_config
-    o = oracle_from_config(cfg)
-    t0 = time.perf_counter()
+    t_all = 0.0
     ps = 0
     steps = 0
-    while steps < max_steps:
-        c = o.counters()
-        live = sum(s["n"] for s in c["species"])
-        o.step(1, allow_capacity=True)
-        ps += live
-        steps += 1
-        if time.perf_counter() - t0 > budget_s:
+    used = 0
+    for cfg in cfgs:
+        o = oracle_from_config(cfg)
+        used += 1
+        for _ in range(40):
+            live = sum(s["n"] for s in o.counters()["species"])
+            t0 = time.perf_counter()
+            o.step(1, allow_capacity=True)
+            t_all += time.perf_counter() - t0
+            ps += live
+            steps += 1
+        o.close()
+        if t_all > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return ps / dt, steps, ps
+    return ps / t_all, ps, used, steps
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cfg = workload_config(args.workload, 0)
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    cfgs = manifest(0, args, steps=args.warmup + args.steps)
     from helpers import oracle_from_config
-    o = oracle_from_config(cfg)
+    # each timed step: one step of every run of a rotating sample of the
+    # manifest (a bounded sample of the batched workload)
+    sample = cfgs[: min(8, len(cfgs))]
+    oracles = [oracle_from_config(c) for c in sample]
     for _ in range(args.warmup):
-        o.step(1, allow_capacity=True)
+        for o in oracles:
+            o.step(1, allow_capacity=True)
     t0 = time.perf_counter()
     ps = 0
     for _ in range(args.steps):
-        ps += sum(s["n"] for s in o.counters()["species"])
-        o.step(1, allow_capacity=True)
+        for o in oracles:
+            ps += sum(s["n"] for s in o.counters()["species"])
+            o.step(1, allow_capacity=True)
+        if time.perf_counter() - t0 > 150:
+            break
     dt = time.perf_counter() - t0
     v = ps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {cfg.name}, {cfg.N} cells, "
-                                   f"{cfg.n_particles} particles, FP64 CPU oracle"},
+            "config": {"workload": f"batched RF-CCP manifest ({len(cfgs)} runs); FP64 CPU oracle "
+                                   f"on the first {len(sample)} runs"},
             "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps of the full workload after "
-                                       f"{args.warmup} warm-up steps"},
+                             "sample": f"{len(sample)} runs of the batched manifest, "
+                                       f"{args.steps} steps each after {args.warmup} warm-up"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arms
+def pump_until_done(eng, chunk=200):
+    while True:
+        r, q = eng.pump(chunk)
+        if r == 0 and q == 0:
+            return
+
+
+def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
+    cfg = I.config_resolved(seed=11)
+    cfg.sample_every = 20
+    run = ecpic.Run.from_config(cfg, device=device, stream=stream.cuda_stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def l2_flush():
+        flush.zero_()
+        flush.sum()
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            l2_flush()
+            run.step(1)
+        run.sync()
+        ps0 = run.diagnostics(profiles=False)
+        n0 = sum(s["n"] for s in ps0["species"])
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            l2_flush()
+            evs[k][0].record(stream)
+            run.step(1)
+            evs[k][1].record(stream)
+        stream.synchronize()
+        run.sync()
+        n1 = sum(s["n"] for s in run.diagnostics(profiles=False)["species"])
+        ms = float(sum(a.elapsed_time(b) for a, b in evs))
+        prof = run.profile_step(min(steps, 50))
+    run.close()
+    del flush
+    v = 0.5 * (n0 + n1) * steps / (ms * 1e-3)
+    return {"value": v, "unit": "particle-steps/s", "ms_per_step": ms / steps,
+            "workload": f"{cfg.name}: {cfg.N} uniform cells, {cfg.n_particles} particles",
+            "l2": "flushed before every timed step",
+            "pass_ms_avg": prof["pass_ms"] / max(1, prof["launches"][0]),
+            "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1])}
+
+
+def one_by_one_block(ecpic, cfgs, stream, device, n_runs=12, steps=200):
+    """The manifest one run at a time through the engine (a sample)."""
+    rng = np.random.default_rng(5)
+    pick = rng.choice(len(cfgs), min(n_runs, len(cfgs)), replace=False)
+    eng = ecpic.Engine(device=device, stream=stream.cuda_stream, max_slots=1, max_cells=1024)
+    t = 0.0
+    ps = 0
+    for i in pick:
+        c = cfgs[i]
+        tk = eng.submit(c, n_steps=steps)
+        eng.pump(0)  # admit and load
+        s0 = eng.stats()["particle_steps"]
+        t0 = time.perf_counter()
+        pump_until_done(eng, chunk=steps)
+        t += time.perf_counter() - t0
+        ps += eng.poll(tk)["particle_steps"]
+        eng.release(tk)
+        del s0
+    eng.close()
+    return {"value": ps / t, "unit": "particle-steps/s", "runs": int(len(pick)),
+            "steps_per_run": steps,
+            "what": "sampled runs of the batched manifest, each alone (wall clock per run)"}
+
+
+def served_block(ecpic, stream, device, capacity, n_req=64, rho=0.7):
+    """Poisson arrivals of CCP run requests (sizes as in the batched manifest,
+    5..50 RF periods at 1/10 of the steps), continuous batching vs one at a
+    time; completion latency = finish - arrival."""
+    reqs = I.served_stream(n_req, seed=1, rate=1.0)
+    for r in reqs:
+        r.config.n_steps = max(40, r.config.n_steps // 10)
+        r.config.sample_every = 40
+    work = np.mean([r.config.n_particles * r.config.n_steps for r in reqs])
+    rate = rho * capacity / work
+    arr = np.cumsum(np.random.default_rng(2).exponential(1.0 / rate, n_req))
+
+    def serve(max_slots):
+        eng = ecpic.Engine(device=device, stream=stream.cuda_stream, max_slots=max_slots,
+                           max_cells=1024, mem_budget=64 << 30)
+        t0 = time.perf_counter()
+        pending = list(range(n_req))
+        live = {}
+        done = {}
+        while len(done) < n_req:
+            now = time.perf_counter() - t0
+            while pending and arr[pending[0]] <= now:
+                i = pending.pop(0)
+                live[eng.submit(reqs[i].config)] = i
+            if not live:
+                time.sleep(max(0.0, arr[pending[0]] - now))
+                continue
+            eng.pump(40)
+            now = time.perf_counter() - t0
+            for tk in list(live):
+                st = eng.poll(tk)
+                if st["state"] == 2 or st["state"] < 0:
+                    done[live.pop(tk)] = (now, st["particle_steps"])
+                    eng.release(tk)
+        total = time.perf_counter() - t0
+        eng.close()
+        lat = np.array([done[i][0] - arr[i] for i in range(n_req)])
+        ps = sum(v[1] for v in done.values())
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "particle_steps_per_s": ps / total, "wall_s": total}
+
+    mix = serve(64)
+    alone = serve(1)
+    return {"requests": n_req, "load": rho, "arrival_rate_per_s": rate,
+            "continuous_batching": mix, "one_at_a_time": alone,
+            "what": "Poisson arrivals; admitted by device memory as slots free; steps/10 of "
+                    "the full request lengths"}
+
+
+def e2e_block(ecpic, cfgs, stream, device, steps):
+    """Whole batched job through the public API: host configs in, host
+    diagnostics out, wall clock."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eng = ecpic.Engine(device=device, stream=stream.cuda_stream, max_slots=len(cfgs),
+                       max_cells=1024)
+    h2d = 0
+    tickets = []
+    for c in cfgs:
+        tickets.append(eng.submit(c, n_steps=steps))
+        h2d += c.edges.nbytes + sum(p.sigma.nbytes for p in c.processes) + 512
+    pump_until_done(eng, chunk=steps)
+    ps = 0
+    d2h = 0
+    for tk, c in zip(tickets, cfgs):
+        r = eng.poll(tk, diagnostics=True, profiles=True)
+        ps += r["particle_steps"]
+        d2h += 8 * (c.N + 1) * (4 * len(c.species) + 1) + 1024
+    dt = time.perf_counter() - t0
+    eng.close()
+    return {"value": ps / dt, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
+            "steps": steps,
+            "what": "ecpic_engine_submit of 256 host configs (particles loaded on the GPU), "
+                    "pump to completion, ecpic_engine_poll of every run's diagnostics; wall clock"}
 
 
 def main():
@@ -179,152 +355,101 @@ def main():
     torch.cuda.set_device(local)
     from paper_2308_13092_gb300 import ecpic
     ecpic.lib(build_if_missing=True)
-
-    cfg = workload_config(args.workload, rank)
-    cfg.sample_every = 20
     stream = torch.cuda.Stream()
-    run = ecpic.Run.from_config(cfg, device=local, stream=stream.cuda_stream)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def live():
-        return sum(s["n"] for s in run.diagnostics(profiles=False)["species"])
+    total = args.warmup + args.steps + 400  # runs never retire inside the window
+    cfgs = manifest(rank, args, total)
+    eng = ecpic.Engine(device=local, stream=stream.cuda_stream, max_slots=len(cfgs),
+                       max_cells=1024)
+    for c in cfgs:
+        eng.submit(c)
+    eng.pump(0)  # admit and load everything
+    eng.pump(args.warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ps0 = eng.stats()["particle_steps"]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev0.record(stream)
+    eng.pump(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ps = eng.stats()["particle_steps"] - ps0
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.zero_()
-            run.step(1)
-        stream.synchronize()
-        run.sync()
-
-        # ---- timed region: each step alone, L2 flushed before it
-        n0 = live()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        counts = []
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-        clocks = Clocks(local)
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            run.step(1)
-            evs[k][1].record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize()
-        ck = clocks.stop()
-        run.sync()
-        n1 = live()
-        step_ms = [a.elapsed_time(b) for a, b in evs]
-        total_ms = float(sum(step_ms))
-        # live particles at the start of each step: interpolate the start/end
-        # counts (they change by < 1% over the window)
-        particle_steps = 0.5 * (n0 + n1) * args.steps
-
-        # ---- per-kernel device time on the same stream, same workload
-        prof = {"pass_ms": 0.0, "field_ms": 0.0, "sort_ms": 0.0, "launches": [0, 0, 0]}
-        nprof = min(args.steps, 100)
-        live_prof = 0
-        for _ in range(nprof):
-            flush.zero_()
-            live_prof += live()
-            p = run.profile_step(1)
-            for k in ("pass_ms", "field_ms", "sort_ms"):
-                prof[k] += p[k]
-            prof["launches"] = [a + b for a, b in zip(prof["launches"], p["launches"])]
+    # per-kernel device time, same workload, same stream
+    nprof = min(args.steps, 64)
+    ps_a = eng.stats()["particle_steps"]
+    prof = eng.profile(nprof)
+    ps_prof = eng.stats()["particle_steps"] - ps_a
+    eng.close()
 
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
+        t = torch.tensor([ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        ps = torch.tensor([particle_steps], dtype=torch.float64)
-        dist.all_reduce(ps, op=dist.ReduceOp.SUM)
-        particle_steps = float(ps.item())
+        p = torch.tensor([float(ps)], dtype=torch.float64)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        ms, ps = float(t.item()), float(p.item())
 
-    value = particle_steps / (total_ms * 1e-3)
+    value = ps / (ms * 1e-3)
     hbm, peak_kind = peaks()
-    pass_avg_ms = prof["pass_ms"] / max(1, prof["launches"][0])
-    per_launch_bytes = BYTES_PER_PARTICLE_STEP * live_prof / max(1, nprof)
-    achieved = per_launch_bytes / (pass_avg_ms * 1e-3) / 1e9
-    kernels_per_step = (prof["launches"][0] + prof["launches"][1] + prof["launches"][2]) / max(1, nprof)
+    pass_ms = prof["pass_ms"] / max(1, prof["launches"][0])
+    bytes_per_launch = BYTES_PER_PARTICLE_STEP * ps_prof / max(1, nprof)
+    achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
+    launches_per_step = sum(prof["launches"]) / max(1, nprof)
 
-    # ---- end to end through the C ABI with host buffers (pinned)
-    e2e = None
-    if rank == 0:
-        e2e = end_to_end(cfg, local, stream, n_steps=min(args.steps, 100))
-
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["single_run"] = single_run_block(torch, ecpic, stream, local)
+        extras["one_by_one"] = one_by_one_block(ecpic, cfgs, stream, local)
+        extras["served"] = served_block(ecpic, stream, local, capacity=value / max(1, world))
+        e2e = e2e_block(ecpic, cfgs, stream, local, steps=200)
+    else:
+        e2e = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, st, ps = oracle_rate(cfg)
+        v, psamp, used, st = oracle_sample(cfgs)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{st} steps ({ps:.3g} particle-steps) of the same workload on one "
-                         f"host core, FP64"}
+               "sample": f"first {used} runs of the batched manifest, 40 steps each "
+                         f"({psamp:.3g} particle-steps), FP64, one host core"}
 
     if rank == 0:
+        n_part = sum(c.n_particles for c in cfgs)
         line = {
             "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {cfg.name}, {cfg.N} uniform cells, "
-                                   f"{cfg.n_particles} particles (2 species), EC, 300 V, 30 mTorr",
-                       "runs": world, "l2": "flushed (512 MB write) before every timed step",
-                       "sort_every": 16, "sample_every": cfg.sample_every},
+            "config": {"workload": f"batched: {len(cfgs)} independent 1D3V EC-PIC RF-CCP runs "
+                                   f"(seeded manifest), {n_part} initial particles, cells "
+                                   f"{min(c.N for c in cfgs)}-{max(c.N for c in cfgs)}",
+                       "runs_per_gpu": len(cfgs), "l2": "inputs larger than L2 (1.5 GB state)",
+                       "sort_every": 16, "sample_every": 40, "scheme": "EC",
+                       "arithmetic": "FP32 particles, FP64 field solve"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": "k_pass", "peak_kind": peak_kind,
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_pass",
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
-                         "pass_ms_avg": pass_avg_ms,
+                         "pass_ms_avg": pass_ms,
                          "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1]),
-                         "sort_ms_per_step": prof["sort_ms"] / max(1, nprof)},
+                         "sort_ms_per_step": prof["sort_ms"] / max(1, nprof),
+                         "pass_share": prof["pass_ms"] / max(1e-9, prof["pass_ms"] + prof["field_ms"]
+                                                             + prof["sort_ms"])},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(round(kernels_per_step * args.steps)),
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": ck,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def end_to_end(cfg, device, stream, n_steps):
-    """Particle-steps/s through the public API: the initial state is uploaded
-    from pinned host buffers, then every step is ecpic_step(1) followed by a
-    device-to-host read of the run's diagnostics (ecpic_diagnostics)."""
-    import torch
-    from paper_2308_13092_gb300 import ecpic
-    run = ecpic.Run.from_config(cfg, device=device, stream=stream.cuda_stream)
-    host = []
-    for s in range(len(cfg.species)):
-        p = run.get_particles(s)
-        pinned = {}
-        for k, a in p.items():
-            t = torch.empty(a.size, dtype={np.int32: torch.int32, np.float32: torch.float32,
-                                           np.uint64: torch.int64}[a.dtype.type], pin_memory=True)
-            t.numpy()[:] = a.view(t.numpy().dtype)
-            pinned[k] = t.numpy().view(a.dtype)
-        host.append(pinned)
-    h2d = sum(a.nbytes for p in host for a in p.values())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, p in enumerate(host):
-        run.set_particles(s, p["cell"], p["xi"], p["vx"], p["vy"], p["vz"], p["id"])
-    ps = 0
-    d2h = 0
-    for _ in range(n_steps):
-        run.step(1)
-        d = run.diagnostics(profiles=False)
-        ps += sum(s["n"] for s in d["species"])
-        d2h += 1024
-    dt = time.perf_counter() - t0
-    run.close()
-    return {"value": ps / dt, "unit": "particle-steps/s",
-            "h2d_bytes_per_step": int(h2d / n_steps), "d2h_bytes_per_step": 1024,
-            "what": "set_particles from pinned host buffers, then per step ecpic_step(1) + "
-                    "ecpic_diagnostics (synchronising D2H read)"}
 
 
 if __name__ == "__main__":

@@ -164,6 +164,82 @@ int ecpic_profile_step(ecpic_run* run, int64_t n_steps, double* ms, int64_t* lau
 int ecpic_set_pass_grid(ecpic_run* run, int ctas);
 
 /* ------------------------------------------------------------------ */
+/* Batched and served runs.  An engine keeps up to max_slots independent
+ * discharges resident on one GPU and advances all of them with one launch per
+ * kernel phase (replayed from CUDA graphs); the runs may differ in grid, cell
+ * count, particle count, voltage, pressure, scheme and time step.  Requests
+ * are admitted first-fit, in submission order, as slots and the device-memory
+ * budget allow; each run stops at its own step count and is retired with its
+ * diagnostics.  The paper ran several simulations concurrently on one GPU
+ * (Sec. 2b); this is that mode of use made first-class. */
+typedef struct ecpic_engine ecpic_engine;
+
+typedef struct {
+  int species;          /* index within the run's species */
+  int kind;             /* ECPIC_ELASTIC ... ECPIC_CX */
+  double threshold_eV;
+  double dE_eV;
+  int n;                /* table entries */
+  const float* sigma_m2;/* host, n entries; copied at submit */
+  int product_species;  /* ionisation only */
+} ecpic_process_desc;
+
+typedef struct {
+  const double* edges;  /* host, n_edges entries; copied at submit */
+  int n_edges;
+  int bc;
+  double v0, freq_hz, phase_rad, v_dc;
+  int scheme;
+  int n_species;
+  double q[ECPIC_MAX_SPECIES], m[ECPIC_MAX_SPECIES], w[ECPIC_MAX_SPECIES];
+  int64_t capacity[ECPIC_MAX_SPECIES];
+  int64_t n_init[ECPIC_MAX_SPECIES];
+  double T_eV[ECPIC_MAX_SPECIES];
+  double n_gas, T_gas, m_gas; /* n_gas = 0: no gas */
+  int n_proc;
+  const ecpic_process_desc* procs; /* host, n_proc entries; copied at submit */
+  uint64_t seed;
+  double dt;
+  int sample_every;     /* diagnostics sampling cadence (0 = off) */
+} ecpic_run_config;
+
+/* max_cells bounds N of every admitted run; species_per_run bounds their
+ * species count; mem_budget_bytes bounds the particle and grid memory of the
+ * resident runs (0 = no limit). */
+int ecpic_engine_create(ecpic_engine** out, int device, void* cuda_stream,
+                        size_t mem_budget_bytes, int max_slots, int max_cells,
+                        int species_per_run);
+void ecpic_engine_destroy(ecpic_engine* eng);
+const char* ecpic_engine_last_error(const ecpic_engine* eng);
+/* Queue a run for n_steps steps; *ticket identifies it.  Validates and
+ * copies the configuration; ECPIC_ERR_NOMEM if it could never fit. */
+int ecpic_engine_submit(ecpic_engine* eng, const ecpic_run_config* cfg, int64_t n_steps,
+                        uint64_t* ticket);
+/* One scheduling round: admit queued runs that fit, advance every resident
+ * run by up to max_steps steps (runs stop at their own step count), wait, and
+ * retire the runs that finished.  *n_resident (may be NULL) receives the
+ * number of runs resident after the round, *n_queued the queue length. */
+int ecpic_engine_pump(ecpic_engine* eng, int64_t max_steps, int* n_resident, int* n_queued);
+/* State of a ticket: 0 queued, 1 resident, 2 finished, < 0 an ecpic_status
+ * error of that run.  When finished and out != NULL, fills its diagnostics
+ * (the profile arrays of out, if not NULL, sized n_species*(N+1) / N+1).
+ * *steps_done / *particle_steps (may be NULL) report its progress. */
+int ecpic_engine_poll(ecpic_engine* eng, uint64_t ticket, int* state, ecpic_diag* out,
+                      int64_t* steps_done, int64_t* particle_steps);
+/* Forget a finished ticket's stored results. */
+int ecpic_engine_release(ecpic_engine* eng, uint64_t ticket);
+/* Totals since creation: particle-steps advanced, runs finished, and the
+ * device bytes currently held by resident runs. */
+int ecpic_engine_stats(ecpic_engine* eng, int64_t* particle_steps, int64_t* runs_finished,
+                       int64_t* bytes_resident);
+/* Tuning: pass-kernel CTAs (0 = all SMs), counting-sort cadence. */
+int ecpic_engine_tune(ecpic_engine* eng, int pass_ctas, int sort_every);
+/* Measurement: advance the resident runs n_steps with plain launches,
+ * bracketing each kernel phase with CUDA events on the engine's stream (see
+ * ecpic_profile_step); synchronises.  No admission or retirement. */
+int ecpic_engine_profile(ecpic_engine* eng, int64_t n_steps, double* ms, int64_t* launches);
+
+/* ------------------------------------------------------------------ */
 /* Doubling non-uniform grid (Sec. 3c rules 1-4): buffers of dx_min cells of
  * total length >= L_buff at both electrodes, then cell sizes doubling up to
  * dx_max (sizes in units of dx_ref = L/n_ref).  Writes the N+1 edges (m) into

@@ -267,47 +267,9 @@ int ecpic_diagnostics(ecpic_run* r, ecpic_diag* out) {
   return guarded(r, [&]() -> int {
     Diag d;
     std::string err;
-    int rc = r->batch->diag(0, &d, &err);
+    const int rc = r->batch->diag(0, &d, &err);
     if (rc) return fail(r, rc, err);
-    const int N = d.N, ns = d.ns;
-    out->step = d.st.step;
-    out->time = (double)d.st.step * r->spec.dt;
-    out->n_species = ns;
-    out->n_cells = N;
-    for (int s = 0; s < ECPIC_MAX_SPECIES; ++s) {
-      out->n_live[s] = 0;
-      out->ke[s] = s < ns ? d.st.ke[s] : 0.0;
-      const unsigned long long* c = d.st.ctr[s];
-      out->absorbed[s][0] = (int64_t)c[ecpic::C_ABS_L];
-      out->absorbed[s][1] = (int64_t)c[ecpic::C_ABS_R];
-      out->births[s] = (int64_t)c[ecpic::C_BIRTHS];
-      out->lost[s] = (int64_t)c[ecpic::C_LOST];
-      out->candidates[s] = (int64_t)c[ecpic::C_CAND];
-      out->clamps[s] = (int64_t)c[ecpic::C_CLAMPS];
-      for (int p = 0; p < ECPIC_MAX_PROC; ++p) out->collisions[s][p] = (int64_t)c[ecpic::C_COLL0 + p];
-    }
-    for (int s = 0; s < ns; ++s) out->n_live[s] = d.n_live[s];
-    out->fe = d.st.fe;
-    out->n_samples = d.st.n_samples;
-    const double inv = d.st.n_samples > 0 ? 1.0 / (double)d.st.n_samples : 0.0;
-    const size_t M = (size_t)N + 1;
-    const double e = 1.602176634e-19;
-    for (int s = 0; s < ns; ++s)
-      for (size_t n = 0; n < M; ++n) {
-        if (out->density) out->density[s * M + n] = d.acc[s * M + n] * inv;
-        if (out->temp_x) out->temp_x[s * M + n] = d.acc[(ns + s) * M + n] * inv;
-        if (out->temp_x_mom) {
-          const double M0 = d.acc[(2 * ns + s) * M + n];
-          double T = 0.0;
-          if (M0 > 0) {
-            const double a = d.acc[(3 * ns + s) * M + n] / M0, b = d.acc[(4 * ns + s) * M + n] / M0;
-            T = r->spec.species[s].m * (b - a * a) / e;
-          }
-          out->temp_x_mom[s * M + n] = T;
-        }
-      }
-    if (out->phi)
-      for (size_t n = 0; n < M; ++n) out->phi[n] = d.acc[(size_t)(5 * ns) * M + n] * inv;
+    ecpic::fill_diag(d, r->spec, out);
     return ECPIC_OK;
   });
 }

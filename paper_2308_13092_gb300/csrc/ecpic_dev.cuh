@@ -69,6 +69,11 @@ struct RunDev {
   const double* x;      // N+1 edges
   const double* dx;     // N widths
   const double* V;      // N+1 node control volumes
+  const double* invV;   // N+1: 1/V
+  const double* mcw;    // N+1: centred-field weight dx_n/(dx_{n-1}+dx_n) (MC scheme)
+  const double* cumV;   // N+1: sum_{m=1..n} V_m (periodic neutralising background)
+  double* g;            // N: (phi_{n+1}-phi_n)/dx_n of the current field, FP64
+  double inv_L;
   const float* dtdx;    // N: dt/dx_j
   const float* rp;      // N: dx_j / dx_{j+1} (wrapped when periodic)
   const float* rm;      // N: dx_j / dx_{j-1}
@@ -98,6 +103,9 @@ struct RunState {
   double ke[kMaxSpecies];       // of the last sampled push
   double fe_field;              // field energy of the current field
   double fe;                    // at the level of the last sampled push
+  double phi0;                  // electrode potential of the current field
+  long long phi_level;          // time level of the potential held in phi
+  unsigned long long psteps;    // particle-steps advanced (live at the start of each step)
   unsigned long long ctr[kMaxSpecies][kNumCtr];
 };
 

@@ -95,9 +95,10 @@ __device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int
   return true;
 }
 
-// exclusive prefix of the particle counts of all segments: pre[0..nseg]
+// exclusive prefix of the work of all segments (particles, or groups of
+// `unit` particles): pre[0..nseg]
 __device__ long long seg_prefix(const BatchView& b, int mode, int only, long long* pre,
-                                long long* wsm) {
+                                long long* wsm, int unit = 1) {
   const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
   const int s0 = threadIdx.x * per;
   long long loc = 0;
@@ -105,8 +106,9 @@ __device__ long long seg_prefix(const BatchView& b, int mode, int only, long lon
     const int s = s0 + k;
     if (s < b.nseg) {
       const int slot = b.segs[s].run;
-      const long long c =
-          run_live(b.runs[slot], b.rst[slot], mode, only, slot) ? b.sst[s].n_proc : 0;
+      const long long c = run_live(b.runs[slot], b.rst[slot], mode, only, slot)
+                              ? (b.sst[s].n_proc + unit - 1) / unit
+                              : 0;
       pre[s] = c;
       loc += c;
     }
@@ -236,16 +238,160 @@ __device__ __forceinline__ void walk_nonuniform(int& c, float& f, float g, int N
   f = g;
 }
 
+constexpr int kQueueCap = 2048;  // collision-candidate queue per CTA (all warps)
+constexpr int kWarpQ = kQueueCap / (kPassBlock / 32);  // per warp: >= 32 + 4 * 32
+
 struct PassShared {
   unsigned long long ctr[kNumCtr];
   long long wsm[32];
   double dsm[32];
   int lohi[2];
+  int qcount;
 };
 
-// one piece [beg, end) of segment s
-__device__ void pass_piece(const BatchView& b, int s, long long beg, long long end, int mode,
-                           unsigned long long* Ssm, float* Msm, PassShared& sh) {
+// Null-collision MCC of one candidate (Sec. 2a step 6), run from the CTA's
+// candidate queue after the streaming phase: reloads the particle (already
+// pushed, L2-resident), redraws Philox block A, picks the process and
+// scatters.  Ionisation appends the secondary electron to this segment and
+// the ion to its species' segment, and deposits both.
+__device__ void collide_candidate(const BatchView& b, const RunDev* R, RunState* st, const SegDev& G,
+                                  SegState* ss, int sp, int cur, long long i, long long k, int N,
+                                  int Nm, bool sample, unsigned long long* Ssm, float* Msm,
+                                  PassShared& sh) {
+  const SpeciesDev* SP = &R->sp[sp];
+  const uint64_t seed = R->seed;
+  const int c = G.cell[cur][i];
+  const float f = G.xi[cur][i];
+  float vx = G.vx[cur][i], vy = G.vy[cur][i], vz = G.vz[cur][i];
+  const uint64_t id = G.id[cur][i];
+  const uint4 A = draw(seed, id, (uint32_t)k, (uint32_t)sp << 8);
+  const int nproc = SP->nproc;
+  float gx = vx, gy = vy, gz = vz, vnx = 0.f, vny = 0.f, vnz = 0.f;
+  if (SP->heavy) {
+    const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+    float z0, z1, z2, z3;
+    box_muller(u24_open(B.x), u24(B.y), z0, z1);
+    box_muller(u24_open(B.z), u24(B.w), z2, z3);
+    const float sd = R->vth_gas;
+    vnx = sd * z0;
+    vny = sd * z1;
+    vnz = sd * z2;
+    gx -= vnx;
+    gy -= vny;
+    gz -= vnz;
+  }
+  const float g2 = gx * gx + gy * gy + gz * gz;
+  const float gm = sqrtf(g2);
+  const float En = SP->half_m_over_e * g2;
+  const float ng = R->ng;
+  float nu[kMaxProc];
+  float tot = 0.0f;
+#pragma unroll
+  for (int p = 0; p < kMaxProc; ++p) {
+    nu[p] = 0.0f;
+    if (p < nproc) {
+      nu[p] = ng * sigma_at(SP->proc[p].sigma, SP->proc[p].thr, En, SP->dE_inv, SP->ntab) * gm;
+      tot += nu[p];
+    }
+  }
+  if (tot > SP->nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
+  const float Rr = u24(A.y) * SP->nu_max;
+  int chosen = -1;
+  float cum = 0.0f;
+#pragma unroll
+  for (int p = 0; p < kMaxProc; ++p) {
+    if (p < nproc && chosen < 0) {
+      cum += nu[p];
+      if (Rr < cum) chosen = p;
+    }
+  }
+  if (chosen >= 0) {
+    atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
+    float d0, d1, d2;
+    isotropic(u24(A.z), u24(A.w), d0, d1, d2);
+    const int kind = SP->proc[chosen].kind;
+    const float thr = SP->proc[chosen].thr;
+    if (kind == ECPIC_ELASTIC) {
+      const float cchi = gm > 0.0f ? (gx * d0 + gy * d1 + gz * d2) / gm : 1.0f;
+      const float E1 = En * (1.0f - SP->two_m_over_M * (1.0f - cchi));
+      const float v1 = sqrtf(SP->two_e_over_m * E1);
+      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+    } else if (kind == ECPIC_EXCITATION) {
+      const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
+      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+    } else if (kind == ECPIC_IONIZATION) {
+      const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+      const float Erem = En - thr;
+      const float fr = u24(B.x);
+      const float v1 = sqrtf(SP->two_e_over_m * (fr * Erem));
+      const float v2 = sqrtf(SP->two_e_over_m * ((1.0f - fr) * Erem));
+      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+      float e0, e1, e2;
+      isotropic(u24(B.y), u24(B.z), e0, e1, e2);
+      const uint4 Cw = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 2u);
+      float z0, z1, z2, z3;
+      box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
+      box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
+      const float sd = R->vth_gas;
+      atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
+      // secondary electron: same segment and species, deposited in shared memory
+      if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
+        deposit_one(Ssm, c, f);
+        if (sample) {
+          const float vb = v2 * e0;
+          atomicAdd(Msm + c, (1.0f - f) * vb);
+          atomicAdd(Msm + c + 1, f * vb);
+          atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
+          atomicAdd(Msm + Nm + c + 1, f * vb * vb);
+        }
+      } else {
+        atomicAdd(&sh.ctr[C_LOST], 1ull);
+        set_status(st, ECPIC_ERR_CAPACITY);
+      }
+      // ion: the product species' segment, deposited straight to HBM
+      const int ps = SP->proc[chosen].product_seg;
+      const int pspec = SP->proc[chosen].product_species;
+      const float ivx = sd * z0;
+      if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
+        deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
+        if (sample) {
+          double* md = R->momd + (size_t)pspec * 2 * (N + 1);
+          atomicAdd(md + c, (double)((1.0f - f) * ivx));
+          atomicAdd(md + c + 1, (double)(f * ivx));
+          atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
+          atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
+        }
+      } else {
+        atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
+        set_status(st, ECPIC_ERR_CAPACITY);
+      }
+    } else if (kind == ECPIC_ION_ELASTIC) {
+      const float h = SP->m_frac * gm;
+      vx = SP->mass_frac * vx + SP->m_frac * vnx + h * d0;
+      vy = SP->mass_frac * vy + SP->m_frac * vny + h * d1;
+      vz = SP->mass_frac * vz + SP->m_frac * vnz + h * d2;
+    } else {  // ECPIC_CX
+      vx = vnx; vy = vny; vz = vnz;
+    }
+    G.vx[cur][i] = vx;
+    G.vy[cur][i] = vy;
+    G.vz[cur][i] = vz;
+  }
+  if (sample) {
+    atomicAdd(Msm + c, (1.0f - f) * vx);
+    atomicAdd(Msm + c + 1, f * vx);
+    atomicAdd(Msm + Nm + c, (1.0f - f) * vx * vx);
+    atomicAdd(Msm + Nm + c + 1, f * vx * vx);
+  }
+}
+
+// Streaming part of one piece: quads [qbeg, qend) of segment s, four
+// particles per thread with 16-byte loads.  Gather (Eq. 6-7 / CIC), leapfrog
+// (Eq. 8-9) in cell units, walls, the Philox candidate test, fixed-point
+// deposit of X^{k+1} (Eq. 2-3).  vy, vz are read only on energy-sample steps;
+// candidates go to a shared-memory queue drained by collide_candidate.
+__device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
+                           unsigned long long* Ssm, float* Msm, int* queue, PassShared& sh) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
@@ -253,12 +399,13 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
   SegState* ss = b.sst + s;
   const int N = R->N, scheme = R->scheme, bc = R->bc, uniform = R->uniform;
   const int cur = ss->cur;
-  int32_t* __restrict__ pc = G.cell[cur];
-  float* __restrict__ pxi = G.xi[cur];
-  float* __restrict__ pvx = G.vx[cur];
-  float* __restrict__ pvy = G.vy[cur];
-  float* __restrict__ pvz = G.vz[cur];
-  const uint64_t* __restrict__ pid = G.id[cur];
+  const long long n = ss->n_proc;
+  int32_t* pc = G.cell[cur];
+  float* pxi = G.xi[cur];
+  float* pvx = G.vx[cur];
+  const float* pvy = G.vy[cur];
+  const float* pvz = G.vz[cur];
+  const uint64_t* pid = G.id[cur];
   const long long k = st->step;
   const bool stepping = (mode == MODE_STEP);
   const bool sample = stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0;
@@ -267,212 +414,176 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
   const float* __restrict__ E = R->E;
   const float* __restrict__ dtdx = R->dtdx;
   const uint32_t thr24 = SP->thr24;
-  const int nproc = SP->nproc;
+  const bool mcc = stepping && SP->nproc > 0 && thr24 > 0;
   const uint64_t seed = R->seed;
   const int Nm = b.nmax + 1;
   const int lane = threadIdx.x & 31;
 
   int my_lo = INT_MAX, my_hi = -1;
   float ke = 0.0f;
-  unsigned cand = 0;
+  unsigned ncand = 0, nlive = 0;
+  // per-warp candidate queue: drained 32 at a time, warp-synchronously
+  int* wq = queue + (threadIdx.x >> 5) * kWarpQ;
+  int wcount = 0;
 
-  for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
-    const long long i = base + lane;
-    bool valid = i < end;
-    int c = valid ? pc[i] : -1;
-    valid = valid && c >= 0;
-    float f = 0.0f, vx = 0.0f;
-    if (valid) {
-      f = pxi[i];
-      vx = pvx[i];
-    }
-    if (valid && stepping) {
-      float vy = pvy[i], vz = pvz[i];
-      // gather: EC face field of the particle's cell (Eq. 6-7) or CIC (MC)
-      float Ei;
-      if (scheme == ECPIC_SCHEME_EC) {
-        Ei = __ldg(E + c);
-      } else {
-        const float e0 = __ldg(E + c), e1 = __ldg(E + c + 1);
-        Ei = e0 + f * (e1 - e0);
+  // block-uniform trip count (warp collectives below need full warps)
+  for (long long base = qbeg; base < qend; base += kPassBlock) {
+    const long long q = base + (long long)threadIdx.x;
+    const long long i0 = 4 * q;
+    const bool inq = q < qend;
+    const bool full = inq && (i0 + 3 < n);
+    int c[4];
+    float f[4], v[4];
+    if (full) {
+      const int4 c4 = *reinterpret_cast<const int4*>(pc + i0);
+      const float4 f4 = *reinterpret_cast<const float4*>(pxi + i0);
+      const float4 v4 = *reinterpret_cast<const float4*>(pvx + i0);
+      c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+      f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
+      v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool in = inq && (i0 + j < n);
+        c[j] = in ? pc[i0 + j] : -1;
+        f[j] = in ? pxi[i0 + j] : 0.0f;
+        v[j] = in ? pvx[i0 + j] : 0.0f;
       }
-      // leapfrog (Eq. 8)
-      const float vnew = vx + qm_dt * Ei;
-      if (sample) ke += vx * vnew + vy * vy + vz * vz;
-      vx = vnew;
-      if (!(fabsf(vx) < 3.0e8f)) {
-        // non-finite or superluminal: drop the particle, flag the run
-        pc[i] = -1;
-        atomicAdd(&sh.ctr[C_NAN], 1ull);
-        set_status(st, ECPIC_ERR_NAN);
-        valid = false;
-      } else {
+    }
+    bool cand[4] = {false, false, false, false};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nlive += c[j] >= 0 ? 1u : 0u;
+    if (stepping) {
+      uint64_t id[4] = {0, 0, 0, 0};
+      if (mcc) {
+        if (full) {
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(pid + i0);
+          const ulonglong2 bq = *reinterpret_cast<const ulonglong2*>(pid + i0 + 2);
+          id[0] = a.x; id[1] = a.y; id[2] = bq.x; id[3] = bq.y;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) id[j] = c[j] >= 0 ? pid[i0 + j] : 0ull;
+        }
+      }
+      float yz[4] = {0.f, 0.f, 0.f, 0.f};
+      if (sample) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c[j] >= 0) yz[j] = pvy[i0 + j] * pvy[i0 + j] + pvz[i0 + j] * pvz[i0 + j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (c[j] < 0) continue;
+        int cj = c[j];
+        float fj = f[j];
+        // gather: face field of the cell (EC) or CIC of node fields (MC)
+        float Ei;
+        if (scheme == ECPIC_SCHEME_EC) {
+          Ei = __ldg(E + cj);
+        } else {
+          const float e0 = __ldg(E + cj), e1 = __ldg(E + cj + 1);
+          Ei = e0 + fj * (e1 - e0);
+        }
+        const float vnew = v[j] + qm_dt * Ei;  // Eq. 8
+        if (sample) ke += v[j] * vnew + yz[j];
+        v[j] = vnew;
+        if (!(fabsf(vnew) < 3.0e8f)) {
+          atomicAdd(&sh.ctr[C_NAN], 1ull);
+          set_status(st, ECPIC_ERR_NAN);
+          c[j] = -1;
+          continue;
+        }
         // Eq. 9 in cell units
         if (uniform) {
-          float g = f + vx * dtdx_u;
+          float g = fj + vnew * dtdx_u;
           if (!(g >= 0.0f && g < 1.0f)) {
             const float fl = floorf(g);
-            c += (int)fl;
+            cj += (int)fl;
             g -= fl;
             if (g >= 1.0f) {
-              c += 1;
+              cj += 1;
               g = 0.0f;
             }
             if (bc == ECPIC_PERIODIC) {
-              c %= N;
-              if (c < 0) c += N;
+              cj %= N;
+              if (cj < 0) cj += N;
             }
           }
-          f = g;
+          fj = g;
         } else {
-          walk_nonuniform(c, f, f + vx * __ldg(dtdx + c), N, bc, R->rp, R->rm);
+          walk_nonuniform(cj, fj, fj + vnew * __ldg(dtdx + cj), N, bc, R->rp, R->rm);
         }
-        // walls: X <= 0 or X >= L
-        if (bc != ECPIC_PERIODIC && (c < 0 || c >= N || (c == 0 && f == 0.0f))) {
-          pc[i] = -1;
-          atomicAdd(&sh.ctr[c >= N ? C_ABS_R : C_ABS_L], 1ull);
-          valid = false;
-        } else {
-          bool yz = false;
-          if (nproc > 0) {
-            const uint64_t id = pid[i];
-            const uint4 A = draw(seed, id, (uint32_t)k, (uint32_t)sp << 8);
-            if ((A.x >> 8) < thr24) {
-              ++cand;
-              float gx = vx, gy = vy, gz = vz, vnx = 0.f, vny = 0.f, vnz = 0.f;
-              if (SP->heavy) {
-                const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
-                float z0, z1, z2, z3;
-                box_muller(u24_open(B.x), u24(B.y), z0, z1);
-                box_muller(u24_open(B.z), u24(B.w), z2, z3);
-                const float sd = R->vth_gas;
-                vnx = sd * z0;
-                vny = sd * z1;
-                vnz = sd * z2;
-                gx -= vnx;
-                gy -= vny;
-                gz -= vnz;
-              }
-              const float g2 = gx * gx + gy * gy + gz * gz;
-              const float gm = sqrtf(g2);
-              const float En = SP->half_m_over_e * g2;
-              const float ng = R->ng;
-              float nu[kMaxProc];
-              float tot = 0.0f;
+        // walls: absorbed when X <= 0 or X >= L
+        if (bc != ECPIC_PERIODIC && (cj < 0 || cj >= N || (cj == 0 && fj == 0.0f))) {
+          atomicAdd(&sh.ctr[cj >= N ? C_ABS_R : C_ABS_L], 1ull);
+          c[j] = -1;
+          continue;
+        }
+        c[j] = cj;
+        f[j] = fj;
+        if (mcc) {
+          const uint4 A = draw(seed, id[j], (uint32_t)k, (uint32_t)sp << 8);
+          cand[j] = (A.x >> 8) < thr24;
+        }
+      }
+      if (full) {
+        *reinterpret_cast<int4*>(pc + i0) = make_int4(c[0], c[1], c[2], c[3]);
+        *reinterpret_cast<float4*>(pxi + i0) = make_float4(f[0], f[1], f[2], f[3]);
+        *reinterpret_cast<float4*>(pvx + i0) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
 #pragma unroll
-              for (int p = 0; p < kMaxProc; ++p) {
-                nu[p] = 0.0f;
-                if (p < nproc) {
-                  nu[p] = ng * sigma_at(SP->proc[p].sigma, SP->proc[p].thr, En, SP->dE_inv, SP->ntab) * gm;
-                  tot += nu[p];
-                }
-              }
-              if (tot > SP->nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
-              const float Rr = u24(A.y) * SP->nu_max;
-              int chosen = -1;
-              float cum = 0.0f;
+        for (int j = 0; j < 4; ++j)
+          if (inq && i0 + j < n) {
+            pc[i0 + j] = c[j];
+            pxi[i0 + j] = f[j];
+            pvx[i0 + j] = v[j];
+          }
+      }
+      if (mcc) {
 #pragma unroll
-              for (int p = 0; p < kMaxProc; ++p) {
-                if (p < nproc && chosen < 0) {
-                  cum += nu[p];
-                  if (Rr < cum) chosen = p;
-                }
-              }
-              if (chosen >= 0) {
-                atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
-                float d0, d1, d2;
-                isotropic(u24(A.z), u24(A.w), d0, d1, d2);
-                const int kind = SP->proc[chosen].kind;
-                const float thr = SP->proc[chosen].thr;
-                yz = true;
-                if (kind == ECPIC_ELASTIC) {
-                  const float cchi = gm > 0.0f ? (gx * d0 + gy * d1 + gz * d2) / gm : 1.0f;
-                  const float E1 = En * (1.0f - SP->two_m_over_M * (1.0f - cchi));
-                  const float v1 = sqrtf(SP->two_e_over_m * E1);
-                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-                } else if (kind == ECPIC_EXCITATION) {
-                  const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
-                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-                } else if (kind == ECPIC_IONIZATION) {
-                  const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
-                  const float Erem = En - thr;
-                  const float fr = u24(B.x);
-                  const float v1 = sqrtf(SP->two_e_over_m * (fr * Erem));
-                  const float v2 = sqrtf(SP->two_e_over_m * ((1.0f - fr) * Erem));
-                  vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-                  float e0, e1, e2;
-                  isotropic(u24(B.y), u24(B.z), e0, e1, e2);
-                  const uint4 Cw = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 2u);
-                  float z0, z1, z2, z3;
-                  box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
-                  box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
-                  const float sd = R->vth_gas;
-                  atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
-                  // secondary electron: same segment, deposited here
-                  if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
-                    deposit_one(Ssm, c, f);
-                    if (sample) {
-                      const float vb = v2 * e0;
-                      atomicAdd(Msm + c, (1.0f - f) * vb);
-                      atomicAdd(Msm + c + 1, f * vb);
-                      atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
-                      atomicAdd(Msm + Nm + c + 1, f * vb * vb);
-                    }
-                  } else {
-                    atomicAdd(&sh.ctr[C_LOST], 1ull);
-                    set_status(st, ECPIC_ERR_CAPACITY);
-                  }
-                  // ion: product species' segment, deposited straight to HBM
-                  const int ps = SP->proc[chosen].product_seg;
-                  const int pspec = SP->proc[chosen].product_species;
-                  const float ivx = sd * z0;
-                  if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2,
-                                      child_id(id, k, 2))) {
-                    deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
-                    if (sample) {
-                      double* md = R->momd + (size_t)pspec * 2 * (N + 1);
-                      atomicAdd(md + c, (double)((1.0f - f) * ivx));
-                      atomicAdd(md + c + 1, (double)(f * ivx));
-                      atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
-                      atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
-                    }
-                  } else {
-                    atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
-                    set_status(st, ECPIC_ERR_CAPACITY);
-                  }
-                } else if (kind == ECPIC_ION_ELASTIC) {
-                  const float h = SP->m_frac * gm;
-                  vx = SP->mass_frac * vx + SP->m_frac * vnx + h * d0;
-                  vy = SP->mass_frac * vy + SP->m_frac * vny + h * d1;
-                  vz = SP->mass_frac * vz + SP->m_frac * vnz + h * d2;
-                } else {  // ECPIC_CX
-                  vx = vnx; vy = vny; vz = vnz;
-                }
-              }
-            }
-          }
-          pc[i] = c;
-          pxi[i] = f;
-          pvx[i] = vx;
-          if (yz) {
-            pvy[i] = vy;
-            pvz[i] = vz;
-          }
+        for (int j = 0; j < 4; ++j) {
+          const unsigned m = __ballot_sync(kFull, cand[j]);
+          if (cand[j]) wq[wcount + __popc(m & ((1u << lane) - 1u))] = (int)(i0 + j);
+          wcount += __popc(m);
+          ncand += cand[j] ? 1u : 0u;
         }
       }
     }
-    // fixed-point CIC deposit of X^{k+1} (Eq. 2-3)
-    deposit_warp(Ssm, valid, c, f);
-    if (valid) {
-      my_lo = min(my_lo, c);
-      my_hi = max(my_hi, c + 1);
-      if (sample) {
-        atomicAdd(Msm + c, (1.0f - f) * vx);
-        atomicAdd(Msm + c + 1, f * vx);
-        atomicAdd(Msm + Nm + c, (1.0f - f) * vx * vx);
-        atomicAdd(Msm + Nm + c + 1, f * vx * vx);
+    // fixed-point CIC deposit of the new positions (Eq. 2-3)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool val = c[j] >= 0;
+      deposit_warp(Ssm, val, c[j], f[j]);
+      if (val) {
+        my_lo = min(my_lo, c[j]);
+        my_hi = max(my_hi, c[j] + 1);
+        if (sample && !cand[j]) {
+          atomicAdd(Msm + c[j], (1.0f - f[j]) * v[j]);
+          atomicAdd(Msm + c[j] + 1, f[j] * v[j]);
+          atomicAdd(Msm + Nm + c[j], (1.0f - f[j]) * v[j] * v[j]);
+          atomicAdd(Msm + Nm + c[j] + 1, f[j] * v[j] * v[j]);
+        }
       }
     }
+    while (mcc && wcount >= 32) {
+      __syncwarp();
+      collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
+      const int rest = wcount - 32;
+      for (int r = 0; r < (rest + 31) / 32; ++r) {
+        const int e = lane + 32 * r;
+        const int val = e < rest ? wq[e + 32] : 0;
+        __syncwarp();
+        if (e < rest) wq[e] = val;
+        __syncwarp();
+      }
+      wcount = rest;
+    }
+  }
+  if (mcc && wcount > 0) {
+    __syncwarp();
+    if (lane < wcount)
+      collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
+    __syncwarp();
   }
 
   // piece epilogue: node range, energy, counters, flush to HBM
@@ -481,13 +592,15 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
     my_lo = min(my_lo, __shfl_xor_sync(kFull, my_lo, o));
     my_hi = max(my_hi, __shfl_xor_sync(kFull, my_hi, o));
   }
-  cand = warp_sum(cand);
+  ncand = warp_sum(ncand);
+  nlive = warp_sum(nlive);
+  if (lane == 0 && stepping && nlive) atomicAdd(&st->psteps, (unsigned long long)nlive);
   if (lane == 0) {
     if (my_hi >= 0) {
       atomicMin(&sh.lohi[0], my_lo);
       atomicMax(&sh.lohi[1], my_hi);
     }
-    if (cand) atomicAdd(&sh.ctr[C_CAND], (unsigned long long)cand);
+    if (ncand) atomicAdd(&sh.ctr[C_CAND], (unsigned long long)ncand);
   }
   if (sample) {
     const double kes = block_sum((double)ke, sh.dsm);
@@ -497,18 +610,18 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
   const int flo = sh.lohi[0], fhi = sh.lohi[1];
   unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   double* md = R->momd + (size_t)sp * 2 * (N + 1);
-  for (int n = flo + (int)threadIdx.x; n <= fhi; n += kPassBlock) {
-    const unsigned long long v = Ssm[n];
-    if (v) {
-      atomicAdd(Sg + n, v);
-      Ssm[n] = 0ull;
+  for (int nn = flo + (int)threadIdx.x; nn <= fhi; nn += kPassBlock) {
+    const unsigned long long val = Ssm[nn];
+    if (val) {
+      atomicAdd(Sg + nn, val);
+      Ssm[nn] = 0ull;
     }
     if (sample) {
-      const float m1 = Msm[n], m2 = Msm[Nm + n];
-      if (m1 != 0.0f) atomicAdd(md + n, (double)m1);
-      if (m2 != 0.0f) atomicAdd(md + (N + 1) + n, (double)m2);
-      Msm[n] = 0.0f;
-      Msm[Nm + n] = 0.0f;
+      const float m1 = Msm[nn], m2 = Msm[Nm + nn];
+      if (m1 != 0.0f) atomicAdd(md + nn, (double)m1);
+      if (m2 != 0.0f) atomicAdd(md + (N + 1) + nn, (double)m2);
+      Msm[nn] = 0.0f;
+      Msm[Nm + nn] = 0.0f;
     }
   }
   if (threadIdx.x == 0) {
@@ -517,9 +630,9 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
   }
   __syncthreads();
   if (threadIdx.x < kNumCtr) {
-    const unsigned long long v = sh.ctr[threadIdx.x];
-    if (v) {
-      atomicAdd(&st->ctr[sp][threadIdx.x], v);
+    const unsigned long long val = sh.ctr[threadIdx.x];
+    if (val) {
+      atomicAdd(&st->ctr[sp][threadIdx.x], val);
       sh.ctr[threadIdx.x] = 0ull;
     }
   }
@@ -531,11 +644,12 @@ __device__ void pass_piece(const BatchView& b, int s, long long beg, long long e
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPassBlock) k_pass(BatchView b, int mode, int only) {
+__global__ void __launch_bounds__(kPassBlock, 3) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
   float* Msm = reinterpret_cast<float*>(Ssm + b.nmax + 1);
+  int* queue = reinterpret_cast<int*>(Msm + 2 * (b.nmax + 1));
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
     Ssm[i] = 0ull;
@@ -546,8 +660,10 @@ __global__ void __launch_bounds__(kPassBlock) k_pass(BatchView b, int mode, int 
   if (threadIdx.x == 0) {
     sh.lohi[0] = INT_MAX;
     sh.lohi[1] = -1;
+    sh.qcount = 0;
   }
-  const long long T = seg_prefix(b, mode, only, pre, sh.wsm);
+  // the work is split in quads of particles, equal quads per CTA
+  const long long T = seg_prefix(b, mode, only, pre, sh.wsm, 4);
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -556,17 +672,29 @@ __global__ void __launch_bounds__(kPassBlock) k_pass(BatchView b, int mode, int 
     const long long beg = max(lo, pre[s]) - pre[s];
     const long long end = min(hi, pre[s + 1]) - pre[s];
     if (beg >= end) continue;
-    pass_piece(b, s, beg, end, mode, Ssm, Msm, sh);
+    pass_piece(b, s, beg, end, mode, Ssm, Msm, queue, sh);
   }
 }
 
 // ----------------------------------------------------------------- field
+// 1/D in FP64 from an FP32 seed and two Newton steps (no FP64 division,
+// which is slow on this part); D > 0.
+__device__ __forceinline__ double recip(double D) {
+  double r = (double)__frcp_rn((float)D);
+  r = r * (2.0 - D * r);
+  r = r * (2.0 - D * r);
+  return r;
+}
+
 // Poisson (Eq. 4 in finite-volume form) solved through Gauss's law: with
 // g_n = (phi_{n+1}-phi_n)/dx_n, Eq. 4 reads g_n - g_{n-1} = -Q_n/eps0, so
 // g_n = g_0 - C_n/eps0 with C_n = sum_{m=1..n} Q_m, and the boundary values
 // fix g_0 = (phi_N - phi_0 + sum_n dx_n C_n / eps0) / L.  This is the exact
-// solution of the same tridiagonal system that a Thomas sweep solves, in two
-// parallel scans.  EC field E_j = -g_j (Eq. 5).
+// solution of the same tridiagonal system that a Thomas sweep solves.  The
+// prefix sums of the fixed-point deposit are taken in 64-bit integers (exact),
+// so FP64 enters only once per node and species.  EC field E_j = -g_j (Eq. 5).
+// One CTA per run; the potential and the field energy are formed only on the
+// steps that sample them (and on refresh).
 __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance, int only) {
   const int slot = blockIdx.x;
   if (slot >= b.max_slots) return;
@@ -579,16 +707,34 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
     return;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* Q = reinterpret_cast<double*>(smem_raw);  // N+1
-  double* g = Q + (b.nmax + 1);                     // N+1
+  double* C = reinterpret_cast<double*>(smem_raw);                        // N+1
+  unsigned long long* P = reinterpret_cast<unsigned long long*>(C + b.nmax + 1);  // N+1
   __shared__ double dsm[32];
+  __shared__ unsigned long long usm[32];
+  __shared__ double phi0_sh;
   const int N = R->N, ns = R->ns;
   const int tid = threadIdx.x;
   const long long kn = advance ? st->step + 1 : st->step;
-  const bool sample = advance && R->sample_every > 0 && (kn % R->sample_every) == 0;
+  const int se = R->sample_every;
+  const bool sample = advance && se > 0 && (kn % se) == 0;
+  // the push of level kn samples the energy when (kn + 1) % se == 0
+  const bool want_fe = !advance || (se > 0 && ((kn + 1) % se) == 0);
+  const bool want_phi = !advance || sample;
   const bool periodic = (R->bc == ECPIC_PERIODIC);
-  const double* V = R->V;
   const double* dx = R->dx;
+  constexpr double kInvEps0 = 1.0 / kEps0;
+  constexpr double kInvQe = 1.0 / 1.602176634e-19;
+  constexpr double k2m32 = 2.3283064365386963e-10;  // 2^-32
+
+  if (tid == 0) {
+    double p0 = 0.0;
+    if (!periodic) {
+      const double t = (double)kn * R->dt;
+      const double arg = __dadd_rn(__dmul_rn(__dmul_rn(kTwoPi, R->freq), t), R->phase);
+      p0 = R->vdc + R->v0 * sin(arg);
+    }
+    phi0_sh = p0;
+  }
 
   // sampled moments (Sec. 3a: density and x temperature per node)
   if (sample) {
@@ -599,7 +745,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
         const double* md = R->momd + (size_t)s * 2 * (N + 1);
         double D, M1, M2;
         if (periodic && (n == 0 || n == N)) {
-          D = (double)S[0] + (double)S[N];
+          D = (double)(S[0] + S[N]);
           M1 = md[0] + md[N];
           M2 = md[N + 1] + md[N + 1 + N];
         } else {
@@ -607,14 +753,14 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
           M1 = md[n];
           M2 = md[N + 1 + n];
         }
-        D *= 2.3283064365386963e-10;  // 2^-32
-        const double m = R->sp[s].m;
+        D *= k2m32;
         double T = 0.0;
         if (D > 0.0) {
-          const double a = M1 / D, c2 = M2 / D;
-          T = m * (c2 - a * a) / 1.602176634e-19;
+          const double iD = recip(D);
+          const double a = M1 * iD;
+          T = R->sp[s].m * (M2 * iD - a * a) * kInvQe;
         }
-        acc[(size_t)s * (N + 1) + n] += R->sp[s].w * D / V[n];
+        acc[(size_t)s * (N + 1) + n] += R->sp[s].w * D * R->invV[n];
         acc[(size_t)(ns + s) * (N + 1) + n] += T;
         acc[(size_t)(2 * ns + s) * (N + 1) + n] += D;
         acc[(size_t)(3 * ns + s) * (N + 1) + n] += M1;
@@ -630,78 +776,82 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
       }
   }
 
-  // charge per node control volume from the fixed-point deposit; clear it
-  for (int n = tid; n <= N; n += kFieldBlock) {
-    double q = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      unsigned long long* S = R->S + (size_t)s * (N + 1);
-      const double cw = R->sp[s].q * R->sp[s].w * 2.3283064365386963e-10;
-      q += cw * (double)S[n];
+  // C_n = sum_s q_s w_s 2^-32 * sum_{m=1..n} S_s,m, the integer prefix exact
+  for (int n = tid; n <= N; n += kFieldBlock) C[n] = 0.0;
+  double qtot = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    unsigned long long* S = R->S + (size_t)s * (N + 1);
+    for (int n = tid; n <= N; n += kFieldBlock) {
+      P[n] = (n == 0) ? 0ull : S[n];
+      if (n == 0) usm[31] = S[0];  // node 0 only enters the total
       S[n] = 0ull;
     }
-    Q[n] = q;
+    __syncthreads();
+    const unsigned long long s0 = usm[31];
+    block_incl_scan_array(P, N + 1, usm);
+    const double cw = R->sp[s].q * R->sp[s].w * k2m32;
+    for (int n = tid; n < N; n += kFieldBlock) C[n] += cw * (double)P[n];
+    qtot += cw * (double)(P[N] + s0);
+    __syncthreads();
   }
-  __syncthreads();
-  double phi0 = 0.0;
   if (periodic) {
-    if (tid == 0) Q[0] += Q[N];
+    // uniform neutralising background: Q_n -= V_n Qtot / L
+    const double a = qtot * R->inv_L;
+    for (int n = tid; n < N; n += kFieldBlock) C[n] -= a * R->cumV[n];
     __syncthreads();
-    double loc = 0.0;
-    for (int n = tid; n < N; n += kFieldBlock) loc += Q[n];
-    const double tot = block_sum(loc, dsm);
-    for (int n = tid; n < N; n += kFieldBlock) Q[n] -= V[n] * tot / R->L;
-    __syncthreads();
-  } else {
-    const double t = (double)kn * R->dt;
-    const double arg = __dadd_rn(__dmul_rn(__dmul_rn(kTwoPi, R->freq), t), R->phase);
-    phi0 = R->vdc + R->v0 * sin(arg);
   }
-  // C_n = sum_{m=1..n} Q_m for n = 0..N-1 (C_0 = 0)
-  if (tid == 0) Q[0] = 0.0;
-  __syncthreads();
-  block_incl_scan_array(Q, N, dsm);
+  const double phi0 = phi0_sh;
   double loc = 0.0;
-  for (int n = tid; n < N; n += kFieldBlock) loc += dx[n] * Q[n];
+  for (int n = tid; n < N; n += kFieldBlock) loc += dx[n] * C[n];
   const double A = block_sum(loc, dsm);
-  const double g0 = (0.0 - phi0 + A / kEps0) / R->L;
+  const double g0 = (A * kInvEps0 - phi0) * R->inv_L;
   double fe = 0.0;
+  double* gst = R->g;
   for (int n = tid; n < N; n += kFieldBlock) {
-    const double gn = g0 - Q[n] / kEps0;
-    g[n] = gn;
-    fe += 0.5 * kEps0 * gn * gn * dx[n];
+    const double gn = g0 - C[n] * kInvEps0;
+    C[n] = gn;
+    gst[n] = gn;
+    if (want_fe) fe += gn * gn * dx[n];
   }
   __syncthreads();
   float* E = R->E;
   if (R->scheme == ECPIC_SCHEME_EC) {
-    for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-g[n]);
+    for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-C[n]);
   } else {
+    const double* w = R->mcw;
     for (int n = tid; n <= N; n += kFieldBlock) {
       double e;
       if (n > 0 && n < N) {
-        e = -(g[n] * dx[n] + g[n - 1] * dx[n - 1]) / (dx[n] + dx[n - 1]);
+        e = -(C[n] * w[n] + C[n - 1] * (1.0 - w[n]));
       } else if (periodic) {
-        e = -(g[0] * dx[0] + g[N - 1] * dx[N - 1]) / (dx[0] + dx[N - 1]);
+        e = -(C[0] * w[0] + C[N - 1] * (1.0 - w[0]));
       } else {
-        e = (n == 0) ? -g[0] : -g[N - 1];
+        e = (n == 0) ? -C[0] : -C[N - 1];
       }
       E[n] = (float)e;
     }
   }
-  const double fe_tot = block_sum(fe, dsm);
-  // potential: phi_n = phi_0 + sum_{m<n} g_m dx_m
-  for (int n = tid; n < N; n += kFieldBlock) g[n] *= dx[n];
-  __syncthreads();
-  block_incl_scan_array(g, N, dsm);
-  double* phi = R->phi;
-  for (int n = tid; n <= N; n += kFieldBlock) {
-    double p;
-    if (n == 0) p = phi0;
-    else if (n == N) p = 0.0;
-    else p = phi0 + g[n - 1];
-    phi[n] = p;
-    if (sample) R->acc[(size_t)(5 * ns) * (N + 1) + n] += p;
+  double fe_tot = 0.0;
+  if (want_fe) fe_tot = 0.5 * kEps0 * block_sum(fe, dsm);
+  if (want_phi) {
+    // potential: phi_n = phi_0 + sum_{m<n} g_m dx_m
+    __syncthreads();
+    for (int n = tid; n < N; n += kFieldBlock) C[n] *= dx[n];
+    __syncthreads();
+    block_incl_scan_array(C, N, dsm);
+    double* phi = R->phi;
+    for (int n = tid; n <= N; n += kFieldBlock) {
+      double p;
+      if (n == 0) p = phi0;
+      else if (n == N) p = periodic ? 0.0 : 0.0;
+      else p = phi0 + C[n - 1];
+      phi[n] = p;
+      if (sample) R->acc[(size_t)(5 * ns) * (N + 1) + n] += p;
+    }
   }
   if (tid == 0) {
+    st->phi0 = phi0;
+    st->phi_level = want_phi ? kn : st->phi_level;
     if (sample) {
       st->fe = st->fe_field;
       for (int s = 0; s < ns; ++s) {
@@ -710,7 +860,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
       }
       st->n_samples += 1;
     }
-    st->fe_field = fe_tot;
+    if (want_fe) st->fe_field = fe_tot;
     if (advance) {
       st->step = kn;
       for (int s = 0; s < ns; ++s) {
@@ -722,6 +872,24 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
       }
     }
   }
+}
+
+// potential of the current field of one run from the stored g (host reads)
+__global__ void __launch_bounds__(kFieldBlock) k_phi(BatchView b, int slot) {
+  const RunDev* R = b.runs + slot;
+  if (!R->active) return;
+  RunState* st = b.rst + slot;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* C = reinterpret_cast<double*>(smem_raw);
+  __shared__ double dsm[32];
+  const int N = R->N;
+  for (int n = threadIdx.x; n < N; n += kFieldBlock) C[n] = R->g[n] * R->dx[n];
+  __syncthreads();
+  block_incl_scan_array(C, N, dsm);
+  const double phi0 = st->phi0;
+  for (int n = threadIdx.x; n <= N; n += kFieldBlock)
+    R->phi[n] = (n == 0) ? phi0 : (n == N ? 0.0 : phi0 + C[n - 1]);
+  if (threadIdx.x == 0) st->phi_level = st->step;
 }
 
 // ----------------------------------------------------------------- sort
@@ -968,7 +1136,8 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 // ----------------------------------------------------------------- launchers
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
-         sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1);
+         sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
+         sizeof(int) * (size_t)kQueueCap;
 }
 
 size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }
@@ -995,6 +1164,12 @@ void launch_field(const BatchView& b, int advance, int only, cudaStream_t s) {
   const size_t sm = field_smem_bytes(b);
   set_smem_attr((const void*)k_field, sm);
   k_field<<<b.max_slots, kFieldBlock, sm, s>>>(b, advance, only);
+}
+
+void launch_phi(const BatchView& b, int slot, cudaStream_t s) {
+  const size_t sm = field_smem_bytes(b);
+  set_smem_attr((const void*)k_phi, sm);
+  k_phi<<<1, kFieldBlock, sm, s>>>(b, slot);
 }
 
 void launch_sort(const BatchView& b, int grid, cudaStream_t s) {

@@ -7,7 +7,7 @@
 namespace ecpic {
 
 constexpr int kPassBlock = 256;
-constexpr int kFieldBlock = 256;
+constexpr int kFieldBlock = 512;
 
 struct BatchView {
   const RunDev* runs;   // device, max_slots
@@ -31,6 +31,7 @@ int pass_max_ctas_per_sm(const BatchView& b);
 
 void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s);
 void launch_field(const BatchView& b, int advance, int only, cudaStream_t s);
+void launch_phi(const BatchView& b, int slot, cudaStream_t s);
 void launch_sort(const BatchView& b, int grid, cudaStream_t s);
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s);
 

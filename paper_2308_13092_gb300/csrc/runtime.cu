@@ -32,6 +32,10 @@ size_t layout_bytes(const RunSpec& s) {
   add(8 * (N + 1));       // x
   add(8 * N);             // dx
   add(8 * (N + 1));       // V
+  add(8 * (N + 1));       // invV
+  add(8 * (N + 1));       // mcw
+  add(8 * (N + 1));       // cumV
+  add(8 * N);             // g
   add(4 * N);             // dtdx
   add(4 * N);             // rp
   add(4 * N);             // rm
@@ -121,6 +125,47 @@ void null_rate(const HostSpecies& sp, const RunSpec& s, double* nu_max, uint32_t
 }
 
 size_t run_bytes(const RunSpec& s) { return layout_bytes(s); }
+
+void fill_diag(const Diag& d, const RunSpec& spec, ecpic_diag* out) {
+  const int N = d.N, ns = d.ns;
+  out->step = d.st.step;
+  out->time = (double)d.st.step * spec.dt;
+  out->n_species = ns;
+  out->n_cells = N;
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    out->n_live[s] = s < ns ? d.n_live[s] : 0;
+    out->ke[s] = s < ns ? d.st.ke[s] : 0.0;
+    const unsigned long long* c = d.st.ctr[s];
+    out->absorbed[s][0] = (int64_t)c[C_ABS_L];
+    out->absorbed[s][1] = (int64_t)c[C_ABS_R];
+    out->births[s] = (int64_t)c[C_BIRTHS];
+    out->lost[s] = (int64_t)c[C_LOST];
+    out->candidates[s] = (int64_t)c[C_CAND];
+    out->clamps[s] = (int64_t)c[C_CLAMPS];
+    for (int p = 0; p < kMaxProc; ++p) out->collisions[s][p] = (int64_t)c[C_COLL0 + p];
+  }
+  out->fe = d.st.fe;
+  out->n_samples = d.st.n_samples;
+  const double inv = d.st.n_samples > 0 ? 1.0 / (double)d.st.n_samples : 0.0;
+  const size_t M = (size_t)N + 1;
+  if (d.acc.size() < (size_t)acc_size(ns) * M) return;
+  for (int s = 0; s < ns; ++s)
+    for (size_t n = 0; n < M; ++n) {
+      if (out->density) out->density[s * M + n] = d.acc[s * M + n] * inv;
+      if (out->temp_x) out->temp_x[s * M + n] = d.acc[(ns + s) * M + n] * inv;
+      if (out->temp_x_mom) {
+        const double M0 = d.acc[(2 * ns + s) * M + n];
+        double T = 0.0;
+        if (M0 > 0) {
+          const double a = d.acc[(3 * ns + s) * M + n] / M0, b = d.acc[(4 * ns + s) * M + n] / M0;
+          T = spec.species[s].m * (b - a * a) / kQe;
+        }
+        out->temp_x_mom[s * M + n] = T;
+      }
+    }
+  if (out->phi)
+    for (size_t n = 0; n < M; ++n) out->phi[n] = d.acc[(size_t)(5 * ns) * M + n] * inv;
+}
 
 // ------------------------------------------------------------------ Batch
 Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
@@ -257,6 +302,10 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   double* d_x = cv.take<double>(N + 1);
   double* d_dx = cv.take<double>(N);
   double* d_V = cv.take<double>(N + 1);
+  double* d_invV = cv.take<double>(N + 1);
+  double* d_mcw = cv.take<double>(N + 1);
+  double* d_cumV = cv.take<double>(N + 1);
+  R.g = cv.take<double>(N);
   float* d_dtdx = cv.take<float>(N);
   float* d_rp = cv.take<float>(N);
   float* d_rm = cv.take<float>(N);
@@ -269,12 +318,26 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   R.x = d_x;
   R.dx = d_dx;
   R.V = d_V;
+  R.invV = d_invV;
+  R.mcw = d_mcw;
+  R.cumV = d_cumV;
+  R.inv_L = 1.0 / R.L;
   R.dtdx = d_dtdx;
   R.rp = d_rp;
   R.rm = d_rm;
   cudaMemcpyAsync(d_x, spec.edges.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_dx, dx.data(), 8 * N, cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_V, V.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  std::vector<double> invV(N + 1), mcw(N + 1, 0.5);
+  for (int n = 0; n <= N; ++n) invV[n] = 1.0 / V[n];
+  for (int n = 1; n < N; ++n) mcw[n] = dx[n] / (dx[n - 1] + dx[n]);
+  if (spec.bc == ECPIC_PERIODIC) mcw[0] = mcw[N] = dx[0] / (dx[N - 1] + dx[0]);
+  cudaMemcpyAsync(d_invV, invV.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_mcw, mcw.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  std::vector<double> cumV(N + 1, 0.0);
+  for (int n = 1; n <= N; ++n) cumV[n] = cumV[n - 1] + V[n];
+  cudaMemcpyAsync(d_cumV, cumV.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  cudaMemsetAsync(R.g, 0, 8 * N, stream_);
   cudaMemcpyAsync(d_dtdx, dtdx.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_rp, rp.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_rm, rm.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
@@ -657,7 +720,12 @@ int Batch::get_fields(int slot, double* phi, float* E, std::string* err) {
   int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
   if (rc) return rc;
   const RunDev& R = h_runs_[slot];
-  if (phi) cudaMemcpy(phi, R.phi, 8 * (size_t)(R.N + 1), cudaMemcpyDeviceToHost);
+  if (phi) {
+    launch_phi(view(), slot, stream_);
+    rc = check(cudaStreamSynchronize(stream_), "potential", err);
+    if (rc) return rc;
+    cudaMemcpy(phi, R.phi, 8 * (size_t)(R.N + 1), cudaMemcpyDeviceToHost);
+  }
   if (E)
     cudaMemcpy(E, R.E, 4 * (size_t)(R.scheme == ECPIC_SCHEME_EC ? R.N : R.N + 1),
                cudaMemcpyDeviceToHost);
@@ -704,6 +772,16 @@ int Batch::reset_averages(int slot, int sample_every, std::string* err) {
   for (int s = 0; s < kMaxSpecies; ++s) st.ke_acc[s] = 0.0;
   cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
   return check(cudaStreamSynchronize(stream_), "reset_averages", err);
+}
+
+int Batch::read_states(std::vector<RunState>* out, std::string* err) {
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  out->resize(max_slots_);
+  return check(cudaMemcpy(out->data(), d_rst_, sizeof(RunState) * max_slots_,
+                          cudaMemcpyDeviceToHost),
+               "state read", err);
 }
 
 int Batch::set_step_end(int slot, long long step_end, std::string* err) {

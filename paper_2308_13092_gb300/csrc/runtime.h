@@ -56,6 +56,9 @@ struct Diag {
   int N = 0, ns = 0;
 };
 
+// fill the public diagnostics record from a device snapshot
+void fill_diag(const Diag& d, const RunSpec& spec, ecpic_diag* out);
+
 class Batch {
  public:
   Batch(int device, cudaStream_t stream, int max_slots, int species_per_slot, int nmax);
@@ -83,6 +86,8 @@ class Batch {
   int diag(int slot, Diag* out, std::string* err);
   int reset_averages(int slot, int sample_every, std::string* err);
   int set_step_end(int slot, long long step_end, std::string* err);
+  // synchronise and read every slot's RunState (engine scheduling)
+  int read_states(std::vector<RunState>* out, std::string* err);
   int set_sort_every(int k);
   void set_pass_grid(int g) { pass_grid_override_ = g; invalidate_graphs(); }
   int pass_grid() const { return pass_grid_; }

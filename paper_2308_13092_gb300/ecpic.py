@@ -46,9 +46,38 @@ class ecpic_diag(C.Structure):
     ]
 
 
+class ecpic_process_desc(C.Structure):
+    _fields_ = [("species", C.c_int), ("kind", C.c_int), ("threshold_eV", C.c_double),
+                ("dE_eV", C.c_double), ("n", C.c_int), ("sigma_m2", C.c_void_p),
+                ("product_species", C.c_int)]
+
+
+class ecpic_run_config(C.Structure):
+    _fields_ = [
+        ("edges", C.c_void_p), ("n_edges", C.c_int), ("bc", C.c_int), ("v0", C.c_double),
+        ("freq_hz", C.c_double), ("phase_rad", C.c_double), ("v_dc", C.c_double),
+        ("scheme", C.c_int), ("n_species", C.c_int), ("q", C.c_double * 4), ("m", C.c_double * 4),
+        ("w", C.c_double * 4), ("capacity", C.c_int64 * 4), ("n_init", C.c_int64 * 4),
+        ("T_eV", C.c_double * 4), ("n_gas", C.c_double), ("T_gas", C.c_double),
+        ("m_gas", C.c_double), ("n_proc", C.c_int), ("procs", C.c_void_p), ("seed", C.c_uint64),
+        ("dt", C.c_double), ("sample_every", C.c_int),
+    ]
+
+
 # name -> (restype, argtypes); the exported symbols of include/ecpic.h
 vp, i32, i64, u32, u64, d = C.c_void_p, C.c_int, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
 SIGNATURES = {
+    "ecpic_engine_create": (i32, [C.POINTER(vp), i32, vp, C.c_size_t, i32, i32, i32]),
+    "ecpic_engine_destroy": (None, [vp]),
+    "ecpic_engine_last_error": (C.c_char_p, [vp]),
+    "ecpic_engine_submit": (i32, [vp, C.POINTER(ecpic_run_config), i64, C.POINTER(u64)]),
+    "ecpic_engine_pump": (i32, [vp, i64, C.POINTER(i32), C.POINTER(i32)]),
+    "ecpic_engine_poll": (i32, [vp, u64, C.POINTER(i32), C.POINTER(ecpic_diag), C.POINTER(i64),
+                                C.POINTER(i64)]),
+    "ecpic_engine_release": (i32, [vp, u64]),
+    "ecpic_engine_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
+    "ecpic_engine_tune": (i32, [vp, i32, i32]),
+    "ecpic_engine_profile": (i32, [vp, i64, vp, vp]),
     "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
     "ecpic_destroy": (None, [vp]),
     "ecpic_last_error": (C.c_char_p, [vp]),
@@ -299,3 +328,133 @@ class Run:
             out["Tx"] = arrs["temp_x"].reshape(ns, M)
             out["Tx_mom"] = arrs["temp_x_mom"].reshape(ns, M)
         return out
+
+
+def _diag_arrays(dg, ns, N):
+    M = N + 1
+    arrs = dict(density=np.zeros(ns * M), phi=np.zeros(M), temp_x=np.zeros(ns * M),
+                temp_x_mom=np.zeros(ns * M))
+    for k, a in arrs.items():
+        setattr(dg, k, _p(a))
+    return arrs
+
+
+def _diag_dict(dg, ns, N, arrs=None):
+    out = dict(step=dg.step, time=dg.time, n_samples=dg.n_samples, fe=dg.fe,
+               ke=np.array(dg.ke[:ns]), species=[])
+    for s in range(ns):
+        out["species"].append(dict(
+            n=dg.n_live[s], absorbed_left=dg.absorbed[s][0], absorbed_right=dg.absorbed[s][1],
+            births=dg.births[s], lost=dg.lost[s], candidates=dg.candidates[s],
+            clamps=dg.clamps[s], collisions=list(dg.collisions[s])))
+    if arrs:
+        M = N + 1
+        out["density"] = arrs["density"].reshape(ns, M)
+        out["phi"] = arrs["phi"]
+        out["Tx"] = arrs["temp_x"].reshape(ns, M)
+        out["Tx_mom"] = arrs["temp_x_mom"].reshape(ns, M)
+    return out
+
+
+class Engine:
+    """Batched / served runs on one GPU (ecpic_engine_* of the C ABI)."""
+
+    QUEUED, RESIDENT, FINISHED = 0, 1, 2
+
+    def __init__(self, device=0, stream=None, mem_budget=0, max_slots=256, max_cells=1024,
+                 species_per_run=2):
+        self._L = lib()
+        h = C.c_void_p()
+        rc = self._L.ecpic_engine_create(C.byref(h), device, stream, int(mem_budget), max_slots,
+                                         max_cells, species_per_run)
+        if rc != ECPIC_OK:
+            raise EcpicError(rc, "ecpic_engine_create")
+        self.h = h
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.ecpic_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what):
+        if rc != ECPIC_OK:
+            raise EcpicError(rc, f"{what}: {self._L.ecpic_engine_last_error(self.h).decode()}")
+
+    def submit(self, cfg, n_steps=None):
+        keep = []
+        rc = ecpic_run_config()
+        e = np.ascontiguousarray(cfg.edges, dtype=np.float64)
+        keep.append(e)
+        rc.edges = _p(e)
+        rc.n_edges = e.size
+        rc.bc, rc.v0, rc.freq_hz, rc.phase_rad, rc.v_dc = cfg.bc, cfg.v0, cfg.freq, cfg.phase, cfg.vdc
+        rc.scheme = cfg.scheme
+        rc.n_species = len(cfg.species)
+        for i, s in enumerate(cfg.species):
+            rc.q[i], rc.m[i], rc.w[i] = s.q, s.m, s.w
+            rc.capacity[i], rc.n_init[i], rc.T_eV[i] = s.capacity, s.n0, s.T_eV
+        rc.n_gas = cfg.n_gas if cfg.processes else 0.0
+        rc.T_gas, rc.m_gas = cfg.T_gas, cfg.m_gas
+        procs = (ecpic_process_desc * max(1, len(cfg.processes)))()
+        for i, p in enumerate(cfg.processes):
+            sg = np.ascontiguousarray(p.sigma, dtype=np.float32)
+            keep.append(sg)
+            procs[i] = ecpic_process_desc(p.species, p.kind, p.threshold, p.dE, sg.size, _p(sg),
+                                          p.product)
+        rc.n_proc = len(cfg.processes)
+        rc.procs = C.cast(procs, C.c_void_p)
+        rc.seed, rc.dt, rc.sample_every = int(cfg.seed), cfg.dt, int(cfg.sample_every)
+        t = C.c_uint64()
+        n = int(cfg.n_steps if n_steps is None else n_steps)
+        self._chk(self._L.ecpic_engine_submit(self.h, C.byref(rc), n, C.byref(t)),
+                  "ecpic_engine_submit")
+        self._meta[t.value] = (len(cfg.species), cfg.N)
+        return t.value
+
+    def pump(self, max_steps):
+        r, q = C.c_int(), C.c_int()
+        self._chk(self._L.ecpic_engine_pump(self.h, int(max_steps), C.byref(r), C.byref(q)),
+                  "ecpic_engine_pump")
+        return r.value, q.value
+
+    def poll(self, ticket, diagnostics=False, profiles=False):
+        st = C.c_int()
+        steps, ps = C.c_int64(), C.c_int64()
+        dg = ecpic_diag()
+        ns, N = self._meta.get(ticket, (0, 0))
+        arrs = _diag_arrays(dg, ns, N) if (diagnostics and profiles) else None
+        self._chk(self._L.ecpic_engine_poll(self.h, ticket, C.byref(st),
+                                            C.byref(dg) if diagnostics else None,
+                                            C.byref(steps), C.byref(ps)), "ecpic_engine_poll")
+        out = dict(state=st.value, steps=steps.value, particle_steps=ps.value)
+        if diagnostics and st.value == self.FINISHED:
+            out["diag"] = _diag_dict(dg, ns, N, arrs)
+        return out
+
+    def release(self, ticket):
+        self._chk(self._L.ecpic_engine_release(self.h, ticket), "ecpic_engine_release")
+        self._meta.pop(ticket, None)
+
+    def stats(self):
+        ps, rf, by = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(self._L.ecpic_engine_stats(self.h, C.byref(ps), C.byref(rf), C.byref(by)),
+                  "ecpic_engine_stats")
+        return dict(particle_steps=ps.value, runs_finished=rf.value, bytes_resident=by.value)
+
+    def profile(self, n):
+        ms = np.zeros(3)
+        cnt = np.zeros(3, np.int64)
+        self._chk(self._L.ecpic_engine_profile(self.h, int(n), _p(ms), _p(cnt)),
+                  "ecpic_engine_profile")
+        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], launches=cnt.tolist())
+
+    def tune(self, pass_ctas=0, sort_every=16):
+        self._chk(self._L.ecpic_engine_tune(self.h, int(pass_ctas), int(sort_every)),
+                  "ecpic_engine_tune")
