@@ -255,6 +255,10 @@ int ecpic_doubling_grid(int n_ref, double L, double L_buff, int dx_min, int dx_m
  * Particles with cell < 0 are skipped.  Async on cuda_stream. */
 int ecpic_deposit_device(int N, int64_t n, const int32_t* d_cell, const float* d_xi,
                          uint64_t* d_S, void* cuda_stream);
+/* Bounds-check record of a library built with -DECPIC_CHECKS: out[0] = first
+ * failing check site (0 = none), out[1] = its index, out[2] = its bound,
+ * out[3] = number of failed checks.  Plain builds report zeros. */
+int ecpic_debug_checks(int64_t* out4);
 /* Philox4x32-10 on the device: out[4i..4i+3] = Philox(counter = ctr[4i..],
  * key = key[2i..]) for i < n.  All pointers device.  Async. */
 int ecpic_philox_device(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key,

@@ -53,6 +53,8 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     extra = list(extra or [])
+    if os.environ.get("ECPIC_CHECKS") == "1":
+        extra.append("-DECPIC_CHECKS")
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

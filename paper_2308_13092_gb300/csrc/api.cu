@@ -372,6 +372,14 @@ int ecpic_deposit_device(int N, int64_t n, const int32_t* d_cell, const float* d
   return cudaGetLastError() == cudaSuccess ? ECPIC_OK : ECPIC_ERR_CUDA;
 }
 
+int ecpic_debug_checks(int64_t* out) {
+  if (!out) return ECPIC_ERR_ARG;
+  unsigned long long v[4] = {0, 0, 0, 0};
+  ecpic::read_checks(v);
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
+  return cudaGetLastError() == cudaSuccess ? ECPIC_OK : ECPIC_ERR_CUDA;
+}
+
 int ecpic_philox_device(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out,
                         void* stream) {
   if (n < 0 || (n > 0 && (!d_ctr || !d_key || !d_out))) return ECPIC_ERR_ARG;

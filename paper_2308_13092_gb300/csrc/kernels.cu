@@ -17,7 +17,28 @@
 
 namespace ecpic {
 
+// Checked builds (-DECPIC_CHECKS): indexed accesses are validated against
+// their bounds; the first violation (site, index, bound) and a violation count
+// are recorded and the access is skipped.  Plain builds compile the checks
+// away.
+__device__ unsigned long long g_check[4];
+
 namespace {
+
+#ifdef ECPIC_CHECKS
+__device__ __noinline__ bool chk(bool ok, int where, long long idx, long long bound) {
+  if (!ok) {
+    if (atomicCAS(&g_check[0], 0ull, (unsigned long long)where) == 0ull) {
+      g_check[1] = (unsigned long long)idx;
+      g_check[2] = (unsigned long long)bound;
+    }
+    atomicAdd(&g_check[3], 1ull);
+  }
+  return ok;
+}
+#else
+__device__ __forceinline__ bool chk(bool, int, long long, long long) { return true; }
+#endif
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr double kEps0 = 8.8541878128e-12;
@@ -142,7 +163,9 @@ __device__ __forceinline__ int seg_find(const long long* pre, int nseg, long lon
 // Warp-aggregated fixed-point CIC deposit into shared memory: lanes that hold
 // the same cell add their shares once.  S[c] += 2^32 - r, S[c+1] += r with
 // r = floor(xi * 2^32) (xi * 2^32 is exact in FP32; rz truncation = floor).
-__device__ __forceinline__ void deposit_warp(unsigned long long* Ssm, bool valid, int c, float f) {
+__device__ __forceinline__ void deposit_warp(unsigned long long* Ssm, bool valid, int c, float f,
+                                             int nmax) {
+  valid = valid && chk(c >= 0 && c < nmax, 1, c, nmax);
   const unsigned key = valid ? (unsigned)c : 0xFFFFFFFFu;
   const unsigned grp = __match_any_sync(kFull, key);
   if (!valid) return;
@@ -170,6 +193,7 @@ __device__ __forceinline__ float sigma_at(const float* tab, float thr, float E, 
   const float fi = floorf(u);
   if (fi >= (float)(n - 1)) return __ldg(tab + n - 1);
   const int i = (int)fi;
+  if (!chk(i >= 0 && i + 1 < n, 17, i, n)) return 0.f;
   const float t = u - fi;
   const float s0 = __ldg(tab + i), s1 = __ldg(tab + i + 1);
   return s0 + t * (s1 - s0);
@@ -260,7 +284,9 @@ __device__ void collide_candidate(const BatchView& b, const RunDev* R, RunState*
                                   PassShared& sh) {
   const SpeciesDev* SP = &R->sp[sp];
   const uint64_t seed = R->seed;
+  if (!chk(i >= 0 && i < G.cap, 6, i, G.cap)) return;
   const int c = G.cell[cur][i];
+  if (!chk(c >= 0 && c < N, 7, c, N)) return;
   const float f = G.xi[cur][i];
   float vx = G.vx[cur][i], vy = G.vy[cur][i], vz = G.vz[cur][i];
   const uint64_t id = G.id[cur][i];
@@ -350,6 +376,7 @@ __device__ void collide_candidate(const BatchView& b, const RunDev* R, RunState*
       }
       // ion: the product species' segment, deposited straight to HBM
       const int ps = SP->proc[chosen].product_seg;
+      if (!chk(ps >= 0 && ps < b.nseg, 18, ps, b.nseg)) return;
       const int pspec = SP->proc[chosen].product_species;
       const float ivx = sd * z0;
       if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
@@ -400,6 +427,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   const int N = R->N, scheme = R->scheme, bc = R->bc, uniform = R->uniform;
   const int cur = ss->cur;
   const long long n = ss->n_proc;
+  if (!chk(n <= G.cap && N <= b.nmax && (cur == 0 || cur == 1), 14, n, G.cap)) return;
   int32_t* pc = G.cell[cur];
   float* pxi = G.xi[cur];
   float* pvx = G.vx[cur];
@@ -430,8 +458,8 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   for (long long base = qbeg; base < qend; base += kPassBlock) {
     const long long q = base + (long long)threadIdx.x;
     const long long i0 = 4 * q;
-    const bool inq = q < qend;
-    const bool full = inq && (i0 + 3 < n);
+    const bool inq = q < qend && chk(i0 < G.cap, 2, i0, G.cap);
+    const bool full = inq && (i0 + 3 < n) && chk(i0 + 3 < G.cap, 3, i0 + 3, G.cap);
     int c[4];
     float f[4], v[4];
     if (full) {
@@ -474,10 +502,18 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (c[j] < 0) continue;
+        if (!chk(c[j] < N, 4, c[j], N)) {
+          c[j] = -1;
+          continue;
+        }
         int cj = c[j];
         float fj = f[j];
         // gather: face field of the cell (EC) or CIC of node fields (MC)
         float Ei;
+        if (!chk(cj >= 0 && cj + (scheme == ECPIC_SCHEME_EC ? 0 : 1) <= N - (scheme == ECPIC_SCHEME_EC ? 1 : 0), 16, cj, N)) {
+          c[j] = -1;
+          continue;
+        }
         if (scheme == ECPIC_SCHEME_EC) {
           Ei = __ldg(E + cj);
         } else {
@@ -543,7 +579,8 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const unsigned m = __ballot_sync(kFull, cand[j]);
-          if (cand[j]) wq[wcount + __popc(m & ((1u << lane) - 1u))] = (int)(i0 + j);
+          const int slotq = wcount + __popc(m & ((1u << lane) - 1u));
+          if (cand[j] && chk(slotq < kWarpQ, 5, slotq, kWarpQ)) wq[slotq] = (int)(i0 + j);
           wcount += __popc(m);
           ncand += cand[j] ? 1u : 0u;
         }
@@ -553,11 +590,11 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const bool val = c[j] >= 0;
-      deposit_warp(Ssm, val, c[j], f[j]);
+      deposit_warp(Ssm, val, c[j], f[j], b.nmax);
       if (val) {
         my_lo = min(my_lo, c[j]);
         my_hi = max(my_hi, c[j] + 1);
-        if (sample && !cand[j]) {
+        if (sample && !cand[j] && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
           atomicAdd(Msm + c[j], (1.0f - f[j]) * v[j]);
           atomicAdd(Msm + c[j] + 1, f[j] * v[j]);
           atomicAdd(Msm + Nm + c[j], (1.0f - f[j]) * v[j] * v[j]);
@@ -567,11 +604,12 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
     }
     while (mcc && wcount >= 32) {
       __syncwarp();
-      collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
+      if (chk(wcount <= kWarpQ, 21, wcount, kWarpQ))
+        collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
       const int rest = wcount - 32;
       for (int r = 0; r < (rest + 31) / 32; ++r) {
         const int e = lane + 32 * r;
-        const int val = e < rest ? wq[e + 32] : 0;
+        const int val = (e < rest && chk(e + 32 < kWarpQ, 15, e + 32, kWarpQ)) ? wq[e + 32] : 0;
         __syncwarp();
         if (e < rest) wq[e] = val;
         __syncwarp();
@@ -581,7 +619,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   }
   if (mcc && wcount > 0) {
     __syncwarp();
-    if (lane < wcount)
+    if (lane < wcount && chk(wcount <= kWarpQ, 22, wcount, kWarpQ))
       collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
     __syncwarp();
   }
@@ -607,10 +645,13 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
     if (threadIdx.x == 0) atomicAdd(&st->ke_acc[sp], 0.5 * SP->m * SP->w * kes);
   }
   __syncthreads();
-  const int flo = sh.lohi[0], fhi = sh.lohi[1];
+  const int flo = sh.lohi[0], fhi = chk(sh.lohi[1] <= N, 8, sh.lohi[1], N) ? sh.lohi[1] : N;
   unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   double* md = R->momd + (size_t)sp * 2 * (N + 1);
-  for (int nn = flo + (int)threadIdx.x; nn <= fhi; nn += kPassBlock) {
+  // an empty range (no live particle in the piece) is (INT_MAX, -1): skip it
+  // before forming flo + threadIdx.x, which would overflow
+  const int nbeg = flo <= fhi ? flo + (int)threadIdx.x : fhi + 1;
+  for (int nn = nbeg; nn <= fhi; nn += kPassBlock) {
     const unsigned long long val = Ssm[nn];
     if (val) {
       atomicAdd(Sg + nn, val);
@@ -672,6 +713,7 @@ __global__ void __launch_bounds__(kPassBlock, 3) k_pass(BatchView b, int mode, i
     const long long beg = max(lo, pre[s]) - pre[s];
     const long long end = min(hi, pre[s + 1]) - pre[s];
     if (beg >= end) continue;
+    if (!chk(b.segs[s].run >= 0 && b.segs[s].run < b.max_slots, 23, s, b.nseg)) continue;
     pass_piece(b, s, beg, end, mode, Ssm, Msm, queue, sh);
   }
 }
@@ -924,7 +966,7 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
       if (c >= Nr) c = -1;
       const unsigned grp = __match_any_sync(kFull, c >= 0 ? (unsigned)c : 0xFFFFFFFFu);
       if (c >= 0) {
-        if (lane == __ffs(grp) - 1) atomicAdd(H + c, __popc(grp));
+        if (lane == __ffs(grp) - 1 && chk(c <= b.nmax, 9, c, b.nmax)) atomicAdd(H + c, __popc(grp));
         my_lo = min(my_lo, c);
         my_hi = max(my_hi, c);
       }
@@ -940,7 +982,8 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
     }
     __syncthreads();
     const int flo = lohi[0], fhi = lohi[1];
-    for (int n = flo + (int)threadIdx.x; n <= fhi; n += kPassBlock) {
+    const int nbeg = flo <= fhi ? flo + (int)threadIdx.x : fhi + 1;  // empty range: skip
+    for (int n = nbeg; n <= fhi; n += kPassBlock) {
       const int v = H[n];
       if (v) {
         atomicAdd(b.hist + G.hoff + n, v);
@@ -1010,6 +1053,7 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
         if (lane == leader) basepos = atomicAdd(cursor + c, __popc(grp));
         basepos = __shfl_sync(grp, basepos, leader);
         const long long j = (long long)basepos + __popc(grp & lt);
+        if (!chk(j >= 0 && j < G.cap && i < G.cap, 10, j, G.cap)) continue;
         G.cell[dst][j] = c;
         G.xi[dst][j] = G.xi[src][i];
         G.vx[dst][j] = G.vx[src][i];
@@ -1085,6 +1129,7 @@ __global__ void k_init(BatchView b, int slot, InitParams p) {
     const double aa = __dmul_rn(kTwoPi, u2a), ab = __dmul_rn(kTwoPi, u2b);
     const double z0 = __dmul_rn(ra, cos(aa)), z1 = __dmul_rn(ra, sin(aa));
     const double z2 = __dmul_rn(rb, cos(ab));
+    if (!chk(i < G.cap && c >= 0 && c < N, 11, i, G.cap)) continue;
     G.cell[cur][i] = c;
     G.xi[cur][i] = f;
     G.vx[cur][i] = __double2float_rn(__dmul_rn(sd, z0));
@@ -1109,7 +1154,7 @@ __global__ void __launch_bounds__(kPassBlock) k_deposit_device(int N, long long 
     int c = i < n ? cell[i] : -1;
     const bool valid = c >= 0 && c < N;
     const float f = valid ? xi[i] : 0.0f;
-    deposit_warp(Ssm, valid, c, f);
+    deposit_warp(Ssm, valid, c, f, N);
   }
   __syncthreads();
   for (int i = threadIdx.x; i <= N; i += kPassBlock) {
@@ -1172,14 +1217,23 @@ void launch_phi(const BatchView& b, int slot, cudaStream_t s) {
   k_phi<<<1, kFieldBlock, sm, s>>>(b, slot);
 }
 
+void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s) {
+  if (phase == 0) {
+    const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
+    set_smem_attr((const void*)k_hist, smh);
+    k_hist<<<grid, kPassBlock, smh, s>>>(b);
+  } else if (phase == 1) {
+    k_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
+  } else if (phase == 2) {
+    const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
+    k_scatter<<<grid, kPassBlock, sms, s>>>(b);
+  } else {
+    k_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
+  }
+}
+
 void launch_sort(const BatchView& b, int grid, cudaStream_t s) {
-  const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
-  set_smem_attr((const void*)k_hist, smh);
-  k_hist<<<grid, kPassBlock, smh, s>>>(b);
-  k_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
-  const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
-  k_scatter<<<grid, kPassBlock, sms, s>>>(b);
-  k_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
+  for (int ph = 0; ph < 4; ++ph) launch_sort_phase(b, grid, ph, s);
 }
 
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s) {
@@ -1209,4 +1263,10 @@ void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key,
   k_philox_device<<<(unsigned)blocks, 256, 0, s>>>(n, ctr, key, out);
 }
 
+}  // namespace ecpic
+
+namespace ecpic {
+void read_checks(unsigned long long out[4]) {
+  cudaMemcpyFromSymbol(out, g_check, sizeof(unsigned long long) * 4);
+}
 }  // namespace ecpic

@@ -33,10 +33,12 @@ void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t 
 void launch_field(const BatchView& b, int advance, int only, cudaStream_t s);
 void launch_phi(const BatchView& b, int slot, cudaStream_t s);
 void launch_sort(const BatchView& b, int grid, cudaStream_t s);
+void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s);
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s);
 
 void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
                            unsigned long long* S, cudaStream_t s);
+void read_checks(unsigned long long out[4]);
 void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s);
 

@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 namespace ecpic {
@@ -547,15 +549,30 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
   double acc[3] = {0, 0, 0};
   long long cnt[3] = {0, 0, 0};
   int rc = ECPIC_OK;
+  // ECPIC_SYNC_PHASES=1: wait after every kernel so a device error names it
+  const char* sp = std::getenv("ECPIC_SYNC_PHASES");
+  const bool each = sp && sp[0] == '1';
   for (long long t = 0; t < n && rc == ECPIC_OK; ++t) {
     cudaEventRecord(ev[0], stream_);
     launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
     cudaEventRecord(ev[1], stream_);
+    if (each && (rc = check(cudaEventSynchronize(ev[1]), "pass kernel", err))) break;
     launch_field(b, 1, -1, stream_);
     cudaEventRecord(ev[2], stream_);
+    if (each && (rc = check(cudaEventSynchronize(ev[2]), "field kernel", err))) break;
     const bool sort = ++since_sort_ >= sort_every_;
     if (sort) {
-      launch_sort(b, pass_grid_, stream_);
+      if (each) {
+        static const char* names[4] = {"sort histogram", "sort scan", "sort scatter",
+                                       "sort finalize"};
+        for (int ph = 0; ph < 4 && rc == ECPIC_OK; ++ph) {
+          launch_sort_phase(b, pass_grid_, ph, stream_);
+          rc = check(cudaStreamSynchronize(stream_), names[ph], err);
+        }
+        if (rc) break;
+      } else {
+        launch_sort(b, pass_grid_, stream_);
+      }
       since_sort_ = 0;
     }
     cudaEventRecord(ev[3], stream_);

@@ -102,6 +102,7 @@ SIGNATURES = {
     "ecpic_doubling_grid": (i32, [i32, d, d, i32, i32, vp, i32]),
     "ecpic_deposit_device": (i32, [i32, i64, vp, vp, vp, vp]),
     "ecpic_philox_device": (i32, [i64, vp, vp, vp, vp]),
+    "ecpic_debug_checks": (i32, [vp]),
 }
 
 _lock = threading.Lock()
