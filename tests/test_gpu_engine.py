@@ -4,8 +4,10 @@ Each run's trajectory depends only on its own state: random numbers are keyed
 on (particle id, step) and the deposit is an integer sum, so a run gives the
 same counters (absorptions, births, collisions per process, candidates) and
 particle counts alone, through the single-run API, and in a mix of uneven
-runs; its averaged profiles agree to FP64 rounding (they are summed with
-floating-point atomics)."""
+runs.  Its averaged density (from the integer deposit) and potential (FP64
+field solve of that deposit) agree to FP64 rounding; the temperature is built
+from FP32 velocity moments summed with atomics in thread order, so it agrees
+to FP32 rounding."""
 import numpy as np
 import pytest
 
@@ -58,8 +60,8 @@ def test_run_alone_equals_run_in_mix():
         assert a["step"] == m["step"] == cfgs[i].n_steps
         assert _key(a) == _key(m)
         assert alone[0]["particle_steps"] == mix[i]["particle_steps"]
-        for k in ("density", "Tx", "phi"):
-            np.testing.assert_allclose(a[k], m[k], rtol=1e-9, atol=1e-12 * np.abs(m[k]).max())
+        for k, tol in (("density", 1e-12), ("phi", 1e-9), ("Tx", 2e-5)):
+            np.testing.assert_allclose(a[k], m[k], rtol=tol, atol=tol * np.abs(m[k]).max())
 
 
 def test_engine_equals_single_run_api():
@@ -86,9 +88,10 @@ def test_memory_budget_admission():
     probe = ecpic.Engine(max_slots=1, max_cells=1024)
     probe.submit(big)
     probe.pump(0)
-    budget = int(2.5 * probe.stats()["bytes_resident"])
+    budget = int(1.5 * probe.stats()["bytes_resident"])
     probe.close()
     eng = ecpic.Engine(max_slots=6, max_cells=1024, mem_budget=budget)
+    cfgs = [big] * 4 + cfgs   # four copies of the largest cannot be resident together
     tickets = [eng.submit(c) for c in cfgs]
     seen_queue = False
     for _ in range(300):
@@ -107,6 +110,7 @@ def test_failing_run_is_isolated():
     bad = cfgs[1]
     for sp in bad.species:
         sp.capacity = sp.n0 + 2
+    bad.species[0].T_eV = 60.0   # hot electrons ionise from the first step
     bad.n_gas *= 50
     out, _ = _run_engine(cfgs)
     assert out[1]["state"] == ecpic.ECPIC_ERR_CAPACITY
