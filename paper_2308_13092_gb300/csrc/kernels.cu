@@ -278,7 +278,7 @@ struct PassShared {
 // pushed, L2-resident), redraws Philox block A, picks the process and
 // scatters.  Ionisation appends the secondary electron to this segment and
 // the ion to its species' segment, and deposits both.
-__device__ void collide_candidate(const BatchView& b, const RunDev* R, RunState* st, const SegDev& G,
+__device__ __noinline__ void collide_candidate(const BatchView& b, const RunDev* R, RunState* st, const SegDev& G,
                                   SegState* ss, int sp, int cur, long long i, long long k, int N,
                                   int Nm, bool sample, unsigned long long* Ssm, float* Msm,
                                   PassShared& sh) {
@@ -499,37 +499,47 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         for (int j = 0; j < 4; ++j)
           if (c[j] >= 0) yz[j] = pvy[i0 + j] * pvy[i0 + j] + pvz[i0 + j] * pvz[i0 + j];
       }
+      // gather (Eq. 6-7; CIC for MC) and push (Eq. 8), branch-free over the
+      // four particles so the loads and arithmetic overlap
+      float Ei[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool ok = c[j] >= 0 && chk(c[j] < N, 4, c[j], N);
+        if (!ok) c[j] = -1;
+        const int cc = ok ? c[j] : 0;
+        if (scheme == ECPIC_SCHEME_EC) {
+          Ei[j] = __ldg(E + cc);
+        } else {
+          const float e0 = __ldg(E + cc), e1 = __ldg(E + cc + 1);
+          Ei[j] = e0 + f[j] * (e1 - e0);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float vnew = v[j] + qm_dt * Ei[j];
+        if (sample && c[j] >= 0) ke += v[j] * vnew + yz[j];
+        v[j] = vnew;
+      }
+      // the Philox candidate draws of all four: independent chains the
+      // scheduler interleaves (the test does not depend on position)
+      uint32_t r0[4] = {0u, 0u, 0u, 0u};
+      if (mcc) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r0[j] = draw(seed, id[j], (uint32_t)k, (uint32_t)sp << 8).x;
+      }
+      // Eq. 9 in cell units, then the walls
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (c[j] < 0) continue;
-        if (!chk(c[j] < N, 4, c[j], N)) {
-          c[j] = -1;
-          continue;
-        }
-        int cj = c[j];
-        float fj = f[j];
-        // gather: face field of the cell (EC) or CIC of node fields (MC)
-        float Ei;
-        if (!chk(cj >= 0 && cj + (scheme == ECPIC_SCHEME_EC ? 0 : 1) <= N - (scheme == ECPIC_SCHEME_EC ? 1 : 0), 16, cj, N)) {
-          c[j] = -1;
-          continue;
-        }
-        if (scheme == ECPIC_SCHEME_EC) {
-          Ei = __ldg(E + cj);
-        } else {
-          const float e0 = __ldg(E + cj), e1 = __ldg(E + cj + 1);
-          Ei = e0 + fj * (e1 - e0);
-        }
-        const float vnew = v[j] + qm_dt * Ei;  // Eq. 8
-        if (sample) ke += v[j] * vnew + yz[j];
-        v[j] = vnew;
+        const float vnew = v[j];
         if (!(fabsf(vnew) < 3.0e8f)) {
           atomicAdd(&sh.ctr[C_NAN], 1ull);
           set_status(st, ECPIC_ERR_NAN);
           c[j] = -1;
           continue;
         }
-        // Eq. 9 in cell units
+        int cj = c[j];
+        float fj = f[j];
         if (uniform) {
           float g = fj + vnew * dtdx_u;
           if (!(g >= 0.0f && g < 1.0f)) {
@@ -557,10 +567,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         }
         c[j] = cj;
         f[j] = fj;
-        if (mcc) {
-          const uint4 A = draw(seed, id[j], (uint32_t)k, (uint32_t)sp << 8);
-          cand[j] = (A.x >> 8) < thr24;
-        }
+        if (mcc) cand[j] = (r0[j] >> 8) < thr24;
       }
       if (full) {
         *reinterpret_cast<int4*>(pc + i0) = make_int4(c[0], c[1], c[2], c[3]);
@@ -685,7 +692,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPassBlock, 3) k_pass(BatchView b, int mode, int only) {
+__global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
@@ -946,7 +953,8 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
     lohi[0] = INT_MAX;
     lohi[1] = -1;
   }
-  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm);
+  // quads of four particles per thread, as in the pass
+  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm, 4);
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -958,17 +966,28 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
     if (beg >= end) continue;
     const SegDev& G = b.segs[s];
     const int32_t* pc = G.cell[b.sst[s].cur];
+    const long long n = b.sst[s].n_proc;
     const int Nr = b.runs[G.run].N;
     int my_lo = INT_MAX, my_hi = -1;
     for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
-      const long long i = base + lane;
-      int c = i < end ? pc[i] : -1;
-      if (c >= Nr) c = -1;
-      const unsigned grp = __match_any_sync(kFull, c >= 0 ? (unsigned)c : 0xFFFFFFFFu);
-      if (c >= 0) {
-        if (lane == __ffs(grp) - 1 && chk(c <= b.nmax, 9, c, b.nmax)) atomicAdd(H + c, __popc(grp));
-        my_lo = min(my_lo, c);
-        my_hi = max(my_hi, c);
+      const long long i0 = 4 * (base + lane);
+      int c[4];
+      if (base + lane < end && i0 + 3 < n && chk(i0 + 3 < G.cap, 26, i0, G.cap)) {
+        const int4 c4 = *reinterpret_cast<const int4*>(pc + i0);
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = (base + lane < end && i0 + j < n) ? pc[i0 + j] : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = c[j] < Nr ? c[j] : -1;
+        const unsigned grp = __match_any_sync(kFull, cj >= 0 ? (unsigned)cj : 0xFFFFFFFFu);
+        if (cj >= 0) {
+          if (lane == __ffs(grp) - 1 && chk(cj <= b.nmax, 9, cj, b.nmax)) atomicAdd(H + cj, __popc(grp));
+          my_lo = min(my_lo, cj);
+          my_hi = max(my_hi, cj);
+        }
       }
     }
 #pragma unroll
@@ -1027,7 +1046,9 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   __shared__ long long wsm[32];
-  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm);
+  // quads of four particles per thread; every field is loaded before the
+  // cursor atomics so the loads overlap
+  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm, 4);
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -1040,26 +1061,64 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
     if (beg >= end) continue;
     const SegDev& G = b.segs[s];
     const int src = b.sst[s].cur, dst = src ^ 1;
+    const long long n = b.sst[s].n_proc;
     int* cursor = b.hist + G.hoff;
     const int Nr = b.runs[G.run].N;
+    const int32_t* sc = G.cell[src];
+    const float* sx = G.xi[src];
+    const float* su = G.vx[src];
+    const float* sv = G.vy[src];
+    const float* sw = G.vz[src];
+    const uint64_t* si = G.id[src];
     for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
-      const long long i = base + lane;
-      int c = i < end ? G.cell[src][i] : -1;
-      if (c >= Nr) c = -1;
-      const unsigned grp = __match_any_sync(kFull, c >= 0 ? (unsigned)c : 0xFFFFFFFFu);
-      if (c >= 0) {
-        const int leader = __ffs(grp) - 1;
-        int basepos = 0;
-        if (lane == leader) basepos = atomicAdd(cursor + c, __popc(grp));
-        basepos = __shfl_sync(grp, basepos, leader);
-        const long long j = (long long)basepos + __popc(grp & lt);
-        if (!chk(j >= 0 && j < G.cap && i < G.cap, 10, j, G.cap)) continue;
-        G.cell[dst][j] = c;
-        G.xi[dst][j] = G.xi[src][i];
-        G.vx[dst][j] = G.vx[src][i];
-        G.vy[dst][j] = G.vy[src][i];
-        G.vz[dst][j] = G.vz[src][i];
-        G.id[dst][j] = G.id[src][i];
+      const long long i0 = 4 * (base + lane);
+      int c[4];
+      float x[4], u[4], v[4], w[4];
+      uint64_t id[4];
+      if (base + lane < end && i0 + 3 < n && chk(i0 + 3 < G.cap, 27, i0, G.cap)) {
+        const int4 c4 = *reinterpret_cast<const int4*>(sc + i0);
+        const float4 x4 = *reinterpret_cast<const float4*>(sx + i0);
+        const float4 u4 = *reinterpret_cast<const float4*>(su + i0);
+        const float4 v4 = *reinterpret_cast<const float4*>(sv + i0);
+        const float4 w4 = *reinterpret_cast<const float4*>(sw + i0);
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(si + i0);
+        const ulonglong2 a2 = *reinterpret_cast<const ulonglong2*>(si + i0 + 2);
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        x[0] = x4.x; x[1] = x4.y; x[2] = x4.z; x[3] = x4.w;
+        u[0] = u4.x; u[1] = u4.y; u[2] = u4.z; u[3] = u4.w;
+        v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
+        w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
+        id[0] = a.x; id[1] = a.y; id[2] = a2.x; id[3] = a2.y;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = base + lane < end && i0 + j < n;
+          c[j] = in ? sc[i0 + j] : -1;
+          x[j] = in ? sx[i0 + j] : 0.f;
+          u[j] = in ? su[i0 + j] : 0.f;
+          v[j] = in ? sv[i0 + j] : 0.f;
+          w[j] = in ? sw[i0 + j] : 0.f;
+          id[j] = in ? si[i0 + j] : 0ull;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = c[j] < Nr ? c[j] : -1;
+        const unsigned grp = __match_any_sync(kFull, cj >= 0 ? (unsigned)cj : 0xFFFFFFFFu);
+        if (cj >= 0) {
+          const int leader = __ffs(grp) - 1;
+          int basepos = 0;
+          if (lane == leader) basepos = atomicAdd(cursor + cj, __popc(grp));
+          basepos = __shfl_sync(grp, basepos, leader);
+          const long long d = (long long)basepos + __popc(grp & lt);
+          if (!chk(d >= 0 && d < G.cap, 10, d, G.cap)) continue;
+          G.cell[dst][d] = cj;
+          G.xi[dst][d] = x[j];
+          G.vx[dst][d] = u[j];
+          G.vy[dst][d] = v[j];
+          G.vz[dst][d] = w[j];
+          G.id[dst][d] = id[j];
+        }
       }
     }
   }
