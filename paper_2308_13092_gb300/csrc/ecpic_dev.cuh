@@ -34,7 +34,6 @@ enum Ctr {
 struct ProcDev {
   int kind;
   float thr;             // eV
-  const float* sigma;    // device table, m^2
   int product_seg;       // ionisation: segment of the ion species in this run
   int product_species;
 };
@@ -53,6 +52,11 @@ struct SpeciesDev {
   int ntab;
   int nproc;
   int heavy;            // samples the target neutral's velocity
+  int np4;              // groups of four processes per table node: (nproc + 3) / 4
+  // cross sections (m^2) of all processes interleaved by node: entry
+  // [node * np4 + g] holds processes 4g..4g+3 (zero past nproc)
+  const float4* sig4;
+  float thr_all[kMaxProc];  // thresholds (eV), FLT_MAX past nproc
   ProcDev proc[kMaxProc];
 };
 

@@ -187,16 +187,39 @@ __device__ __forceinline__ void deposit_one(unsigned long long* S, int c, float 
 }
 
 // ----------------------------------------------------------------- MCC helpers
-__device__ __forceinline__ float sigma_at(const float* tab, float thr, float E, float dE_inv, int n) {
-  if (E < thr) return 0.f;
-  const float u = E * dE_inv;
+// Collision frequencies nu_p = n_g sigma_p(E) |g| of a species' processes, in
+// process order, from its node-interleaved table: linear interpolation
+// between nodes dE apart, the last node's value past the table, zero below a
+// process threshold.  Returns the first p whose running sum exceeds Rr (the
+// selection of Sec. 2a step 6; -1 for a null collision) and the total in *tot.
+__device__ __forceinline__ int select_process(const SpeciesDev* SP, float E, float gm, float ng,
+                                              float Rr, float* tot) {
+  const int n = SP->ntab, np4 = SP->np4;
+  const float u = E * SP->dE_inv;
   const float fi = floorf(u);
-  if (fi >= (float)(n - 1)) return __ldg(tab + n - 1);
-  const int i = (int)fi;
-  if (!chk(i >= 0 && i + 1 < n, 17, i, n)) return 0.f;
-  const float t = u - fi;
-  const float s0 = __ldg(tab + i), s1 = __ldg(tab + i + 1);
-  return s0 + t * (s1 - s0);
+  const bool top = fi >= (float)(n - 1);
+  int i = top ? n - 1 : (int)fi;
+  if (!chk(i >= 0 && i < n, 17, i, n)) i = 0;
+  const int i1 = top ? i : i + 1;
+  const float t = top ? 0.0f : u - fi;
+  const float4* tab = SP->sig4;
+  float cum = 0.0f;
+  int chosen = -1;
+  for (int g = 0; g < np4; ++g) {
+    const float4 a = __ldg(tab + (size_t)i * np4 + g);
+    const float4 b = __ldg(tab + (size_t)i1 * np4 + g);
+    const float sg[4] = {a.x + t * (b.x - a.x), a.y + t * (b.y - a.y), a.z + t * (b.z - a.z),
+                         a.w + t * (b.w - a.w)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = 4 * g + q;
+      const float sig = E < SP->thr_all[p] ? 0.0f : sg[q];
+      cum += ng * sig * gm;
+      if (chosen < 0 && Rr < cum) chosen = p;
+    }
+  }
+  *tot = cum;
+  return chosen;
 }
 
 __device__ __forceinline__ void box_muller(float u1, float u2, float& z0, float& z1) {
@@ -262,8 +285,8 @@ __device__ __forceinline__ void walk_nonuniform(int& c, float& f, float g, int N
   f = g;
 }
 
-constexpr int kQueueCap = 2048;  // collision-candidate queue per CTA (all warps)
-constexpr int kWarpQ = kQueueCap / (kPassBlock / 32);  // per warp: >= 32 + 4 * 32
+constexpr int kRing = 160;  // candidate ring per warp: >= 31 left over + 4 * 32 added
+constexpr int kReal = 64;   // real-collision ring per warp: >= 31 left over + 32 added
 
 struct PassShared {
   unsigned long long ctr[kNumCtr];
@@ -273,25 +296,99 @@ struct PassShared {
   int qcount;
 };
 
-// Null-collision MCC of one candidate (Sec. 2a step 6), run from the CTA's
-// candidate queue after the streaming phase: reloads the particle (already
-// pushed, L2-resident), redraws Philox block A, picks the process and
-// scatters.  Ionisation appends the secondary electron to this segment and
-// the ion to its species' segment, and deposits both.
-__device__ __noinline__ void collide_candidate(const BatchView& b, const RunDev* R, RunState* st, const SegDev& G,
-                                  SegState* ss, int sp, int cur, long long i, long long k, int N,
-                                  int Nm, bool sample, unsigned long long* Ssm, float* Msm,
-                                  PassShared& sh) {
+// Ionisation of the electron at (c, f) with energy Erem above threshold
+// left to share (Sec. 2a step 6): the two electrons split it by a uniform
+// fraction, the primary leaving along (d0, d1, d2), the secondary isotropic;
+// the ion is drawn from the gas Maxwellian.  The secondary is appended to
+// this segment and deposited in shared memory, the ion to its species'
+// segment and deposited to HBM.  Out of line: ionisations are a small
+// fraction of the collisions and need the most registers.  Returns the
+// primary's new velocity.
+__device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int c, float f, uint64_t id,
+                                      long long k, float Erem, bool sample, float d0, float d1, float d2,
+                                      unsigned long long* Ssm, float* Msm, PassShared& sh) {
+  const SegDev& G = b.segs[s];
+  const int slot = G.run, sp = G.species;
+  const RunDev* R = b.runs + slot;
+  RunState* st = b.rst + slot;
+  SegState* ss = b.sst + s;
   const SpeciesDev* SP = &R->sp[sp];
+  const int N = R->N, Nm = b.nmax + 1;
   const uint64_t seed = R->seed;
-  if (!chk(i >= 0 && i < G.cap, 6, i, G.cap)) return;
+  const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+  const float fr = u24(B.x);
+  const float v1 = sqrtf(SP->two_e_over_m * (fr * Erem));
+  const float v2 = sqrtf(SP->two_e_over_m * ((1.0f - fr) * Erem));
+  float e0, e1, e2;
+  isotropic(u24(B.y), u24(B.z), e0, e1, e2);
+  const uint4 Cw = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 2u);
+  float z0, z1, z2, z3;
+  box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
+  box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
+  const float sd = R->vth_gas;
+  atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
+  // secondary electron: same segment and species, deposited in shared memory
+  if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
+    deposit_one(Ssm, c, f);
+    if (sample) {
+      const float vb = v2 * e0;
+      atomicAdd(Msm + c, (1.0f - f) * vb);
+      atomicAdd(Msm + c + 1, f * vb);
+      atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
+      atomicAdd(Msm + Nm + c + 1, f * vb * vb);
+    }
+  } else {
+    atomicAdd(&sh.ctr[C_LOST], 1ull);
+    set_status(st, ECPIC_ERR_CAPACITY);
+  }
+  // ion: the product species' segment, deposited straight to HBM
+  const int ps = SP->proc[chosen].product_seg;
+  if (chk(ps >= 0 && ps < b.nseg, 18, ps, b.nseg)) {
+    const int pspec = SP->proc[chosen].product_species;
+    const float ivx = sd * z0;
+    if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
+      deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
+      if (sample) {
+        double* md = R->momd + (size_t)pspec * 2 * (N + 1);
+        atomicAdd(md + c, (double)((1.0f - f) * ivx));
+        atomicAdd(md + c + 1, (double)(f * ivx));
+        atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
+        atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
+      }
+    } else {
+      atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
+      set_status(st, ECPIC_ERR_CAPACITY);
+    }
+  }
+  return make_float3(v1 * d0, v1 * d1, v1 * d2);
+}
+
+// A real (non-null) collision of process `chosen` (Sec. 2a step 6).  Reloads
+// the pushed particle, redraws Philox block A (scattering angles) and, for heavy
+// species, block B (the target neutral's velocity), and scatters.  On sample steps the streaming
+// part has already added the pre-collision vx moments; the change is added
+// here.
+__device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, long long k, int flags,
+                                          float En, float gm, unsigned long long* Ssm, float* Msm,
+                                          PassShared& sh) {
+  const SegDev& G = b.segs[s];
+  const int slot = G.run, sp = G.species;
+  const RunDev* R = b.runs + slot;
+  RunState* st = b.rst + slot;
+  SegState* ss = b.sst + s;
+  const SpeciesDev* SP = &R->sp[sp];
+  const int cur = flags & 1, chosen = flags >> 2;
+  const bool sample = (flags & 2) != 0;
+  const int N = R->N, Nm = b.nmax + 1;
+  const uint64_t seed = R->seed;
+  if (!chk(i >= 0 && i < G.cap && chosen < kMaxProc, 6, i, G.cap)) return;
   const int c = G.cell[cur][i];
   if (!chk(c >= 0 && c < N, 7, c, N)) return;
   const float f = G.xi[cur][i];
   float vx = G.vx[cur][i], vy = G.vy[cur][i], vz = G.vz[cur][i];
+  const float vx_old = vx;
   const uint64_t id = G.id[cur][i];
   const uint4 A = draw(seed, id, (uint32_t)k, (uint32_t)sp << 8);
-  const int nproc = SP->nproc;
   float gx = vx, gy = vy, gz = vz, vnx = 0.f, vny = 0.f, vnz = 0.f;
   if (SP->heavy) {
     const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
@@ -306,119 +403,55 @@ __device__ __noinline__ void collide_candidate(const BatchView& b, const RunDev*
     gy -= vny;
     gz -= vnz;
   }
-  const float g2 = gx * gx + gy * gy + gz * gz;
-  const float gm = sqrtf(g2);
-  const float En = SP->half_m_over_e * g2;
-  const float ng = R->ng;
-  float nu[kMaxProc];
-  float tot = 0.0f;
-#pragma unroll
-  for (int p = 0; p < kMaxProc; ++p) {
-    nu[p] = 0.0f;
-    if (p < nproc) {
-      nu[p] = ng * sigma_at(SP->proc[p].sigma, SP->proc[p].thr, En, SP->dE_inv, SP->ntab) * gm;
-      tot += nu[p];
-    }
+  atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
+  float d0, d1, d2;
+  isotropic(u24(A.z), u24(A.w), d0, d1, d2);
+  const int kind = SP->proc[chosen].kind;
+  const float thr = SP->proc[chosen].thr;
+  if (kind == ECPIC_ELASTIC) {
+    const float cchi = gm > 0.0f ? (gx * d0 + gy * d1 + gz * d2) / gm : 1.0f;
+    const float E1 = En * (1.0f - SP->two_m_over_M * (1.0f - cchi));
+    const float v1 = sqrtf(SP->two_e_over_m * E1);
+    vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+  } else if (kind == ECPIC_EXCITATION) {
+    const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
+    vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
+  } else if (kind == ECPIC_IONIZATION) {
+    const float3 v1 = ionize(b, s, chosen, c, f, id, k, En - thr, sample, d0, d1, d2, Ssm, Msm, sh);
+    vx = v1.x; vy = v1.y; vz = v1.z;
+  } else if (kind == ECPIC_ION_ELASTIC) {
+    const float h = SP->m_frac * gm;
+    vx = SP->mass_frac * vx + SP->m_frac * vnx + h * d0;
+    vy = SP->mass_frac * vy + SP->m_frac * vny + h * d1;
+    vz = SP->mass_frac * vz + SP->m_frac * vnz + h * d2;
+  } else {  // ECPIC_CX
+    vx = vnx; vy = vny; vz = vnz;
   }
-  if (tot > SP->nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
-  const float Rr = u24(A.y) * SP->nu_max;
-  int chosen = -1;
-  float cum = 0.0f;
-#pragma unroll
-  for (int p = 0; p < kMaxProc; ++p) {
-    if (p < nproc && chosen < 0) {
-      cum += nu[p];
-      if (Rr < cum) chosen = p;
-    }
-  }
-  if (chosen >= 0) {
-    atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
-    float d0, d1, d2;
-    isotropic(u24(A.z), u24(A.w), d0, d1, d2);
-    const int kind = SP->proc[chosen].kind;
-    const float thr = SP->proc[chosen].thr;
-    if (kind == ECPIC_ELASTIC) {
-      const float cchi = gm > 0.0f ? (gx * d0 + gy * d1 + gz * d2) / gm : 1.0f;
-      const float E1 = En * (1.0f - SP->two_m_over_M * (1.0f - cchi));
-      const float v1 = sqrtf(SP->two_e_over_m * E1);
-      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-    } else if (kind == ECPIC_EXCITATION) {
-      const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
-      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-    } else if (kind == ECPIC_IONIZATION) {
-      const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
-      const float Erem = En - thr;
-      const float fr = u24(B.x);
-      const float v1 = sqrtf(SP->two_e_over_m * (fr * Erem));
-      const float v2 = sqrtf(SP->two_e_over_m * ((1.0f - fr) * Erem));
-      vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
-      float e0, e1, e2;
-      isotropic(u24(B.y), u24(B.z), e0, e1, e2);
-      const uint4 Cw = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 2u);
-      float z0, z1, z2, z3;
-      box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
-      box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
-      const float sd = R->vth_gas;
-      atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
-      // secondary electron: same segment and species, deposited in shared memory
-      if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
-        deposit_one(Ssm, c, f);
-        if (sample) {
-          const float vb = v2 * e0;
-          atomicAdd(Msm + c, (1.0f - f) * vb);
-          atomicAdd(Msm + c + 1, f * vb);
-          atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
-          atomicAdd(Msm + Nm + c + 1, f * vb * vb);
-        }
-      } else {
-        atomicAdd(&sh.ctr[C_LOST], 1ull);
-        set_status(st, ECPIC_ERR_CAPACITY);
-      }
-      // ion: the product species' segment, deposited straight to HBM
-      const int ps = SP->proc[chosen].product_seg;
-      if (!chk(ps >= 0 && ps < b.nseg, 18, ps, b.nseg)) return;
-      const int pspec = SP->proc[chosen].product_species;
-      const float ivx = sd * z0;
-      if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
-        deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
-        if (sample) {
-          double* md = R->momd + (size_t)pspec * 2 * (N + 1);
-          atomicAdd(md + c, (double)((1.0f - f) * ivx));
-          atomicAdd(md + c + 1, (double)(f * ivx));
-          atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
-          atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
-        }
-      } else {
-        atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
-        set_status(st, ECPIC_ERR_CAPACITY);
-      }
-    } else if (kind == ECPIC_ION_ELASTIC) {
-      const float h = SP->m_frac * gm;
-      vx = SP->mass_frac * vx + SP->m_frac * vnx + h * d0;
-      vy = SP->mass_frac * vy + SP->m_frac * vny + h * d1;
-      vz = SP->mass_frac * vz + SP->m_frac * vnz + h * d2;
-    } else {  // ECPIC_CX
-      vx = vnx; vy = vny; vz = vnz;
-    }
-    G.vx[cur][i] = vx;
-    G.vy[cur][i] = vy;
-    G.vz[cur][i] = vz;
-  }
+  G.vx[cur][i] = vx;
+  G.vy[cur][i] = vy;
+  G.vz[cur][i] = vz;
   if (sample) {
-    atomicAdd(Msm + c, (1.0f - f) * vx);
-    atomicAdd(Msm + c + 1, f * vx);
-    atomicAdd(Msm + Nm + c, (1.0f - f) * vx * vx);
-    atomicAdd(Msm + Nm + c + 1, f * vx * vx);
+    const float d1v = vx - vx_old, d2v = vx * vx - vx_old * vx_old;
+    atomicAdd(Msm + c, (1.0f - f) * d1v);
+    atomicAdd(Msm + c + 1, f * d1v);
+    atomicAdd(Msm + Nm + c, (1.0f - f) * d2v);
+    atomicAdd(Msm + Nm + c + 1, f * d2v);
   }
 }
 
 // Streaming part of one piece: quads [qbeg, qend) of segment s, four
 // particles per thread with 16-byte loads.  Gather (Eq. 6-7 / CIC), leapfrog
 // (Eq. 8-9) in cell units, walls, the Philox candidate test, fixed-point
-// deposit of X^{k+1} (Eq. 2-3).  vy, vz are read only on energy-sample steps;
-// candidates go to a shared-memory queue drained by collide_candidate.
+// deposit of X^{k+1} (Eq. 2-3).  Collisions (Sec. 2a step 6) go through two
+// per-warp rings, each drained 32 entries at a time so that all lanes work:
+// candidates enter the first with their selection word and |g|^2 (or vx)
+// and get the null-collision test; the few real collisions enter the second
+// and are scattered there.  vy, vz are streamed when a species' candidate
+// probability is 1/16 or more (its candidates then touch most 32-byte
+// sectors anyway) and on energy-sample steps; otherwise the test reads them
+// per candidate.
 __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
-                           unsigned long long* Ssm, float* Msm, int* queue, PassShared& sh) {
+                           unsigned long long* Ssm, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
@@ -440,195 +473,295 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
   const float* __restrict__ E = R->E;
-  const float* __restrict__ dtdx = R->dtdx;
   const uint32_t thr24 = SP->thr24;
   const bool mcc = stepping && SP->nproc > 0 && thr24 > 0;
+  const bool heavy = SP->heavy != 0;
+  const bool yz_stream = mcc && !heavy && thr24 >= (1u << 20);
+  const bool load_yz = sample || yz_stream;
+  const bool walls = bc != ECPIC_PERIODIC;
   const uint64_t seed = R->seed;
-  const int Nm = b.nmax + 1;
   const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
 
   int my_lo = INT_MAX, my_hi = -1;
   float ke = 0.0f;
-  unsigned ncand = 0, nlive = 0;
-  // per-warp candidate queue: drained 32 at a time, warp-synchronously
-  int* wq = queue + (threadIdx.x >> 5) * kWarpQ;
-  int wcount = 0;
+  unsigned ncand = 0, nlive = 0, nabs_l = 0, nabs_r = 0, nnan = 0;
+  // this warp's rings: candidates (index, Philox word A.y, |g|^2 or vx) and
+  // real collisions (index, process, E, |g|)
+  int* qi = reinterpret_cast<int*>(ring) + (threadIdx.x >> 5) * (3 * kRing + 4 * kReal);
+  uint32_t* qr = reinterpret_cast<uint32_t*>(qi + kRing);
+  float* qw = reinterpret_cast<float*>(qi + 2 * kRing);
+  int* xi_ = qi + 3 * kRing;
+  int* xp = xi_ + kReal;
+  float* xe = reinterpret_cast<float*>(xi_ + 2 * kReal);
+  float* xg = reinterpret_cast<float*>(xi_ + 3 * kReal);
+  int head = 0, wcount = 0, rhead = 0, rcount = 0;  // warp-uniform
 
-  // block-uniform trip count (warp collectives below need full warps)
-  for (long long base = qbeg; base < qend; base += kPassBlock) {
-    const long long q = base + (long long)threadIdx.x;
-    const long long i0 = 4 * q;
-    const bool inq = q < qend && chk(i0 < G.cap, 2, i0, G.cap);
-    const bool full = inq && (i0 + 3 < n) && chk(i0 + 3 < G.cap, 3, i0 + 3, G.cap);
-    int c[4];
-    float f[4], v[4];
-    if (full) {
-      const int4 c4 = *reinterpret_cast<const int4*>(pc + i0);
-      const float4 f4 = *reinterpret_cast<const float4*>(pxi + i0);
-      const float4 v4 = *reinterpret_cast<const float4*>(pvx + i0);
-      c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-      f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
-      v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
-    } else {
+  // block-uniform trip count (warp collectives below need full warps); the
+  // pass after the last quad empties both rings
+  for (long long base = qbeg;; base += kPassBlock) {
+    const bool more = base < qend;
+    if (more) {
+      const long long q = base + (long long)threadIdx.x;
+      const long long i0 = 4 * q;
+      const bool inq = q < qend && chk(i0 < G.cap, 2, i0, G.cap);
+      const bool full = inq && (i0 + 3 < n) && chk(i0 + 3 < G.cap, 3, i0 + 3, G.cap);
+      int c[4];
+      float f[4], v[4];
+      if (full) {
+        const int4 c4 = *reinterpret_cast<const int4*>(pc + i0);
+        const float4 f4 = *reinterpret_cast<const float4*>(pxi + i0);
+        const float4 v4 = *reinterpret_cast<const float4*>(pvx + i0);
+        c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        f[0] = f4.x; f[1] = f4.y; f[2] = f4.z; f[3] = f4.w;
+        v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
+      } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool in = inq && (i0 + j < n);
-        c[j] = in ? pc[i0 + j] : -1;
-        f[j] = in ? pxi[i0 + j] : 0.0f;
-        v[j] = in ? pvx[i0 + j] : 0.0f;
-      }
-    }
-    bool cand[4] = {false, false, false, false};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) nlive += c[j] >= 0 ? 1u : 0u;
-    if (stepping) {
-      uint64_t id[4] = {0, 0, 0, 0};
-      if (mcc) {
-        if (full) {
-          const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(pid + i0);
-          const ulonglong2 bq = *reinterpret_cast<const ulonglong2*>(pid + i0 + 2);
-          id[0] = a.x; id[1] = a.y; id[2] = bq.x; id[3] = bq.y;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) id[j] = c[j] >= 0 ? pid[i0 + j] : 0ull;
+        for (int j = 0; j < 4; ++j) {
+          const bool in = inq && (i0 + j < n);
+          c[j] = in ? pc[i0 + j] : -1;
+          f[j] = in ? pxi[i0 + j] : 0.0f;
+          v[j] = in ? pvx[i0 + j] : 0.0f;
         }
       }
-      float yz[4] = {0.f, 0.f, 0.f, 0.f};
-      if (sample) {
+      bool cand[4] = {false, false, false, false};
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (c[j] >= 0) yz[j] = pvy[i0 + j] * pvy[i0 + j] + pvz[i0 + j] * pvz[i0 + j];
-      }
-      // gather (Eq. 6-7; CIC for MC) and push (Eq. 8), branch-free over the
-      // four particles so the loads and arithmetic overlap
-      float Ei[4];
+      for (int j = 0; j < 4; ++j) nlive += c[j] >= 0 ? 1u : 0u;
+      if (stepping) {
+        uint64_t id[4] = {0, 0, 0, 0};
+        if (mcc) {
+          if (full) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(pid + i0);
+            const ulonglong2 bq = *reinterpret_cast<const ulonglong2*>(pid + i0 + 2);
+            id[0] = a.x; id[1] = a.y; id[2] = bq.x; id[3] = bq.y;
+          } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool ok = c[j] >= 0 && chk(c[j] < N, 4, c[j], N);
-        if (!ok) c[j] = -1;
-        const int cc = ok ? c[j] : 0;
-        if (scheme == ECPIC_SCHEME_EC) {
-          Ei[j] = __ldg(E + cc);
-        } else {
-          const float e0 = __ldg(E + cc), e1 = __ldg(E + cc + 1);
-          Ei[j] = e0 + f[j] * (e1 - e0);
+            for (int j = 0; j < 4; ++j) id[j] = c[j] >= 0 ? pid[i0 + j] : 0ull;
+          }
         }
-      }
+        // vy^2 + vz^2 (collisions do not change it before the push reads it)
+        float yz[4] = {0.f, 0.f, 0.f, 0.f};
+        if (load_yz) {
+          if (full) {
+            const float4 y4 = *reinterpret_cast<const float4*>(pvy + i0);
+            const float4 z4 = *reinterpret_cast<const float4*>(pvz + i0);
+            yz[0] = y4.x * y4.x + z4.x * z4.x;
+            yz[1] = y4.y * y4.y + z4.y * z4.y;
+            yz[2] = y4.z * y4.z + z4.z * z4.z;
+            yz[3] = y4.w * y4.w + z4.w * z4.w;
+          } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float vnew = v[j] + qm_dt * Ei[j];
-        if (sample && c[j] >= 0) ke += v[j] * vnew + yz[j];
-        v[j] = vnew;
-      }
-      // the Philox candidate draws of all four: independent chains the
-      // scheduler interleaves (the test does not depend on position)
-      uint32_t r0[4] = {0u, 0u, 0u, 0u};
-      if (mcc) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) r0[j] = draw(seed, id[j], (uint32_t)k, (uint32_t)sp << 8).x;
-      }
-      // Eq. 9 in cell units, then the walls
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (c[j] < 0) continue;
-        const float vnew = v[j];
-        if (!(fabsf(vnew) < 3.0e8f)) {
-          atomicAdd(&sh.ctr[C_NAN], 1ull);
-          set_status(st, ECPIC_ERR_NAN);
-          c[j] = -1;
-          continue;
+            for (int j = 0; j < 4; ++j)
+              if (c[j] >= 0) yz[j] = pvy[i0 + j] * pvy[i0 + j] + pvz[i0 + j] * pvz[i0 + j];
+          }
         }
-        int cj = c[j];
-        float fj = f[j];
+        // gather (Eq. 6-7; CIC for MC) and push (Eq. 8), branch-free over the
+        // four particles so the loads and arithmetic overlap
+        float Ei[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool ok = c[j] >= 0 && chk(c[j] < N, 4, c[j], N);
+          if (!ok) c[j] = -1;
+          const int cc = ok ? c[j] : 0;
+          if (scheme == ECPIC_SCHEME_EC) {
+            Ei[j] = __ldg(E + cc);
+          } else {
+            const float e0 = __ldg(E + cc), e1 = __ldg(E + cc + 1);
+            Ei[j] = e0 + f[j] * (e1 - e0);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float vnew = v[j] + qm_dt * Ei[j];
+          if (sample && c[j] >= 0) ke += v[j] * vnew + yz[j];
+          v[j] = vnew;
+        }
+        // Philox block A of all four: independent chains the scheduler
+        // interleaves; A.x decides the candidate, A.y selects the process
+        uint32_t r0[4] = {0u, 0u, 0u, 0u}, ry[4] = {0u, 0u, 0u, 0u};
+        if (mcc) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint4 A = draw(seed, id[j], (uint32_t)k, (uint32_t)sp << 8);
+            r0[j] = A.x;
+            ry[j] = A.y;
+          }
+        }
+        // Eq. 9 in cell units, then the walls: absorbed when X <= 0 or X >= L
         if (uniform) {
-          float g = fj + vnew * dtdx_u;
-          if (!(g >= 0.0f && g < 1.0f)) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool live = c[j] >= 0;
+            const bool bad = live && !(fabsf(v[j]) < 3.0e8f);
+            float g = f[j] + v[j] * dtdx_u;
             const float fl = floorf(g);
-            cj += (int)fl;
+            int cj = c[j] + (int)fl;
             g -= fl;
-            if (g >= 1.0f) {
-              cj += 1;
-              g = 0.0f;
-            }
-            if (bc == ECPIC_PERIODIC) {
+            const bool up = g >= 1.0f;  // g - floor(g) rounded to 1
+            cj += up ? 1 : 0;
+            g = up ? 0.0f : g;
+            if (!walls && (cj < 0 || cj >= N)) {
               cj %= N;
               if (cj < 0) cj += N;
             }
+            const bool out = walls && (cj < 0 || cj >= N || (cj == 0 && g == 0.0f));
+            const bool ok = live && !bad && !out;
+            nnan += bad ? 1u : 0u;
+            nabs_r += (live && !bad && out && cj >= N) ? 1u : 0u;
+            nabs_l += (live && !bad && out && cj < N) ? 1u : 0u;
+            c[j] = ok ? cj : -1;
+            f[j] = g;
+            cand[j] = mcc && ok && (r0[j] >> 8) < thr24;
           }
-          fj = g;
         } else {
-          walk_nonuniform(cj, fj, fj + vnew * __ldg(dtdx + cj), N, bc, R->rp, R->rm);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (c[j] < 0) continue;
+            if (!(fabsf(v[j]) < 3.0e8f)) {
+              ++nnan;
+              c[j] = -1;
+              continue;
+            }
+            int cj = c[j];
+            float fj = f[j];
+            walk_nonuniform(cj, fj, fj + v[j] * __ldg(R->dtdx + cj), N, bc, R->rp, R->rm);
+            if (walls && (cj < 0 || cj >= N || (cj == 0 && fj == 0.0f))) {
+              nabs_r += cj >= N ? 1u : 0u;
+              nabs_l += cj >= N ? 0u : 1u;
+              c[j] = -1;
+              continue;
+            }
+            c[j] = cj;
+            f[j] = fj;
+            cand[j] = mcc && (r0[j] >> 8) < thr24;
+          }
         }
-        // walls: absorbed when X <= 0 or X >= L
-        if (bc != ECPIC_PERIODIC && (cj < 0 || cj >= N || (cj == 0 && fj == 0.0f))) {
-          atomicAdd(&sh.ctr[cj >= N ? C_ABS_R : C_ABS_L], 1ull);
-          c[j] = -1;
+        if (full) {
+          *reinterpret_cast<int4*>(pc + i0) = make_int4(c[0], c[1], c[2], c[3]);
+          *reinterpret_cast<float4*>(pxi + i0) = make_float4(f[0], f[1], f[2], f[3]);
+          *reinterpret_cast<float4*>(pvx + i0) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (inq && i0 + j < n) {
+              pc[i0 + j] = c[j];
+              pxi[i0 + j] = f[j];
+              pvx[i0 + j] = v[j];
+            }
+        }
+        if (mcc) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const unsigned m = __ballot_sync(kFull, cand[j]);
+            if (cand[j]) {
+              int pos = head + wcount + __popc(m & lt_mask);
+              if (pos >= kRing) pos -= kRing;
+              if (chk(pos >= 0 && pos < kRing, 5, pos, kRing)) {
+                qi[pos] = (int)(i0 + j);
+                qr[pos] = ry[j];
+                qw[pos] = yz_stream ? v[j] * v[j] + yz[j] : v[j];
+              }
+            }
+            wcount += __popc(m);
+            ncand += cand[j] ? 1u : 0u;
+          }
+        }
+      }
+      // fixed-point CIC deposit of the new positions (Eq. 2-3); vx moments
+      // (pre-collision: the collision adds the change)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool val = c[j] >= 0;
+        deposit_warp(Ssm, val, c[j], f[j], b.nmax);
+        if (val) {
+          my_lo = min(my_lo, c[j]);
+          my_hi = max(my_hi, c[j] + 1);
+          if (sample && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
+            const int Nm = b.nmax + 1;
+            atomicAdd(Msm + c[j], (1.0f - f[j]) * v[j]);
+            atomicAdd(Msm + c[j] + 1, f[j] * v[j]);
+            atomicAdd(Msm + Nm + c[j], (1.0f - f[j]) * v[j] * v[j]);
+            atomicAdd(Msm + Nm + c[j] + 1, f[j] * v[j] * v[j]);
+          }
+        }
+      }
+    }
+    if (mcc) {
+      __syncwarp();
+      for (;;) {
+        if (rcount >= 32 || (!more && wcount == 0 && rcount > 0)) {
+          // scatter up to 32 real collisions
+          const int take = min(rcount, 32);
+          if (lane < take) {
+            int pos = rhead + lane;
+            if (pos >= kReal) pos -= kReal;
+            collide_real(b, s, xi_[pos], k, (cur | (sample ? 2 : 0)) | (xp[pos] << 2), xe[pos], xg[pos],
+                         Ssm, Msm, sh);
+          }
+          rhead += take;
+          if (rhead >= kReal) rhead -= kReal;
+          rcount -= take;
+          __syncwarp();
           continue;
         }
-        c[j] = cj;
-        f[j] = fj;
-        if (mcc) cand[j] = (r0[j] >> 8) < thr24;
-      }
-      if (full) {
-        *reinterpret_cast<int4*>(pc + i0) = make_int4(c[0], c[1], c[2], c[3]);
-        *reinterpret_cast<float4*>(pxi + i0) = make_float4(f[0], f[1], f[2], f[3]);
-        *reinterpret_cast<float4*>(pvx + i0) = make_float4(v[0], v[1], v[2], v[3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (inq && i0 + j < n) {
-            pc[i0 + j] = c[j];
-            pxi[i0 + j] = f[j];
-            pvx[i0 + j] = v[j];
+        if (!(wcount >= 32 || (!more && wcount > 0))) break;
+        // null-collision test of up to 32 candidates
+        const int take = min(wcount, 32);
+        const bool act = lane < take;
+        int pos = head + lane;
+        if (pos >= kRing) pos -= kRing;
+        int i = 0;
+        uint32_t ryv = 0u;
+        float w = 0.0f;
+        if (act) {
+          i = qi[pos];
+          ryv = qr[pos];
+          w = qw[pos];
+        }
+        float g2 = w;
+        if (heavy) {
+          // relative speed to a target neutral drawn from the gas Maxwellian
+          if (act) {
+            const float vx = pvx[i], vy = pvy[i], vz = pvz[i];
+            const uint4 B = draw(seed, pid[i], (uint32_t)k, ((uint32_t)sp << 8) | 1u);
+            float z0, z1, z2, z3;
+            box_muller(u24_open(B.x), u24(B.y), z0, z1);
+            box_muller(u24_open(B.z), u24(B.w), z2, z3);
+            const float sd = R->vth_gas;
+            const float gx = vx - sd * z0, gy = vy - sd * z1, gz = vz - sd * z2;
+            g2 = gx * gx + gy * gy + gz * gz;
           }
-      }
-      if (mcc) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const unsigned m = __ballot_sync(kFull, cand[j]);
-          const int slotq = wcount + __popc(m & ((1u << lane) - 1u));
-          if (cand[j] && chk(slotq < kWarpQ, 5, slotq, kWarpQ)) wq[slotq] = (int)(i0 + j);
-          wcount += __popc(m);
-          ncand += cand[j] ? 1u : 0u;
+        } else if (!yz_stream) {
+          if (act) {
+            const float vy = pvy[i], vz = pvz[i];
+            g2 = w * w + (vy * vy + vz * vz);
+          }
         }
-      }
-    }
-    // fixed-point CIC deposit of the new positions (Eq. 2-3)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool val = c[j] >= 0;
-      deposit_warp(Ssm, val, c[j], f[j], b.nmax);
-      if (val) {
-        my_lo = min(my_lo, c[j]);
-        my_hi = max(my_hi, c[j] + 1);
-        if (sample && !cand[j] && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
-          atomicAdd(Msm + c[j], (1.0f - f[j]) * v[j]);
-          atomicAdd(Msm + c[j] + 1, f[j] * v[j]);
-          atomicAdd(Msm + Nm + c[j], (1.0f - f[j]) * v[j] * v[j]);
-          atomicAdd(Msm + Nm + c[j] + 1, f[j] * v[j] * v[j]);
+        const float gm = sqrtf(g2), En = SP->half_m_over_e * g2;
+        const float nu_max = SP->nu_max;
+        float tot = 0.0f;
+        int chosen = -1;
+        if (act) chosen = select_process(SP, En, gm, R->ng, u24(ryv) * nu_max, &tot);
+        if (tot > nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
+        const unsigned m = __ballot_sync(kFull, chosen >= 0);
+        if (chosen >= 0) {
+          int rp = rhead + rcount + __popc(m & lt_mask);
+          if (rp >= kReal) rp -= kReal;
+          if (chk(rp >= 0 && rp < kReal, 24, rp, kReal)) {
+            xi_[rp] = i;
+            xp[rp] = chosen;
+            xe[rp] = En;
+            xg[rp] = gm;
+          }
         }
-      }
-    }
-    while (mcc && wcount >= 32) {
-      __syncwarp();
-      if (chk(wcount <= kWarpQ, 21, wcount, kWarpQ))
-        collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
-      const int rest = wcount - 32;
-      for (int r = 0; r < (rest + 31) / 32; ++r) {
-        const int e = lane + 32 * r;
-        const int val = (e < rest && chk(e + 32 < kWarpQ, 15, e + 32, kWarpQ)) ? wq[e + 32] : 0;
-        __syncwarp();
-        if (e < rest) wq[e] = val;
+        rcount += __popc(m);
+        head += take;
+        if (head >= kRing) head -= kRing;
+        wcount -= take;
         __syncwarp();
       }
-      wcount = rest;
     }
-  }
-  if (mcc && wcount > 0) {
-    __syncwarp();
-    if (lane < wcount && chk(wcount <= kWarpQ, 22, wcount, kWarpQ))
-      collide_candidate(b, R, st, G, ss, sp, cur, wq[lane], k, N, Nm, sample, Ssm, Msm, sh);
-    __syncwarp();
+    if (!more) break;
   }
 
   // piece epilogue: node range, energy, counters, flush to HBM
@@ -639,6 +772,9 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   }
   ncand = warp_sum(ncand);
   nlive = warp_sum(nlive);
+  nabs_l = warp_sum(nabs_l);
+  nabs_r = warp_sum(nabs_r);
+  nnan = warp_sum(nnan);
   if (lane == 0 && stepping && nlive) atomicAdd(&st->psteps, (unsigned long long)nlive);
   if (lane == 0) {
     if (my_hi >= 0) {
@@ -646,6 +782,12 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
       atomicMax(&sh.lohi[1], my_hi);
     }
     if (ncand) atomicAdd(&sh.ctr[C_CAND], (unsigned long long)ncand);
+    if (nabs_l) atomicAdd(&sh.ctr[C_ABS_L], (unsigned long long)nabs_l);
+    if (nabs_r) atomicAdd(&sh.ctr[C_ABS_R], (unsigned long long)nabs_r);
+    if (nnan) {
+      atomicAdd(&sh.ctr[C_NAN], (unsigned long long)nnan);
+      set_status(st, ECPIC_ERR_NAN);
+    }
   }
   if (sample) {
     const double kes = block_sum((double)ke, sh.dsm);
@@ -653,6 +795,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   }
   __syncthreads();
   const int flo = sh.lohi[0], fhi = chk(sh.lohi[1] <= N, 8, sh.lohi[1], N) ? sh.lohi[1] : N;
+  const int Nm = b.nmax + 1;
   unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   double* md = R->momd + (size_t)sp * 2 * (N + 1);
   // an empty range (no live particle in the piece) is (INT_MAX, -1): skip it
@@ -697,7 +840,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
   float* Msm = reinterpret_cast<float*>(Ssm + b.nmax + 1);
-  int* queue = reinterpret_cast<int*>(Msm + 2 * (b.nmax + 1));
+  unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 2 * (b.nmax + 1));
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
     Ssm[i] = 0ull;
@@ -721,7 +864,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const long long end = min(hi, pre[s + 1]) - pre[s];
     if (beg >= end) continue;
     if (!chk(b.segs[s].run >= 0 && b.segs[s].run < b.max_slots, 23, s, b.nseg)) continue;
-    pass_piece(b, s, beg, end, mode, Ssm, Msm, queue, sh);
+    pass_piece(b, s, beg, end, mode, Ssm, Msm, ring, sh);
   }
 }
 
@@ -1241,7 +1384,7 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
          sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
-         sizeof(int) * (size_t)kQueueCap;
+         sizeof(int) * (size_t)(3 * kRing + 4 * kReal) * (kPassBlock / 32);
 }
 
 size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }

@@ -2,6 +2,7 @@
 #include "runtime.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -47,7 +48,7 @@ size_t layout_bytes(const RunSpec& s) {
   add(8 * ns * 2 * (N + 1));  // momd
   add(8 * (size_t)acc_size((int)ns) * (N + 1));
   for (const auto& sp : s.species)
-    for (const auto& p : sp.procs) add(4 * p.sigma.size());
+    if (!sp.procs.empty()) add(16 * sp.procs[0].sigma.size() * ((sp.procs.size() + 3) / 4));
   for (const auto& sp : s.species)
     for (int buf = 0; buf < 2; ++buf) {
       const size_t c = (size_t)sp.cap;
@@ -371,14 +372,25 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     D.heavy = 0;
     D.ntab = hs.procs.empty() ? 2 : (int)hs.procs[0].sigma.size();
     D.dE_inv = hs.procs.empty() ? 1.0f : (float)(1.0 / hs.procs[0].dE);
+    D.np4 = (D.nproc + 3) / 4;
+    D.sig4 = nullptr;
+    for (int p = 0; p < kMaxProc; ++p) D.thr_all[p] = FLT_MAX;
+    if (D.nproc > 0) {
+      // node-major interleaving: one 16-byte load per node serves four processes
+      const size_t nt = (size_t)D.ntab, g4 = (size_t)D.np4;
+      std::vector<float> il(nt * g4 * 4, 0.0f);
+      for (int p = 0; p < D.nproc; ++p)
+        for (size_t i = 0; i < nt; ++i) il[(i * g4 + p / 4) * 4 + p % 4] = hs.procs[p].sigma[i];
+      float4* tab = cv.take<float4>(nt * g4);
+      cudaMemcpyAsync(tab, il.data(), 16 * nt * g4, cudaMemcpyHostToDevice, stream_);
+      D.sig4 = tab;
+    }
     for (int p = 0; p < D.nproc; ++p) {
       const HostProc& hp = hs.procs[p];
       ProcDev& P = D.proc[p];
       P.kind = hp.kind;
       P.thr = (float)hp.thr;
-      float* tab = cv.take<float>(hp.sigma.size());
-      cudaMemcpyAsync(tab, hp.sigma.data(), 4 * hp.sigma.size(), cudaMemcpyHostToDevice, stream_);
-      P.sigma = tab;
+      D.thr_all[p] = P.thr;
       P.product_species = hp.kind == ECPIC_IONIZATION ? hp.product : -1;
       P.product_seg = hp.kind == ECPIC_IONIZATION ? R.seg0 + hp.product : -1;
       if (hp.kind == ECPIC_ION_ELASTIC || hp.kind == ECPIC_CX) D.heavy = 1;
