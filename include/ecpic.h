@@ -264,6 +264,44 @@ int ecpic_debug_checks(int64_t* out4);
 int ecpic_philox_device(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key,
                         uint32_t* d_out, void* cuda_stream);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free variant of ecpic_deposit_device.  The paper has no
+ * counterpart: this is a service entry point of this library, not a step of
+ * the method.
+ *
+ * It is for callers that must not allocate device memory while they run: a
+ * process that handed all free HBM to its own pool at start-up (a cudaMalloc
+ * would fail there), or a latency-bound loop that a cudaMalloc/cudaFree would
+ * stall by synchronising the device.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its scratch is a fixed array of
+ * ECPIC_NOALLOC_SCRATCH_BYTES (4 MiB) in the library's own device image,
+ * holding per-block partial sums; nothing in it has to start at zero, since
+ * each call writes every entry that it later reads.
+ *
+ * Arguments and result as ecpic_deposit_device: d_cell/d_xi device, n
+ * entries (cell < 0 skipped, 0 <= xi < 1); d_S device, N+1 uint64, the
+ * fixed-point sums are ADDED to it (a plain read-modify-write, not atomics).
+ * Bit-identical to ecpic_deposit_device on the same input.  Async on
+ * cuda_stream, which must belong to the current device.
+ *
+ * Limits and errors: 1 <= N <= ECPIC_NOALLOC_MAX_CELLS (2048), else
+ * ECPIC_ERR_CAPACITY for N above it and ECPIC_ERR_ARG for bad arguments; n is
+ * not limited.
+ *
+ * Set-up: the first call on each device (with that device current) looks up
+ * the scratch array's address and keeps it; if you capture streams, make a
+ * first call on each device before any capture begins.
+ *
+ * Races: all calls on a device share the one scratch array.  Calls that may
+ * overlap -- on different streams or from different host threads without
+ * ordering between them -- race on it and corrupt each other's results, and a
+ * kernel writing d_S while a call runs races on d_S; order such calls on one
+ * stream or with events. */
+#define ECPIC_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define ECPIC_NOALLOC_MAX_CELLS 2048
+int ecpic_deposit_device_noalloc(int N, int64_t n, const int32_t* d_cell, const float* d_xi,
+                                 uint64_t* d_S, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ SIGNATURES = {
     "ecpic_set_pass_grid": (i32, [vp, i32]),
     "ecpic_doubling_grid": (i32, [i32, d, d, i32, i32, vp, i32]),
     "ecpic_deposit_device": (i32, [i32, i64, vp, vp, vp, vp]),
+    "ecpic_deposit_device_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
     "ecpic_philox_device": (i32, [i64, vp, vp, vp, vp]),
     "ecpic_debug_checks": (i32, [vp]),
 }
@@ -164,6 +165,12 @@ def ecpic_deposit_device(N, n, d_cell, d_xi, d_S, stream=None):
     rc = lib().ecpic_deposit_device(N, n, d_cell, d_xi, d_S, stream)
     if rc != ECPIC_OK:
         raise EcpicError(rc, "ecpic_deposit_device")
+
+
+def ecpic_deposit_device_noalloc(N, n, d_cell, d_xi, d_S, stream=None):
+    rc = lib().ecpic_deposit_device_noalloc(N, n, d_cell, d_xi, d_S, stream)
+    if rc != ECPIC_OK:
+        raise EcpicError(rc, "ecpic_deposit_device_noalloc")
 
 
 def ecpic_philox_device(n, d_ctr, d_key, d_out, stream=None):
