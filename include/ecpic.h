@@ -41,7 +41,8 @@ typedef enum {
   ECPIC_ERR_ARG = -1,      /* invalid argument */
   ECPIC_ERR_STATE = -2,    /* call out of order */
   ECPIC_ERR_NOMEM = -3,    /* device allocation or memory budget */
-  ECPIC_ERR_CAPACITY = -4, /* particle births exceeded a species capacity */
+  ECPIC_ERR_CAPACITY = -4, /* a fixed capacity was exceeded (species particles,
+                              real-collision records, scratch size) */
   ECPIC_ERR_CUDA = -5,     /* CUDA runtime error */
   ECPIC_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
   ECPIC_ERR_NAN = -7       /* non-finite particle state detected */
@@ -156,9 +157,9 @@ int ecpic_set_sort_every(ecpic_run* run, int sort_every);
 int ecpic_sort_now(ecpic_run* run);
 /* Measurement: advance n_steps with plain launches (no graph), bracketing
  * each kernel phase with CUDA events on the run's stream; synchronises.
- * ms[0..2] = summed device time of the particle pass, the field solve and the
- * counting sort; launches[0..2] = their launch counts.  Same physics as
- * ecpic_step. */
+ * ms[0..3] = summed device time of the particle pass, the field solve, the
+ * counting sort and the real-collision kernel; launches[0..3] = their launch
+ * counts.  Same physics as ecpic_step. */
 int ecpic_profile_step(ecpic_run* run, int64_t n_steps, double* ms, int64_t* launches);
 /* Pass-kernel grid size override (0 = automatic); for tuning. */
 int ecpic_set_pass_grid(ecpic_run* run, int ctas);
@@ -236,7 +237,8 @@ int ecpic_engine_stats(ecpic_engine* eng, int64_t* particle_steps, int64_t* runs
 int ecpic_engine_tune(ecpic_engine* eng, int pass_ctas, int sort_every);
 /* Measurement: advance the resident runs n_steps with plain launches,
  * bracketing each kernel phase with CUDA events on the engine's stream (see
- * ecpic_profile_step); synchronises.  No admission or retirement. */
+ * ecpic_profile_step: ms[0..3], launches[0..3]); synchronises.  No admission
+ * or retirement. */
 int ecpic_engine_profile(ecpic_engine* eng, int64_t n_steps, double* ms, int64_t* launches);
 
 /* ------------------------------------------------------------------ */

@@ -339,10 +339,10 @@ int ecpic_profile_step(ecpic_run* r, int64_t n, double* ms, int64_t* launches) {
   if (!r || n < 0) return ECPIC_ERR_ARG;
   if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
   std::string err;
-  long long l[3] = {0, 0, 0};
+  long long l[4] = {0, 0, 0, 0};
   const int rc = r->batch->profile_step(n, ms, l, &err);
   if (launches)
-    for (int i = 0; i < 3; ++i) launches[i] = l[i];
+    for (int i = 0; i < 4; ++i) launches[i] = l[i];
   return rc ? fail(r, rc, err) : ECPIC_OK;
 }
 

@@ -125,6 +125,10 @@ struct SegDev {
   int species;
   int hoff;             // offset of this segment's histogram (N ints)
   int pad;
+  // real collisions of the current step, recorded by the pass for the
+  // collision kernel: {index, process, E (eV) bits, |g| (m/s) bits}
+  int4* real;
+  long long real_cap;
 };
 
 struct SegState {
@@ -132,6 +136,7 @@ struct SegState {
   long long n_alloc;    // append cursor for births (>= n_proc)
   long long n_live;     // written by the sort scan
   long long n_dead;     // slots below n_proc marked absorbed since the last sort
+  long long n_real;     // records in SegDev::real this step (reset by the field kernel)
   int cur;              // current buffer set
   int pad;
 };

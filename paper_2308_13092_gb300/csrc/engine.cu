@@ -314,10 +314,10 @@ int ecpic_engine_stats(ecpic_engine* e, int64_t* particle_steps, int64_t* runs_f
 int ecpic_engine_profile(ecpic_engine* e, int64_t n, double* ms, int64_t* launches) {
   if (!e || n < 0) return ECPIC_ERR_ARG;
   std::string err;
-  long long l[3] = {0, 0, 0};
+  long long l[4] = {0, 0, 0, 0};
   const int rc = e->batch->profile_step(n, ms, l, &err);
   if (launches)
-    for (int i = 0; i < 3; ++i) launches[i] = l[i];
+    for (int i = 0; i < 4; ++i) launches[i] = l[i];
   return rc ? efail(e, rc, err) : ECPIC_OK;
 }
 

@@ -116,10 +116,10 @@ __device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int
   return true;
 }
 
-// exclusive prefix of the work of all segments (particles, or groups of
-// `unit` particles): pre[0..nseg]
+// exclusive prefix of the work of all segments (particles, groups of `unit`
+// particles, or recorded real collisions): pre[0..nseg]
 __device__ long long seg_prefix(const BatchView& b, int mode, int only, long long* pre,
-                                long long* wsm, int unit = 1) {
+                                long long* wsm, int unit = 1, bool reals = false) {
   const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
   const int s0 = threadIdx.x * per;
   long long loc = 0;
@@ -127,9 +127,9 @@ __device__ long long seg_prefix(const BatchView& b, int mode, int only, long lon
     const int s = s0 + k;
     if (s < b.nseg) {
       const int slot = b.segs[s].run;
-      const long long c = run_live(b.runs[slot], b.rst[slot], mode, only, slot)
-                              ? (b.sst[s].n_proc + unit - 1) / unit
-                              : 0;
+      const long long c = !run_live(b.runs[slot], b.rst[slot], mode, only, slot) ? 0
+                          : reals ? b.sst[s].n_real
+                                  : (b.sst[s].n_proc + unit - 1) / unit;
       pre[s] = c;
       loc += c;
     }
@@ -286,7 +286,6 @@ __device__ __forceinline__ void walk_nonuniform(int& c, float& f, float g, int N
 }
 
 constexpr int kRing = 160;  // candidate ring per warp: >= 31 left over + 4 * 32 added
-constexpr int kReal = 64;   // real-collision ring per warp: >= 31 left over + 32 added
 
 struct PassShared {
   unsigned long long ctr[kNumCtr];
@@ -300,20 +299,19 @@ struct PassShared {
 // left to share (Sec. 2a step 6): the two electrons split it by a uniform
 // fraction, the primary leaving along (d0, d1, d2), the secondary isotropic;
 // the ion is drawn from the gas Maxwellian.  The secondary is appended to
-// this segment and deposited in shared memory, the ion to its species'
-// segment and deposited to HBM.  Out of line: ionisations are a small
-// fraction of the collisions and need the most registers.  Returns the
-// primary's new velocity.
+// this segment, the ion to its species' segment; both are deposited (and,
+// on sample steps, enter the vx moments) in HBM.  Returns the primary's new
+// velocity.
 __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int c, float f, uint64_t id,
-                                      long long k, float Erem, bool sample, float d0, float d1, float d2,
-                                      unsigned long long* Ssm, float* Msm, PassShared& sh) {
+                                      long long k, float Erem, bool sample, float d0, float d1,
+                                      float d2) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
   RunState* st = b.rst + slot;
   SegState* ss = b.sst + s;
   const SpeciesDev* SP = &R->sp[sp];
-  const int N = R->N, Nm = b.nmax + 1;
+  const int N = R->N;
   const uint64_t seed = R->seed;
   const uint4 B = draw(seed, id, (uint32_t)k, ((uint32_t)sp << 8) | 1u);
   const float fr = u24(B.x);
@@ -326,22 +324,23 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   box_muller(u24_open(Cw.x), u24(Cw.y), z0, z1);
   box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
   const float sd = R->vth_gas;
-  atomicAdd(&sh.ctr[C_BIRTHS], 1ull);
-  // secondary electron: same segment and species, deposited in shared memory
-  if (append_particle(G, ss, c, f, v2 * e0, v2 * e1, v2 * e2, child_id(id, k, 1))) {
-    deposit_one(Ssm, c, f);
+  atomicAdd(&st->ctr[sp][C_BIRTHS], 1ull);
+  // secondary electron: same segment and species
+  const float vb = v2 * e0;
+  if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1))) {
+    deposit_one(R->S + (size_t)sp * (N + 1), c, f);
     if (sample) {
-      const float vb = v2 * e0;
-      atomicAdd(Msm + c, (1.0f - f) * vb);
-      atomicAdd(Msm + c + 1, f * vb);
-      atomicAdd(Msm + Nm + c, (1.0f - f) * vb * vb);
-      atomicAdd(Msm + Nm + c + 1, f * vb * vb);
+      double* md = R->momd + (size_t)sp * 2 * (N + 1);
+      atomicAdd(md + c, (double)((1.0f - f) * vb));
+      atomicAdd(md + c + 1, (double)(f * vb));
+      atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * vb * vb));
+      atomicAdd(md + (N + 1) + c + 1, (double)(f * vb * vb));
     }
   } else {
-    atomicAdd(&sh.ctr[C_LOST], 1ull);
+    atomicAdd(&st->ctr[sp][C_LOST], 1ull);
     set_status(st, ECPIC_ERR_CAPACITY);
   }
-  // ion: the product species' segment, deposited straight to HBM
+  // ion: the product species' segment
   const int ps = SP->proc[chosen].product_seg;
   if (chk(ps >= 0 && ps < b.nseg, 18, ps, b.nseg)) {
     const int pspec = SP->proc[chosen].product_species;
@@ -363,25 +362,25 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   return make_float3(v1 * d0, v1 * d1, v1 * d2);
 }
 
-// A real (non-null) collision of process `chosen` (Sec. 2a step 6).  Reloads
-// the pushed particle, redraws Philox block A (scattering angles) and, for heavy
-// species, block B (the target neutral's velocity), and scatters.  On sample steps the streaming
-// part has already added the pre-collision vx moments; the change is added
+// A real (non-null) collision of process `chosen` at energy En and relative
+// speed gm (Sec. 2a step 6), as recorded by the pass: reloads the pushed
+// particle, redraws Philox block A (scattering angles) and, for heavy species,
+// block B (the target neutral's velocity), and scatters.  On sample steps the
+// pass has already added the pre-collision vx moments; the change is added
 // here.
-__device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, long long k, int flags,
-                                          float En, float gm, unsigned long long* Ssm, float* Msm,
-                                          PassShared& sh) {
+__device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, int chosen, float En,
+                                             float gm) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
-  RunState* st = b.rst + slot;
-  SegState* ss = b.sst + s;
+  const RunState* st = b.rst + slot;
   const SpeciesDev* SP = &R->sp[sp];
-  const int cur = flags & 1, chosen = flags >> 2;
-  const bool sample = (flags & 2) != 0;
-  const int N = R->N, Nm = b.nmax + 1;
+  const int cur = b.sst[s].cur;
+  const long long k = st->step;
+  const bool sample = R->sample_every > 0 && ((k + 1) % R->sample_every) == 0;
+  const int N = R->N;
   const uint64_t seed = R->seed;
-  if (!chk(i >= 0 && i < G.cap && chosen < kMaxProc, 6, i, G.cap)) return;
+  if (!chk(i >= 0 && i < G.cap && chosen >= 0 && chosen < SP->nproc, 6, i, G.cap)) return;
   const int c = G.cell[cur][i];
   if (!chk(c >= 0 && c < N, 7, c, N)) return;
   const float f = G.xi[cur][i];
@@ -403,7 +402,6 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, l
     gy -= vny;
     gz -= vnz;
   }
-  atomicAdd(&sh.ctr[C_COLL0 + chosen], 1ull);
   float d0, d1, d2;
   isotropic(u24(A.z), u24(A.w), d0, d1, d2);
   const int kind = SP->proc[chosen].kind;
@@ -417,7 +415,7 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, l
     const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
     vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
   } else if (kind == ECPIC_IONIZATION) {
-    const float3 v1 = ionize(b, s, chosen, c, f, id, k, En - thr, sample, d0, d1, d2, Ssm, Msm, sh);
+    const float3 v1 = ionize(b, s, chosen, c, f, id, k, En - thr, sample, d0, d1, d2);
     vx = v1.x; vy = v1.y; vz = v1.z;
   } else if (kind == ECPIC_ION_ELASTIC) {
     const float h = SP->m_frac * gm;
@@ -431,25 +429,26 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, l
   G.vy[cur][i] = vy;
   G.vz[cur][i] = vz;
   if (sample) {
+    double* md = R->momd + (size_t)sp * 2 * (N + 1);
     const float d1v = vx - vx_old, d2v = vx * vx - vx_old * vx_old;
-    atomicAdd(Msm + c, (1.0f - f) * d1v);
-    atomicAdd(Msm + c + 1, f * d1v);
-    atomicAdd(Msm + Nm + c, (1.0f - f) * d2v);
-    atomicAdd(Msm + Nm + c + 1, f * d2v);
+    atomicAdd(md + c, (double)((1.0f - f) * d1v));
+    atomicAdd(md + c + 1, (double)(f * d1v));
+    atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * d2v));
+    atomicAdd(md + (N + 1) + c + 1, (double)(f * d2v));
   }
 }
 
 // Streaming part of one piece: quads [qbeg, qend) of segment s, four
 // particles per thread with 16-byte loads.  Gather (Eq. 6-7 / CIC), leapfrog
 // (Eq. 8-9) in cell units, walls, the Philox candidate test, fixed-point
-// deposit of X^{k+1} (Eq. 2-3).  Collisions (Sec. 2a step 6) go through two
-// per-warp rings, each drained 32 entries at a time so that all lanes work:
-// candidates enter the first with their selection word and |g|^2 (or vx)
-// and get the null-collision test; the few real collisions enter the second
-// and are scattered there.  vy, vz are streamed when a species' candidate
-// probability is 1/16 or more (its candidates then touch most 32-byte
-// sectors anyway) and on energy-sample steps; otherwise the test reads them
-// per candidate.
+// deposit of X^{k+1} (Eq. 2-3).  Collision candidates (Sec. 2a step 6)
+// enter a per-warp ring with their selection word and |g|^2 (or vx); the
+// warp drains it 32 at a time (all lanes busy) with the null-collision test.
+// The few real collisions are recorded for k_collide, which scatters them
+// with its own register budget.  vy, vz are streamed when a species'
+// candidate probability is 1/16 or more (its candidates then touch most
+// 32-byte sectors anyway) and on energy-sample steps; otherwise the test
+// reads them per candidate.
 __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            unsigned long long* Ssm, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
@@ -486,16 +485,11 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   int my_lo = INT_MAX, my_hi = -1;
   float ke = 0.0f;
   unsigned ncand = 0, nlive = 0, nabs_l = 0, nabs_r = 0, nnan = 0;
-  // this warp's rings: candidates (index, Philox word A.y, |g|^2 or vx) and
-  // real collisions (index, process, E, |g|)
-  int* qi = reinterpret_cast<int*>(ring) + (threadIdx.x >> 5) * (3 * kRing + 4 * kReal);
+  // this warp's candidate ring: index, Philox word A.y, |g|^2 or vx
+  int* qi = reinterpret_cast<int*>(ring) + (threadIdx.x >> 5) * (3 * kRing);
   uint32_t* qr = reinterpret_cast<uint32_t*>(qi + kRing);
   float* qw = reinterpret_cast<float*>(qi + 2 * kRing);
-  int* xi_ = qi + 3 * kRing;
-  int* xp = xi_ + kReal;
-  float* xe = reinterpret_cast<float*>(xi_ + 2 * kReal);
-  float* xg = reinterpret_cast<float*>(xi_ + 3 * kReal);
-  int head = 0, wcount = 0, rhead = 0, rcount = 0;  // warp-uniform
+  int head = 0, wcount = 0;  // warp-uniform
 
   // block-uniform trip count (warp collectives below need full warps); the
   // pass after the last quad empties both rings
@@ -688,23 +682,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
     }
     if (mcc) {
       __syncwarp();
-      for (;;) {
-        if (rcount >= 32 || (!more && wcount == 0 && rcount > 0)) {
-          // scatter up to 32 real collisions
-          const int take = min(rcount, 32);
-          if (lane < take) {
-            int pos = rhead + lane;
-            if (pos >= kReal) pos -= kReal;
-            collide_real(b, s, xi_[pos], k, (cur | (sample ? 2 : 0)) | (xp[pos] << 2), xe[pos], xg[pos],
-                         Ssm, Msm, sh);
-          }
-          rhead += take;
-          if (rhead >= kReal) rhead -= kReal;
-          rcount -= take;
-          __syncwarp();
-          continue;
-        }
-        if (!(wcount >= 32 || (!more && wcount > 0))) break;
+      while (wcount >= 32 || (!more && wcount > 0)) {
         // null-collision test of up to 32 candidates
         const int take = min(wcount, 32);
         const bool act = lane < take;
@@ -743,18 +721,21 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         int chosen = -1;
         if (act) chosen = select_process(SP, En, gm, R->ng, u24(ryv) * nu_max, &tot);
         if (tot > nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
+        // real collisions: one record each for the collision kernel
         const unsigned m = __ballot_sync(kFull, chosen >= 0);
-        if (chosen >= 0) {
-          int rp = rhead + rcount + __popc(m & lt_mask);
-          if (rp >= kReal) rp -= kReal;
-          if (chk(rp >= 0 && rp < kReal, 24, rp, kReal)) {
-            xi_[rp] = i;
-            xp[rp] = chosen;
-            xe[rp] = En;
-            xg[rp] = gm;
+        if (m) {
+          const int lead = __ffs(m) - 1;
+          unsigned long long base = 0ull;
+          if (lane == lead) base = atomicAdd((unsigned long long*)&ss->n_real, (unsigned long long)__popc(m));
+          base = __shfl_sync(kFull, base, lead);
+          if (chosen >= 0) {
+            const long long idx = (long long)base + __popc(m & lt_mask);
+            if (idx < G.real_cap)
+              G.real[idx] = make_int4(i, chosen, __float_as_int(En), __float_as_int(gm));
+            else
+              set_status(st, ECPIC_ERR_CAPACITY);
           }
         }
-        rcount += __popc(m);
         head += take;
         if (head >= kRing) head -= kRing;
         wcount -= take;
@@ -865,6 +846,37 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     if (beg >= end) continue;
     if (!chk(b.segs[s].run >= 0 && b.segs[s].run < b.max_slots, 23, s, b.nseg)) continue;
     pass_piece(b, s, beg, end, mode, Ssm, Msm, ring, sh);
+  }
+}
+
+// Real collisions recorded by this step's pass, all segments, equal records
+// per warp.  Process counters are summed over the lanes that share a
+// (segment, process) before one atomic each.
+__global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* pre = reinterpret_cast<long long*>(smem_raw);
+  __shared__ long long wsm[32];
+  const long long T = seg_prefix(b, MODE_STEP, -1, pre, wsm, 1, true);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * kCollideBlock;
+  for (long long w0 = (long long)blockIdx.x * kCollideBlock + (threadIdx.x & ~31); w0 < T; w0 += stride) {
+    const long long r = w0 + lane;
+    const bool valid = r < T;
+    int s = 0;
+    int4 rec = make_int4(0, -1, 0, 0);
+    if (valid) {
+      s = seg_find(pre, b.nseg, r);
+      const long long j = r - pre[s];
+      if (chk(j >= 0 && j < b.segs[s].real_cap, 25, j, b.segs[s].real_cap)) rec = b.segs[s].real[j];
+    }
+    const bool ok = valid && rec.y >= 0 && rec.y < kMaxProc;
+    const unsigned key = ok ? ((unsigned)s << 4) | (unsigned)rec.y : 0xFFFFFFFFu;
+    const unsigned grp = __match_any_sync(kFull, key);
+    if (ok && lane == __ffs(grp) - 1) {
+      const SegDev& G = b.segs[s];
+      atomicAdd(&b.rst[G.run].ctr[G.species][C_COLL0 + rec.y], (unsigned long long)__popc(grp));
+    }
+    if (ok) collide_real(b, s, rec.x, rec.y, __int_as_float(rec.z), __int_as_float(rec.w));
   }
 }
 
@@ -1061,6 +1073,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
         const long long n = ss->n_alloc < cap ? ss->n_alloc : cap;
         ss->n_proc = n;
         ss->n_alloc = n;
+        ss->n_real = 0;
       }
     }
   }
@@ -1384,7 +1397,7 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
          sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
-         sizeof(int) * (size_t)(3 * kRing + 4 * kReal) * (kPassBlock / 32);
+         sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32);
 }
 
 size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }
@@ -1405,6 +1418,12 @@ void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t 
   const size_t sm = pass_smem_bytes(b);
   set_smem_attr((const void*)k_pass, sm);
   k_pass<<<grid, kPassBlock, sm, s>>>(b, mode, only);
+}
+
+void launch_collide(const BatchView& b, int grid, cudaStream_t s) {
+  const size_t sm = sizeof(long long) * (size_t)(b.nseg + 1);
+  set_smem_attr((const void*)k_collide, sm);
+  k_collide<<<grid, kCollideBlock, sm, s>>>(b);
 }
 
 void launch_field(const BatchView& b, int advance, int only, cudaStream_t s) {

@@ -8,6 +8,7 @@ namespace ecpic {
 
 constexpr int kPassBlock = 256;
 constexpr int kFieldBlock = 512;
+constexpr int kCollideBlock = 256;
 
 struct BatchView {
   const RunDev* runs;   // device, max_slots
@@ -30,6 +31,7 @@ size_t field_smem_bytes(const BatchView& b);
 int pass_max_ctas_per_sm(const BatchView& b);
 
 void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s);
+void launch_collide(const BatchView& b, int grid, cudaStream_t s);
 void launch_field(const BatchView& b, int advance, int only, cudaStream_t s);
 void launch_phi(const BatchView& b, int slot, cudaStream_t s);
 void launch_sort(const BatchView& b, int grid, cudaStream_t s);

@@ -28,6 +28,20 @@ struct Carve {
   }
 };
 
+// Records for the real collisions of one step: at most one per candidate,
+// and the candidate count of n <= cap particles is binomial with the
+// null-collision probability P; mean + 12 standard deviations + 256 is never
+// exceeded in practice (an overflow fails the run with ECPIC_ERR_CAPACITY).
+long long real_capacity(const HostSpecies& sp, const RunSpec& s) {
+  double nu = 0.0;
+  uint32_t thr = 0;
+  null_rate(sp, s, &nu, &thr);
+  if (thr == 0 || sp.cap <= 0) return 0;
+  const double mean = (double)sp.cap * ((double)thr / 16777216.0);
+  const double bound = std::ceil(mean + 12.0 * std::sqrt(mean) + 256.0);
+  return bound < (double)sp.cap ? (long long)bound : (long long)sp.cap;
+}
+
 size_t layout_bytes(const RunSpec& s) {
   const size_t N = s.edges.size() - 1, ns = s.species.size();
   size_t b = 0;
@@ -54,6 +68,7 @@ size_t layout_bytes(const RunSpec& s) {
       const size_t c = (size_t)sp.cap;
       add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(8 * c);
     }
+  for (const auto& sp : s.species) add(16 * (size_t)real_capacity(sp, s));
   return b;
 }
 }  // namespace
@@ -417,6 +432,13 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
       std::memset(G.cell, 0, sizeof(G.cell));
       G.cap = 0;
     }
+    G.real = nullptr;
+    G.real_cap = 0;
+  }
+  for (int s = 0; s < ns; ++s) {
+    SegDev& G = h_segs_[R.seg0 + s];
+    G.real_cap = real_capacity(spec.species[s], spec);
+    G.real = cv.take<int4>((size_t)G.real_cap);
   }
   cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
                   stream_);
@@ -505,6 +527,7 @@ int Batch::ensure_graphs(std::string* err) {
     const int steps = which == 0 ? sort_every_ : 1;
     for (int t = 0; t < steps; ++t) {
       launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_collide(b, pass_grid_, stream_);
       launch_field(b, 1, -1, stream_);
     }
     if (which == 0) launch_sort(b, pass_grid_, stream_);
@@ -541,6 +564,7 @@ int Batch::step(long long n, std::string* err) {
       if (rc) return rc;
     } else {
       launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_collide(b, pass_grid_, stream_);
       launch_field(b, 1, -1, stream_);
     }
     --n;
@@ -556,10 +580,10 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
   cudaSetDevice(device_);
   if (pass_grid_ <= 0) pass_grid_ = choose_grid();
   const BatchView b = view();
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[5];
   for (auto& e : ev) cudaEventCreate(&e);
-  double acc[3] = {0, 0, 0};
-  long long cnt[3] = {0, 0, 0};
+  double acc[4] = {0, 0, 0, 0};
+  long long cnt[4] = {0, 0, 0, 0};
   int rc = ECPIC_OK;
   // ECPIC_SYNC_PHASES=1: wait after every kernel so a device error names it
   const char* sp = std::getenv("ECPIC_SYNC_PHASES");
@@ -569,6 +593,9 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
     launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
     cudaEventRecord(ev[1], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[1]), "pass kernel", err))) break;
+    launch_collide(b, pass_grid_, stream_);
+    cudaEventRecord(ev[4], stream_);
+    if (each && (rc = check(cudaEventSynchronize(ev[4]), "collision kernel", err))) break;
     launch_field(b, 1, -1, stream_);
     cudaEventRecord(ev[2], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[2]), "field kernel", err))) break;
@@ -589,21 +616,24 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
     }
     cudaEventRecord(ev[3], stream_);
     rc = check(cudaEventSynchronize(ev[3]), "profile step", err);
-    float a = 0, f = 0, c = 0;
+    float a = 0, x = 0, f = 0, c = 0;
     cudaEventElapsedTime(&a, ev[0], ev[1]);
-    cudaEventElapsedTime(&f, ev[1], ev[2]);
+    cudaEventElapsedTime(&x, ev[1], ev[4]);
+    cudaEventElapsedTime(&f, ev[4], ev[2]);
     cudaEventElapsedTime(&c, ev[2], ev[3]);
     acc[0] += a;
     acc[1] += f;
+    acc[3] += x;
     cnt[0] += 1;
     cnt[1] += 1;
+    cnt[3] += 1;
     if (sort) {
       acc[2] += c;
       cnt[2] += 4;
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (ms) ms[i] = acc[i];
     if (launches) launches[i] = cnt[i];
   }

@@ -268,11 +268,12 @@ class Run:
         _chk(self.h, self._L.ecpic_sort_now(self.h), "ecpic_sort_now")
 
     def profile_step(self, n):
-        ms = np.zeros(3)
-        cnt = np.zeros(3, np.int64)
+        ms = np.zeros(4)
+        cnt = np.zeros(4, np.int64)
         _chk(self.h, self._L.ecpic_profile_step(self.h, int(n), _p(ms), _p(cnt)),
              "ecpic_profile_step")
-        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], launches=cnt.tolist())
+        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], collide_ms=ms[3],
+                    launches=cnt.tolist())
 
     def set_pass_grid(self, ctas):
         _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
@@ -457,11 +458,12 @@ class Engine:
         return dict(particle_steps=ps.value, runs_finished=rf.value, bytes_resident=by.value)
 
     def profile(self, n):
-        ms = np.zeros(3)
-        cnt = np.zeros(3, np.int64)
+        ms = np.zeros(4)
+        cnt = np.zeros(4, np.int64)
         self._chk(self._L.ecpic_engine_profile(self.h, int(n), _p(ms), _p(cnt)),
                   "ecpic_engine_profile")
-        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], launches=cnt.tolist())
+        return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], collide_ms=ms[3],
+                    launches=cnt.tolist())
 
     def tune(self, pass_ctas=0, sort_every=16):
         self._chk(self._L.ecpic_engine_tune(self.h, int(pass_ctas), int(sort_every)),
