@@ -160,23 +160,64 @@ __device__ __forceinline__ int seg_find(const long long* pre, int nseg, long lon
 }
 
 // ----------------------------------------------------------------- deposit
-// Warp-aggregated fixed-point CIC deposit into shared memory: lanes that hold
-// the same cell add their shares once.  S[c] += 2^32 - r, S[c+1] += r with
-// r = floor(xi * 2^32) (xi * 2^32 is exact in FP32; rz truncation = floor).
-__device__ __forceinline__ void deposit_warp(unsigned long long* Ssm, bool valid, int c, float f,
-                                             int nmax) {
-  valid = valid && chk(c >= 0 && c < nmax, 1, c, nmax);
-  const unsigned key = valid ? (unsigned)c : 0xFFFFFFFFu;
-  const unsigned grp = __match_any_sync(kFull, key);
-  if (!valid) return;
-  const unsigned r = __float2uint_rz(f * 4294967296.0f);
-  const unsigned lo16 = __reduce_add_sync(grp, r & 0xFFFFu);
-  const unsigned hi16 = __reduce_add_sync(grp, r >> 16);
-  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) {
-    const unsigned long long sr = ((unsigned long long)hi16 << 16) + (unsigned long long)lo16;
-    const unsigned long long cnt = (unsigned long long)__popc(grp);
-    atomicAdd(Ssm + c, (cnt << 32) - sr);
-    atomicAdd(Ssm + c + 1, sr);
+// Fixed-point CIC deposit (Eq. 2-3) in units of 2^-32 particle: a particle at
+// (c, xi) with r = floor(xi 2^32) (xi * 2^32 is exact in FP32; rz truncation
+// = floor) adds 2^32 - r to node c and r to node c+1.  In shared memory each
+// cell keeps three 32-bit sums, updated with native 32-bit atomics: its
+// particle count, and the sums of the low and high 16 bits of r.  The flush
+// forms the node values, S[c] += cnt 2^32 - R and S[c+1] += R with
+// R = hi 2^16 + lo.  With at most kFlushParticles particles between flushes
+// no sum reaches 2^32.
+constexpr int kFlushParticles = 65536;
+constexpr int kFlushIters = kFlushParticles / (4 * kPassBlock);  // quad iterations of a block
+
+// Adds four particles (cells c[j] < 0 skipped); a thread's consecutive
+// particles in the same cell are merged first, so sorted data costs one
+// atomic triple per run.
+__device__ __forceinline__ void dep_add4(uint32_t* dcnt, uint32_t* dlo, uint32_t* dhi, const int c[4],
+                                         const float f[4]) {
+  unsigned lo[4], hi[4], cn[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool v = c[j] >= 0;
+    const unsigned r = v ? __float2uint_rz(f[j] * 4294967296.0f) : 0u;
+    lo[j] = r & 0xFFFFu;
+    hi[j] = r >> 16;
+    cn[j] = v ? 1u : 0u;
+  }
+#pragma unroll
+  for (int j = 3; j >= 1; --j) {
+    if (c[j] >= 0 && c[j] == c[j - 1]) {
+      lo[j - 1] += lo[j];
+      hi[j - 1] += hi[j];
+      cn[j - 1] += cn[j];
+      cn[j] = 0u;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (cn[j]) {
+      atomicAdd(dcnt + c[j], cn[j]);
+      atomicAdd(dlo + c[j], lo[j]);
+      atomicAdd(dhi + c[j], hi[j]);
+    }
+  }
+}
+
+// Adds the shared sums of cells [a, e) to the node array S in HBM and clears
+// them.  Every thread of the block calls it, between barriers.
+__device__ void dep_flush(uint32_t* dcnt, uint32_t* dlo, uint32_t* dhi, int a, int e,
+                          unsigned long long* S) {
+  for (int c = a + (int)threadIdx.x; c < e; c += (int)blockDim.x) {
+    const uint32_t n = dcnt[c];
+    if (n) {
+      const unsigned long long R = ((unsigned long long)dhi[c] << 16) + (unsigned long long)dlo[c];
+      atomicAdd(S + c, ((unsigned long long)n << 32) - R);
+      if (R) atomicAdd(S + c + 1, R);
+      dcnt[c] = 0u;
+      dlo[c] = 0u;
+      dhi[c] = 0u;
+    }
   }
 }
 
@@ -450,7 +491,7 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, i
 // 32-byte sectors anyway) and on energy-sample steps; otherwise the test
 // reads them per candidate.
 __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
-                           unsigned long long* Ssm, float* Msm, unsigned char* ring, PassShared& sh) {
+                           uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
@@ -490,6 +531,11 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   uint32_t* qr = reinterpret_cast<uint32_t*>(qi + kRing);
   float* qw = reinterpret_cast<float*>(qi + 2 * kRing);
   int head = 0, wcount = 0;  // warp-uniform
+  uint32_t* dcnt = dep;
+  uint32_t* dlo = dep + (b.nmax + 1);
+  uint32_t* dhi = dep + 2 * (b.nmax + 1);
+  unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
+  int since_flush = 0;
 
   // block-uniform trip count (warp collectives below need full warps); the
   // pass after the last quad empties both rings
@@ -663,11 +709,10 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
       }
       // fixed-point CIC deposit of the new positions (Eq. 2-3); vx moments
       // (pre-collision: the collision adds the change)
+      dep_add4(dcnt, dlo, dhi, c, f);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const bool val = c[j] >= 0;
-        deposit_warp(Ssm, val, c[j], f[j], b.nmax);
-        if (val) {
+        if (c[j] >= 0) {
           my_lo = min(my_lo, c[j]);
           my_hi = max(my_hi, c[j] + 1);
           if (sample && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
@@ -743,6 +788,12 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
       }
     }
     if (!more) break;
+    if (++since_flush == kFlushIters) {
+      __syncthreads();
+      dep_flush(dcnt, dlo, dhi, 0, N, Sg);
+      __syncthreads();
+      since_flush = 0;
+    }
   }
 
   // piece epilogue: node range, energy, counters, flush to HBM
@@ -777,24 +828,17 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   __syncthreads();
   const int flo = sh.lohi[0], fhi = chk(sh.lohi[1] <= N, 8, sh.lohi[1], N) ? sh.lohi[1] : N;
   const int Nm = b.nmax + 1;
-  unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   double* md = R->momd + (size_t)sp * 2 * (N + 1);
   // an empty range (no live particle in the piece) is (INT_MAX, -1): skip it
   // before forming flo + threadIdx.x, which would overflow
+  if (flo < fhi) dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
   const int nbeg = flo <= fhi ? flo + (int)threadIdx.x : fhi + 1;
-  for (int nn = nbeg; nn <= fhi; nn += kPassBlock) {
-    const unsigned long long val = Ssm[nn];
-    if (val) {
-      atomicAdd(Sg + nn, val);
-      Ssm[nn] = 0ull;
-    }
-    if (sample) {
-      const float m1 = Msm[nn], m2 = Msm[Nm + nn];
-      if (m1 != 0.0f) atomicAdd(md + nn, (double)m1);
-      if (m2 != 0.0f) atomicAdd(md + (N + 1) + nn, (double)m2);
-      Msm[nn] = 0.0f;
-      Msm[Nm + nn] = 0.0f;
-    }
+  for (int nn = nbeg; nn <= fhi && sample; nn += kPassBlock) {
+    const float m1 = Msm[nn], m2 = Msm[Nm + nn];
+    if (m1 != 0.0f) atomicAdd(md + nn, (double)m1);
+    if (m2 != 0.0f) atomicAdd(md + (N + 1) + nn, (double)m2);
+    Msm[nn] = 0.0f;
+    Msm[Nm + nn] = 0.0f;
   }
   if (threadIdx.x == 0) {
     const unsigned long long dead = sh.ctr[C_ABS_L] + sh.ctr[C_ABS_R] + sh.ctr[C_NAN];
@@ -819,12 +863,14 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
 __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
-  unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
-  float* Msm = reinterpret_cast<float*>(Ssm + b.nmax + 1);
+  uint32_t* dep = reinterpret_cast<uint32_t*>(pre + b.nseg + 1);  // 3 (nmax+1): count, lo, hi
+  float* Msm = reinterpret_cast<float*>(dep + 3 * (b.nmax + 1));
   unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 2 * (b.nmax + 1));
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
-    Ssm[i] = 0ull;
+    dep[i] = 0u;
+    dep[b.nmax + 1 + i] = 0u;
+    dep[2 * (b.nmax + 1) + i] = 0u;
     Msm[i] = 0.0f;
     Msm[b.nmax + 1 + i] = 0.0f;
   }
@@ -845,7 +891,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const long long end = min(hi, pre[s + 1]) - pre[s];
     if (beg >= end) continue;
     if (!chk(b.segs[s].run >= 0 && b.segs[s].run < b.max_slots, 23, s, b.nseg)) continue;
-    pass_piece(b, s, beg, end, mode, Ssm, Msm, ring, sh);
+    pass_piece(b, s, beg, end, mode, dep, Msm, ring, sh);
   }
 }
 
@@ -1359,23 +1405,37 @@ __global__ void __launch_bounds__(kPassBlock) k_deposit_device(int N, long long 
                                                                const float* xi,
                                                                unsigned long long* S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned long long* Ssm = reinterpret_cast<unsigned long long*>(smem_raw);
-  for (int i = threadIdx.x; i <= N; i += kPassBlock) Ssm[i] = 0ull;
+  uint32_t* dcnt = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* dlo = dcnt + (N + 1);
+  uint32_t* dhi = dcnt + 2 * (N + 1);
+  for (int i = threadIdx.x; i < 3 * (N + 1); i += kPassBlock) dcnt[i] = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * kPassBlock + (threadIdx.x & ~31); base < n;
+  const long long nq = (n + 3) / 4;
+  int since_flush = 0;
+  // block-uniform trip count: the periodic flush needs every thread
+  for (long long base = (long long)blockIdx.x * kPassBlock; base < nq;
        base += (long long)gridDim.x * kPassBlock) {
-    const long long i = base + lane;
-    int c = i < n ? cell[i] : -1;
-    const bool valid = c >= 0 && c < N;
-    const float f = valid ? xi[i] : 0.0f;
-    deposit_warp(Ssm, valid, c, f, N);
+    const long long q = base + threadIdx.x;
+    int c[4];
+    float f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long i = 4 * q + j;
+      const int cc = (q < nq && i < n) ? cell[i] : -1;
+      const bool ok = cc >= 0 && cc < N;
+      c[j] = ok ? cc : -1;
+      f[j] = ok ? xi[i] : 0.0f;
+    }
+    dep_add4(dcnt, dlo, dhi, c, f);
+    if (++since_flush == kFlushIters) {
+      __syncthreads();
+      dep_flush(dcnt, dlo, dhi, 0, N, S);
+      __syncthreads();
+      since_flush = 0;
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i <= N; i += kPassBlock) {
-    const unsigned long long v = Ssm[i];
-    if (v) atomicAdd(S + i, v);
-  }
+  dep_flush(dcnt, dlo, dhi, 0, N, S);
 }
 
 __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t* key,
@@ -1396,7 +1456,7 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 // ----------------------------------------------------------------- launchers
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
-         sizeof(unsigned long long) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
+         3 * sizeof(uint32_t) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
          sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32);
 }
 
@@ -1470,8 +1530,8 @@ void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
                            unsigned long long* S, cudaStream_t s) {
   long long blocks = (n + kPassBlock * 8 - 1) / (kPassBlock * 8);
   if (blocks < 1) blocks = 1;
-  if (blocks > 1024) blocks = 1024;
-  const size_t sm = sizeof(unsigned long long) * (size_t)(N + 1);
+  if (blocks > 304) blocks = 304;
+  const size_t sm = 3 * sizeof(uint32_t) * (size_t)(N + 1);
   set_smem_attr((const void*)k_deposit_device, sm);
   k_deposit_device<<<(unsigned)blocks, kPassBlock, sm, s>>>(N, n, cell, xi, S);
 }

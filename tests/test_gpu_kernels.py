@@ -73,6 +73,23 @@ def test_deposit_device_bit_exact(E, N, n, order):
     assert int(got.sum(dtype=np.uint64)) == n * 2 ** 32
 
 
+@pytest.mark.parametrize("N,order", [(2048, "random"), (96, "clustered")])
+def test_deposit_device_many_flushes(E, N, order):
+    # 2^25 + 5 particles over at most 304 blocks: each block adds more than
+    # 65,536 particles, so its shared sums are flushed to S mid-way
+    n = (1 << 25) + 5
+    rng = np.random.default_rng(N)
+    if order == "clustered":
+        cell = rng.integers(N // 2 - 2, N // 2 + 2, n).astype(np.int32)
+    else:
+        cell = rng.integers(0, N, n).astype(np.int32)
+    xi = rng.random(n, dtype=np.float32)
+    xi[:1000] = np.float32(1) - np.float32(2 ** -24)
+    got, want = _deposit_case(E, N, cell, xi)
+    assert np.array_equal(got, want)
+    assert int(got.sum(dtype=np.uint64)) == n * 2 ** 32
+
+
 def test_deposit_device_skips_dead_and_empty(E):
     rng = np.random.default_rng(1)
     N, n = 100, 5000
