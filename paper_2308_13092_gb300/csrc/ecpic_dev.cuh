@@ -47,6 +47,8 @@ struct SpeciesDev {
   float m_frac;         // m_gas / (m + m_gas)
   float mass_frac;      // m / (m + m_gas)
   float nu_max;         // 1/s (FP32 copy of the host FP64 value)
+  float nu_bnd;         // n_g * max over nodes of the summed cross sections, padded by
+                        // 2^-16 so that nu_bnd * |g| bounds the FP32 total rate
   uint32_t thr24;       // candidate iff (r0 >> 8) < thr24
   float dE_inv;
   int ntab;

@@ -690,6 +690,17 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
             }
         }
         if (mcc) {
+          // a candidate with Rr >= nu_bnd |g| is a null collision whatever its
+          // energy (the total rate never exceeds nu_bnd |g|): where |g| is at
+          // hand, only the others go on to the cross-section test
+          const float nu_max = SP->nu_max, nu_bnd = SP->nu_bnd;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool test = cand[j] && (!yz_stream ||
+                u24(ry[j]) * nu_max < nu_bnd * sqrtf(v[j] * v[j] + yz[j]));
+            ncand += cand[j] ? 1u : 0u;
+            cand[j] = test;
+          }
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const unsigned m = __ballot_sync(kFull, cand[j]);
@@ -703,7 +714,6 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
               }
             }
             wcount += __popc(m);
-            ncand += cand[j] ? 1u : 0u;
           }
         }
       }
@@ -762,9 +772,10 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         }
         const float gm = sqrtf(g2), En = SP->half_m_over_e * g2;
         const float nu_max = SP->nu_max;
+        const float Rr = u24(ryv) * nu_max;
         float tot = 0.0f;
         int chosen = -1;
-        if (act) chosen = select_process(SP, En, gm, R->ng, u24(ryv) * nu_max, &tot);
+        if (act && Rr < SP->nu_bnd * gm) chosen = select_process(SP, En, gm, R->ng, Rr, &tot);
         if (tot > nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
         // real collisions: one record each for the collision kernel
         const unsigned m = __ballot_sync(kFull, chosen >= 0);

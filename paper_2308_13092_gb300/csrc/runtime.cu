@@ -387,6 +387,15 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     D.heavy = 0;
     D.ntab = hs.procs.empty() ? 2 : (int)hs.procs[0].sigma.size();
     D.dE_inv = hs.procs.empty() ? 1.0f : (float)(1.0 / hs.procs[0].dE);
+    {
+      double smax = 0.0;
+      for (size_t i = 0; !hs.procs.empty() && i < hs.procs[0].sigma.size(); ++i) {
+        double a = 0.0;
+        for (const auto& hp : hs.procs) a += (double)hp.sigma[i];
+        smax = a > smax ? a : smax;
+      }
+      D.nu_bnd = (float)((spec.gas ? spec.ng : 0.0) * smax * (1.0 + 1.0 / 65536.0));
+    }
     D.np4 = (D.nproc + 3) / 4;
     D.sig4 = nullptr;
     for (int p = 0; p < kMaxProc; ++p) D.thr_all[p] = FLT_MAX;
