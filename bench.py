@@ -50,6 +50,24 @@ from paper_2308_13092_gb300 import inputs as I  # noqa: E402
 BYTES_PER_PARTICLE_STEP = 40
 METRIC = "particle-steps/s"
 N_RUNS = 256
+SORT_EVERY = 16  # counting-sort cadence K of the headline workload
+
+# DRAM traffic of k_pass measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of one stepping launch on the 64-run manifest, see
+# profiles/k_pass_batched64.md), per particle-step.  It is reported only while
+# the kernel sources hash to the measured version; after any change the
+# traffic is unknown (null) until it is measured again.
+TRAFFIC = {"sources_sha256": "95172eb32cd97094baab5af01f5d8a3ffc992c2c8357648e8dcb874b907f4363",
+           "dram_bytes_per_particle_step": 525.727e6 / 14.326e6}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "ecpic_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_13092_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def parse():
@@ -361,6 +379,8 @@ def main():
     cfgs = manifest(rank, args, total)
     eng = ecpic.Engine(device=local, stream=stream.cuda_stream, max_slots=len(cfgs),
                        max_cells=1024)
+    eng_sort_every = SORT_EVERY
+    eng.tune(0, eng_sort_every)
     for c in cfgs:
         eng.submit(c)
     eng.pump(0)  # admit and load everything
@@ -402,6 +422,10 @@ def main():
     bytes_per_launch = BYTES_PER_PARTICLE_STEP * ps_prof / max(1, nprof)
     achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
     launches_per_step = sum(prof["launches"]) / max(1, nprof)
+    traffic = None
+    if kernel_sources_sha256() == TRAFFIC["sources_sha256"]:
+        traffic = TRAFFIC["dram_bytes_per_particle_step"] * ps_prof / max(1, nprof)
+    sort_every = eng_sort_every
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -429,17 +453,19 @@ def main():
                                    f"(seeded manifest), {n_part} initial particles, cells "
                                    f"{min(c.N for c in cfgs)}-{max(c.N for c in cfgs)}",
                        "runs_per_gpu": len(cfgs), "l2": "inputs larger than L2 (1.5 GB state)",
-                       "sort_every": 16, "sample_every": 40, "scheme": "EC",
+                       "sort_every": sort_every, "sample_every": 40, "scheme": "EC",
                        "arithmetic": "FP32 particles, FP64 field solve"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "k_pass",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "k_pass",
+                         "traffic_unit": "bytes per launch (DRAM read + write)",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
                          "pass_ms_avg": pass_ms,
                          "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1]),
+                         "collide_ms_avg": prof["collide_ms"] / max(1, prof["launches"][3]),
                          "sort_ms_per_step": prof["sort_ms"] / max(1, nprof),
                          "pass_share": prof["pass_ms"] / max(1e-9, prof["pass_ms"] + prof["field_ms"]
-                                                             + prof["sort_ms"])},
+                                                             + prof["sort_ms"] + prof["collide_ms"])},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
