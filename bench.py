@@ -84,6 +84,19 @@ def parse():
     return ap.parse_args()
 
 
+def combine_ranks(ms, ps):
+    """Whole-job figures of a weak-scaling replica run: the slowest rank's
+    time and the particle-steps of all ranks (host-side gloo reductions; the
+    ranks share no data)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(ps)], dtype=torch.float64)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -409,12 +422,7 @@ def main():
     eng.close()
 
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([float(ps)], dtype=torch.float64)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        ms, ps = float(t.item()), float(p.item())
+        ms, ps = combine_ranks(ms, ps)
 
     value = ps / (ms * 1e-3)
     hbm, peak_kind = peaks()
