@@ -1,0 +1,105 @@
+"""Full-run statistical parity with the oracle: time-averaged profiles and
+event rates of the small discharge (128 cells, 16,384 particles at start,
+1200 steps of its ionisation-driven growth, averages sampled every 10 steps,
+capacity doubled so that no run fills it).
+
+A run's trajectory depends on FP32 vs FP64 rounding, so the GPU and the
+oracle decorrelate after some hundreds of steps even from one seed.  They are
+compared as ensembles: the mean of 8 GPU runs against the mean of 2 oracle
+runs (other seeds).  The noise of a single run is estimated from the spread
+of the 8 GPU runs; the oracle pair must show the same spread, and the two
+means must agree within three standard errors of their difference."""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_2308_13092_gb300 import inputs as I
+from helpers import oracle_from_config, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 1200
+GPU_SEEDS = tuple(range(100, 108))
+ORACLE_SEEDS = (200, 201)
+PROFILES = ("ne", "ni", "phi", "Te", "Ti")
+
+
+def _cfg(seed):
+    c = I.config_small(seed=seed)
+    c.sample_every = 10
+    c.n_steps = STEPS
+    for sp in c.species:
+        sp.capacity *= 2
+    return c
+
+
+def _summary(avg, species):
+    """Profiles and per-step event rates of one run."""
+    out = dict(ne=np.asarray(avg["density"][0], float), ni=np.asarray(avg["density"][1], float),
+               phi=np.asarray(avg["phi"], float), Te=np.asarray(avg["Tx"][0], float),
+               Ti=np.asarray(avg["Tx"][1], float))
+    e, i = species[0], species[1]
+    out["rates"] = np.array([e["collisions"][0], e["collisions"][1], e["collisions"][2],
+                             i["collisions"][0], i["collisions"][1], e["births"],
+                             e["absorbed_left"] + e["absorbed_right"],
+                             i["absorbed_left"] + i["absorbed_right"]], float) / STEPS
+    return out
+
+
+@pytest.fixture(scope="module")
+def ensembles():
+    require_gpu()
+    from paper_2308_13092_gb300 import ecpic
+    eng = ecpic.Engine(max_slots=len(GPU_SEEDS), max_cells=256)
+    tickets = [eng.submit(_cfg(s)) for s in GPU_SEEDS]
+    for _ in range(100):
+        r, q = eng.pump(500)
+        if r == 0 and q == 0:
+            break
+    gpu = []
+    for t in tickets:
+        res = eng.poll(t, diagnostics=True, profiles=True)
+        assert res["state"] == 2
+        d = res["diag"]
+        assert d["step"] == STEPS
+        gpu.append(_summary(d, d["species"]))
+    eng.close()
+    ora = []
+    for s in ORACLE_SEEDS:
+        o = oracle_from_config(_cfg(s))
+        o.step(STEPS, allow_capacity=True)
+        ora.append(_summary(o.averages(), o.counters()["species"]))
+        o.close()
+    return gpu, ora
+
+
+def _single_run_noise(runs, key):
+    pairs = [rel_l2(a[key], b[key]) for a, b in itertools.combinations(runs, 2)]
+    return float(np.mean(pairs)) / np.sqrt(2.0)
+
+
+@pytest.mark.parametrize("key", PROFILES)
+def test_profiles_match_oracle_ensemble(ensembles, key):
+    gpu, ora = ensembles
+    sig = _single_run_noise(gpu, key)
+    sig_o = rel_l2(ora[0][key], ora[1][key]) / np.sqrt(2.0)
+    # the oracle pair scatters like the GPU runs do
+    assert sig / 4 <= sig_o <= 4 * sig, (key, sig, sig_o)
+    mg = np.mean([g[key] for g in gpu], axis=0)
+    mo = np.mean([o[key] for o in ora], axis=0)
+    expected = sig * np.sqrt(1.0 / len(gpu) + 1.0 / len(ora))
+    assert rel_l2(mg, mo) <= 3.0 * expected + 2e-3, (key, rel_l2(mg, mo), expected)
+
+
+def test_event_rates_match_oracle_ensemble(ensembles):
+    gpu, ora = ensembles
+    G = np.array([g["rates"] for g in gpu])
+    O = np.array([o["rates"] for o in ora])
+    names = ["e elastic", "excitation", "ionisation", "ion elastic", "charge exchange",
+             "births", "electron wall loss", "ion wall loss"]
+    assert np.all(G.mean(0) > 0), dict(zip(names, G.mean(0)))
+    sd = G.std(0, ddof=1)
+    tol = 3.0 * sd * np.sqrt(1.0 / len(gpu) + 1.0 / len(ora)) + 1e-3 * G.mean(0)
+    for n, g, o, t in zip(names, G.mean(0), O.mean(0), tol):
+        assert abs(g - o) <= t, (n, g, o, t)
