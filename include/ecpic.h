@@ -163,6 +163,16 @@ int ecpic_sort_now(ecpic_run* run);
 int ecpic_profile_step(ecpic_run* run, int64_t n_steps, double* ms, int64_t* launches);
 /* Pass-kernel grid size override (0 = automatic); for tuning. */
 int ecpic_set_pass_grid(ecpic_run* run, int ctas);
+/* Autotuner (SURVEY plan: sort cadence K, particles per CTA): times the
+ * graph-replayed step for each candidate pair of counting-sort cadence K in
+ * {8, 16, 32, 64} and pass grid (automatic, one wave at full or half
+ * occupancy, two waves), steps_per_trial steps each (at least 2K), and keeps
+ * the pair with the least device time per particle-step.  The trials advance
+ * the run for real; results do not depend on K or the grid (integer
+ * deposit, id-keyed random numbers).  Outputs may be NULL: the chosen K, the
+ * chosen grid (0 = automatic) and its ns per particle-step.  Synchronises. */
+int ecpic_autotune(ecpic_run* run, int64_t steps_per_trial, int* sort_every, int* pass_ctas,
+                   double* ns_per_particle_step);
 
 /* ------------------------------------------------------------------ */
 /* Batched and served runs.  An engine keeps up to max_slots independent
@@ -235,6 +245,10 @@ int ecpic_engine_stats(ecpic_engine* eng, int64_t* particle_steps, int64_t* runs
                        int64_t* bytes_resident);
 /* Tuning: pass-kernel CTAs (0 = all SMs), counting-sort cadence. */
 int ecpic_engine_tune(ecpic_engine* eng, int pass_ctas, int sort_every);
+/* Autotuner over the resident runs, as ecpic_autotune (advances them; runs
+ * that reach their end during the trials finish normally). */
+int ecpic_engine_autotune(ecpic_engine* eng, int64_t steps_per_trial, int* sort_every,
+                          int* pass_ctas, double* ns_per_particle_step);
 /* Measurement: advance the resident runs n_steps with plain launches,
  * bracketing each kernel phase with CUDA events on the engine's stream (see
  * ecpic_profile_step: ms[0..3], launches[0..3]); synchronises.  No admission

@@ -346,6 +346,15 @@ int ecpic_profile_step(ecpic_run* r, int64_t n, double* ms, int64_t* launches) {
   return rc ? fail(r, rc, err) : ECPIC_OK;
 }
 
+int ecpic_autotune(ecpic_run* r, int64_t steps_per_trial, int* sort_every, int* pass_ctas,
+                   double* ns_per_particle_step) {
+  if (!r || steps_per_trial < 1) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  std::string err;
+  const int rc = r->batch->autotune(steps_per_trial, sort_every, pass_ctas, ns_per_particle_step, &err);
+  return rc ? fail(r, rc, err) : ECPIC_OK;
+}
+
 int ecpic_set_pass_grid(ecpic_run* r, int ctas) {
   if (!r || ctas < 0) return ECPIC_ERR_ARG;
   if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");

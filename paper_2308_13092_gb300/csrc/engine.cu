@@ -321,6 +321,14 @@ int ecpic_engine_profile(ecpic_engine* e, int64_t n, double* ms, int64_t* launch
   return rc ? efail(e, rc, err) : ECPIC_OK;
 }
 
+int ecpic_engine_autotune(ecpic_engine* e, int64_t steps_per_trial, int* sort_every, int* pass_ctas,
+                          double* ns_per_particle_step) {
+  if (!e || steps_per_trial < 1) return ECPIC_ERR_ARG;
+  std::string err;
+  const int rc = e->batch->autotune(steps_per_trial, sort_every, pass_ctas, ns_per_particle_step, &err);
+  return rc ? efail(e, rc, err) : ECPIC_OK;
+}
+
 int ecpic_engine_tune(ecpic_engine* e, int pass_ctas, int sort_every) {
   if (!e || pass_ctas < 0 || sort_every < 1) return ECPIC_ERR_ARG;
   e->batch->set_pass_grid(pass_ctas);

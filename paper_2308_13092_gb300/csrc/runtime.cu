@@ -657,6 +657,72 @@ int Batch::sort_now(std::string* err) {
   return check(cudaGetLastError(), "sort", err);
 }
 
+int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, std::string* err) {
+  cudaSetDevice(device_);
+  if (steps < 1) {
+    if (err) *err = "steps per trial must be positive";
+    return ECPIC_ERR_ARG;
+  }
+  // candidates: the counting-sort cadence (8-64 steps) and the pass grid
+  // (automatic = 0, one wave at full occupancy, one at half, two waves)
+  const int occ = pass_max_ctas_per_sm(view());
+  std::vector<int> grids = {0, occ * sm_count_};
+  if (occ >= 2) grids.push_back((occ / 2) * sm_count_);
+  grids.push_back(2 * occ * sm_count_);
+  const int Ks[4] = {8, 16, 32, 64};
+  const int K0 = sort_every_, G0 = pass_grid_override_;
+  auto psteps = [&](unsigned long long* out) -> int {
+    std::vector<RunState> st;
+    const int rc = read_states(&st, err);
+    if (rc) return rc;
+    unsigned long long t = 0;
+    for (int s = 0; s < max_slots_; ++s)
+      if (active_[s]) t += st[s].psteps;
+    *out = t;
+    return ECPIC_OK;
+  };
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double best = -1.0;
+  int bestK = K0, bestG = G0;
+  int rc = ECPIC_OK;
+  for (int K : Ks) {
+    for (int g : grids) {
+      set_pass_grid(g);
+      set_sort_every(K);
+      const long long n = ((std::max(steps, 2LL * K) + K - 1) / K) * K;
+      if ((rc = step(K, err))) break;  // builds the graphs, starts the cadence
+      unsigned long long p0 = 0, p1 = 0;
+      if ((rc = psteps(&p0))) break;
+      cudaEventRecord(a, stream_);
+      if ((rc = step(n, err))) break;
+      cudaEventRecord(b, stream_);
+      if ((rc = check(cudaEventSynchronize(b), "autotune", err))) break;
+      if ((rc = psteps(&p1))) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (p1 <= p0) continue;  // nothing left to step
+      const double ns = 1e6 * (double)ms / (double)(p1 - p0);
+      if (best < 0.0 || ns < best) {
+        best = ns;
+        bestK = K;
+        bestG = g;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  set_pass_grid(bestG);
+  set_sort_every(bestK);
+  if (rc) return rc;
+  if (K_out) *K_out = bestK;
+  if (grid_out) *grid_out = bestG;
+  if (ns_out) *ns_out = best;
+  return ECPIC_OK;
+}
+
 int Batch::set_sort_every(int k) {
   if (k < 1) return ECPIC_ERR_ARG;
   sort_every_ = k;

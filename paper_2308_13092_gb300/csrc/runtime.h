@@ -90,6 +90,10 @@ class Batch {
   int read_states(std::vector<RunState>* out, std::string* err);
   int set_sort_every(int k);
   void set_pass_grid(int g) { pass_grid_override_ = g; invalidate_graphs(); }
+  // measure (sort cadence, pass grid) candidates on the resident runs and
+  // keep the fastest per particle-step; advances the runs (synchronises)
+  int autotune(long long steps_per_trial, int* sort_every, int* pass_ctas, double* ns_per_pstep,
+               std::string* err);
   int pass_grid() const { return pass_grid_; }
   int sort_every() const { return sort_every_; }
   void set_use_graphs(bool on) { use_graphs_ = on; }

@@ -78,6 +78,8 @@ SIGNATURES = {
     "ecpic_engine_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
     "ecpic_engine_tune": (i32, [vp, i32, i32]),
     "ecpic_engine_profile": (i32, [vp, i64, vp, vp]),
+    "ecpic_engine_autotune": (i32, [vp, i64, vp, vp, vp]),
+    "ecpic_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
     "ecpic_destroy": (None, [vp]),
     "ecpic_last_error": (C.c_char_p, [vp]),
@@ -278,6 +280,12 @@ class Run:
     def set_pass_grid(self, ctas):
         _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
 
+    def autotune(self, steps_per_trial=64):
+        k, g, ns = C.c_int(), C.c_int(), C.c_double()
+        _chk(self.h, self._L.ecpic_autotune(self.h, int(steps_per_trial), C.byref(k), C.byref(g),
+                                            C.byref(ns)), "ecpic_autotune")
+        return dict(sort_every=k.value, pass_ctas=g.value, ns_per_particle_step=ns.value)
+
     def nu_max(self, species):
         nu = C.c_double()
         t = C.c_uint32()
@@ -464,6 +472,12 @@ class Engine:
                   "ecpic_engine_profile")
         return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], collide_ms=ms[3],
                     launches=cnt.tolist())
+
+    def autotune(self, steps_per_trial=64):
+        k, g, ns = C.c_int(), C.c_int(), C.c_double()
+        self._chk(self._L.ecpic_engine_autotune(self.h, int(steps_per_trial), C.byref(k),
+                                                C.byref(g), C.byref(ns)), "ecpic_engine_autotune")
+        return dict(sort_every=k.value, pass_ctas=g.value, ns_per_particle_step=ns.value)
 
     def tune(self, pass_ctas=0, sort_every=16):
         self._chk(self._L.ecpic_engine_tune(self.h, int(pass_ctas), int(sort_every)),
