@@ -115,6 +115,21 @@ struct RunState {
   unsigned long long ctr[kMaxSpecies][kNumCtr];
 };
 
+// A real collision recorded by the pass for the collision kernel, with the
+// particle's state after the push (48 B, written and read as three 16-byte
+// words).
+struct __align__(16) RealRec {
+  uint64_t id;
+  int i;            // index in the current buffer set
+  int chosen;       // process
+  float En, gm;     // energy (eV) and relative speed (m/s) of the null-collision test
+  float vx, vy, vz;
+  int c;
+  float f;
+  int pad;
+};
+static_assert(sizeof(RealRec) == 48, "RealRec layout");
+
 struct SegDev {
   int32_t* cell[2];
   float* xi[2];
@@ -128,8 +143,8 @@ struct SegDev {
   int hoff;             // offset of this segment's histogram (N ints)
   int pad;
   // real collisions of the current step, recorded by the pass for the
-  // collision kernel: {index, process, E (eV) bits, |g| (m/s) bits}
-  int4* real;
+  // collision kernel
+  RealRec* real;
   long long real_cap;
 };
 

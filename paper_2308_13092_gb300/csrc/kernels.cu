@@ -403,14 +403,15 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   return make_float3(v1 * d0, v1 * d1, v1 * d2);
 }
 
-// A real (non-null) collision of process `chosen` at energy En and relative
-// speed gm (Sec. 2a step 6), as recorded by the pass: reloads the pushed
-// particle, redraws Philox block A (scattering angles) and, for heavy species,
-// block B (the target neutral's velocity), and scatters.  On sample steps the
-// pass has already added the pre-collision vx moments; the change is added
-// here.
-__device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, int chosen, float En,
-                                             float gm) {
+// A real (non-null) collision as recorded by the pass (Sec. 2a step 6):
+// process, energy En and relative speed gm of the null-collision test, and
+// the particle's pushed state.  Redraws Philox block A (scattering angles)
+// and, for heavy species, block B (the target neutral's velocity), scatters
+// and writes the new velocity.  On sample steps the pass has already added
+// the pre-collision vx moments; the change is added here.
+__device__ __forceinline__ void collide_real(const BatchView& b, int s, const RealRec& rec) {
+  const int i = rec.i, chosen = rec.chosen;
+  const float En = rec.En, gm = rec.gm;
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
@@ -422,12 +423,12 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int i, i
   const int N = R->N;
   const uint64_t seed = R->seed;
   if (!chk(i >= 0 && i < G.cap && chosen >= 0 && chosen < SP->nproc, 6, i, G.cap)) return;
-  const int c = G.cell[cur][i];
+  const int c = rec.c;
   if (!chk(c >= 0 && c < N, 7, c, N)) return;
-  const float f = G.xi[cur][i];
-  float vx = G.vx[cur][i], vy = G.vy[cur][i], vz = G.vz[cur][i];
+  const float f = rec.f;
+  float vx = rec.vx, vy = rec.vy, vz = rec.vz;
   const float vx_old = vx;
-  const uint64_t id = G.id[cur][i];
+  const uint64_t id = rec.id;
   const uint4 A = draw(seed, id, (uint32_t)k, (uint32_t)sp << 8);
   float gx = vx, gy = vy, gz = vz, vnx = 0.f, vny = 0.f, vnz = 0.f;
   if (SP->heavy) {
@@ -777,7 +778,8 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         int chosen = -1;
         if (act && Rr < SP->nu_bnd * gm) chosen = select_process(SP, En, gm, R->ng, Rr, &tot);
         if (tot > nu_max) atomicAdd(&sh.ctr[C_CLAMPS], 1ull);
-        // real collisions: one record each for the collision kernel
+        // real collisions: a record each, with the particle's pushed state
+        // (still in L1/L2 here), for the collision kernel
         const unsigned m = __ballot_sync(kFull, chosen >= 0);
         if (m) {
           const int lead = __ffs(m) - 1;
@@ -786,10 +788,16 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
           base = __shfl_sync(kFull, base, lead);
           if (chosen >= 0) {
             const long long idx = (long long)base + __popc(m & lt_mask);
-            if (idx < G.real_cap)
-              G.real[idx] = make_int4(i, chosen, __float_as_int(En), __float_as_int(gm));
-            else
+            if (idx < G.real_cap) {
+              const uint64_t id = pid[i];
+              int4* dst = reinterpret_cast<int4*>(G.real + idx);  // RealRec field order
+              dst[0] = make_int4((int)(uint32_t)id, (int)(uint32_t)(id >> 32), i, chosen);
+              dst[1] = make_int4(__float_as_int(En), __float_as_int(gm), __float_as_int(pvx[i]),
+                                 __float_as_int(pvy[i]));
+              dst[2] = make_int4(__float_as_int(pvz[i]), pc[i], __float_as_int(pxi[i]), 0);
+            } else {
               set_status(st, ECPIC_ERR_CAPACITY);
+            }
           }
         }
         head += take;
@@ -920,20 +928,34 @@ __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
     const long long r = w0 + lane;
     const bool valid = r < T;
     int s = 0;
-    int4 rec = make_int4(0, -1, 0, 0);
+    RealRec rec;
+    rec.chosen = -1;
     if (valid) {
       s = seg_find(pre, b.nseg, r);
       const long long j = r - pre[s];
-      if (chk(j >= 0 && j < b.segs[s].real_cap, 25, j, b.segs[s].real_cap)) rec = b.segs[s].real[j];
+      if (chk(j >= 0 && j < b.segs[s].real_cap, 25, j, b.segs[s].real_cap)) {
+        const int4* src = reinterpret_cast<const int4*>(b.segs[s].real + j);  // RealRec field order
+        const int4 w0 = src[0], w1 = src[1], w2 = src[2];
+        rec.id = (uint64_t)(uint32_t)w0.x | ((uint64_t)(uint32_t)w0.y << 32);
+        rec.i = w0.z;
+        rec.chosen = w0.w;
+        rec.En = __int_as_float(w1.x);
+        rec.gm = __int_as_float(w1.y);
+        rec.vx = __int_as_float(w1.z);
+        rec.vy = __int_as_float(w1.w);
+        rec.vz = __int_as_float(w2.x);
+        rec.c = w2.y;
+        rec.f = __int_as_float(w2.z);
+      }
     }
-    const bool ok = valid && rec.y >= 0 && rec.y < kMaxProc;
-    const unsigned key = ok ? ((unsigned)s << 4) | (unsigned)rec.y : 0xFFFFFFFFu;
+    const bool ok = valid && rec.chosen >= 0 && rec.chosen < kMaxProc;
+    const unsigned key = ok ? ((unsigned)s << 4) | (unsigned)rec.chosen : 0xFFFFFFFFu;
     const unsigned grp = __match_any_sync(kFull, key);
     if (ok && lane == __ffs(grp) - 1) {
       const SegDev& G = b.segs[s];
-      atomicAdd(&b.rst[G.run].ctr[G.species][C_COLL0 + rec.y], (unsigned long long)__popc(grp));
+      atomicAdd(&b.rst[G.run].ctr[G.species][C_COLL0 + rec.chosen], (unsigned long long)__popc(grp));
     }
-    if (ok) collide_real(b, s, rec.x, rec.y, __int_as_float(rec.z), __int_as_float(rec.w));
+    if (ok) collide_real(b, s, rec);
   }
 }
 

@@ -28,7 +28,7 @@ struct Carve {
   }
 };
 
-// Records for the real collisions of one step: at most one per candidate,
+// Records (48 B) for the real collisions of one step: at most one per candidate,
 // and the candidate count of n <= cap particles is binomial with the
 // null-collision probability P; mean + 12 standard deviations + 256 is never
 // exceeded in practice (an overflow fails the run with ECPIC_ERR_CAPACITY).
@@ -68,7 +68,7 @@ size_t layout_bytes(const RunSpec& s) {
       const size_t c = (size_t)sp.cap;
       add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(8 * c);
     }
-  for (const auto& sp : s.species) add(16 * (size_t)real_capacity(sp, s));
+  for (const auto& sp : s.species) add(sizeof(RealRec) * (size_t)real_capacity(sp, s));
   return b;
 }
 }  // namespace
@@ -447,7 +447,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   for (int s = 0; s < ns; ++s) {
     SegDev& G = h_segs_[R.seg0 + s];
     G.real_cap = real_capacity(spec.species[s], spec);
-    G.real = cv.take<int4>((size_t)G.real_cap);
+    G.real = cv.take<RealRec>((size_t)G.real_cap);
   }
   cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
                   stream_);
