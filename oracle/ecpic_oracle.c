@@ -81,6 +81,7 @@ struct or_run {
   double dt;
   int64_t step;
   int initialized;
+  int quiet; /* loader: evenly spaced positions instead of random ones */
   double *Q, *phi, *E;
   double fe;
   int sample_every;
@@ -647,8 +648,9 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
   r->dt = dt;
   r->step = 0;
   /* Sec. 2b: uniform density, Maxwellian temperature.  Position from
-   * 32-bit word 0 of the block with word3 = (s<<8)|0x80; velocities from
-   * the block with word3 = (s<<8)|0x81 (Box-Muller on 32-bit uniforms). */
+   * 32-bit word 0 of the block with word3 = (s<<8)|0x80 (or, for a quiet
+   * start, X = (i + 1/2) L / n); velocities from the block with
+   * word3 = (s<<8)|0x81 (Box-Muller on 32-bit uniforms). */
   for (int si = 0; si < r->ns; ++si) {
     or_species* s = &r->sp[si];
     double sd = sqrt(OR_QE * T_eV[si] / s->m);
@@ -658,6 +660,7 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
       or_draw(r, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)si << 8) | 0x80u, a);
       or_draw(r, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)si << 8) | 0x81u, b);
       double u = (double)a[0] * (1.0 / 4294967296.0);
+      if (r->quiet) u = ((double)i + 0.5) / (double)s->n;
       s->X[i] = u * r->L;
       double z0, z1, z2, z3;
       or_box_muller(((double)b[0] + 1.0) * (1.0 / 4294967296.0),
@@ -678,6 +681,13 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
   r->initialized = 1;
   r->fe = 0.0;
   return or_refresh(r);
+}
+
+int oracle_set_quiet_start(or_run* r, int quiet) {
+  if (!r || (quiet != 0 && quiet != 1)) return -1;
+  if (r->initialized) return -2;
+  r->quiet = quiet;
+  return 0;
 }
 
 int oracle_set_particles(or_run* r, int species, const double* X,

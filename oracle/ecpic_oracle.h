@@ -99,6 +99,11 @@ int oracle_set_gas(or_run* r, double n_g, double T_g, double m_g);
 int oracle_add_process(or_run* r, int species, int kind, double threshold_eV,
                        double dE_eV, int n, const float* sigma,
                        int product_species);
+/* Loader positions: 0 = uniform random (Philox, default), 1 = quiet start,
+ * X_i = (i + 1/2) L / n for i < n per species (the paper is silent on the
+ * loading; a quiet start keeps the initial charge noise, and the field energy
+ * it holds, near zero).  Before oracle_init. */
+int oracle_set_quiet_start(or_run* r, int quiet);
 /* uniform positions + Maxwellian velocities from Philox; w per species is
  * the weight given to oracle_add_species. */
 int oracle_init(or_run* r, uint64_t seed, double dt,

@@ -69,6 +69,7 @@ def _load(path):
         "oracle_set_gas": (i32, [vp, d, d, d]),
         "oracle_add_process": (i32, [vp, i32, i32, d, d, i32, vp, i32]),
         "oracle_init": (i32, [vp, u64, d, vp, vp]),
+        "oracle_set_quiet_start": (i32, [vp, i32]),
         "oracle_set_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, i64]),
         "oracle_get_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, i64, P(i64)]),
         "oracle_set_particles_cell": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64]),
@@ -207,6 +208,9 @@ class OracleRun:
         s = np.ascontiguousarray(sigma, dtype=np.float32)
         _chk(self._L.oracle_add_process(self.h, species, kind, threshold, dE, s.size,
                                         _ptr(s), product), "oracle_add_process")
+
+    def set_quiet_start(self, quiet=True):
+        _chk(self._L.oracle_set_quiet_start(self.h, 1 if quiet else 0), "oracle_set_quiet_start")
 
     def init(self, seed, dt, n_per_species, T_eV):
         n = np.ascontiguousarray(n_per_species, dtype=np.int64)

@@ -83,6 +83,7 @@ class RunConfig:
     dt: float
     n_steps: int
     sample_every: int = 0
+    quiet: bool = False  # loader: evenly spaced positions (quiet start)
 
     @property
     def N(self) -> int:
@@ -234,6 +235,28 @@ def batched_manifest(n_runs: int = 256, seed: int = 0, steps: int = 4400,
     return runs
 
 
+def appendix_b_sweep(ratios=(0.5, 1.0, 2.0, 4.0, 8.0, 16.0), ppc: int = 64, N: int = 2048,
+                     steps: int = 100_000, seed: int = 0, schemes=(EC, MC),
+                     sample_every: int = 1000, quiet: bool = True) -> List[RunConfig]:
+    """App. B heating-rate sweep: collisionless periodic electrons on an
+    immobile neutralising background with the Table 1 plasma (n0 = 7e15 m^-3,
+    Te = 2.585 eV), N cells of dx = r * lambda_De (L grows with r),
+    dt = 0.1/w_pe, 10,000/w_pe = 100,000 steps; one run per (scheme, r),
+    energies sampled every `sample_every` steps.  Quiet start by default: a
+    random load at dx >> lambda_De starts with long-wavelength charge noise
+    whose field energy exceeds the kinetic energy and relaxes into it."""
+    runs = []
+    for scheme in schemes:
+        for i, r in enumerate(ratios):
+            c = periodic_plasma(N=N, dx_lambda=float(r), ppc=ppc, dt_wpe=0.1, n_steps=steps,
+                                seed=seed * 1000 + 10 * i + scheme, scheme=scheme,
+                                n0=7e15, Te=2.585, quiet=quiet)
+            c.name = f"appB-{'EC' if scheme == EC else 'MC'}-dx{r:g}"
+            c.sample_every = sample_every
+            runs.append(c)
+    return runs
+
+
 @dataclasses.dataclass
 class Request:
     arrival: float  # seconds after the stream starts
@@ -290,7 +313,8 @@ def random_state(rng: np.random.Generator, N: int, n: int, vth: float, cells_per
 
 def periodic_plasma(N: int = 64, dx_lambda: float = 4.0, ppc: int = 64, dt_wpe: float = 0.1,
                     n_steps: int = 1000, seed: int = 0, scheme: int = EC, ions: bool = False,
-                    n0: float = 1e14, Te: float = 2.0, Ti: float = 0.5) -> RunConfig:
+                    n0: float = 1e14, Te: float = 2.0, Ti: float = 0.5,
+                    quiet: bool = False) -> RunConfig:
     """Collisionless periodic Maxwellian of App. B: electrons (and optionally
     mobile ions) on a uniform neutralising background, dx = dx_lambda * lambda_De,
     dt = dt_wpe / w_pe."""
@@ -305,4 +329,4 @@ def periodic_plasma(N: int = 64, dx_lambda: float = 4.0, ppc: int = 64, dt_wpe: 
     return RunConfig(name=f"periodic-{N}", edges=uniform_edges(N, L), bc=PERIODIC, v0=0.0,
                      freq=0.0, phase=0.0, vdc=0.0, scheme=scheme, species=sp, n_gas=0.0,
                      T_gas=T_GAS, m_gas=M_ION, processes=[], seed=seed, dt=dt_wpe / wpe,
-                     n_steps=n_steps)
+                     n_steps=n_steps, quiet=quiet)

@@ -18,6 +18,8 @@ def oracle_from_config(cfg: I.RunConfig, init: bool = True):
         o.add_process(p.species, p.kind, p.threshold, p.dE, p.sigma, p.product)
     if cfg.sample_every:
         o.reset_averages(cfg.sample_every)
+    if getattr(cfg, "quiet", False):
+        o.set_quiet_start(True)
     if init:
         o.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
     return o

@@ -2,6 +2,7 @@
 sanity of a short RF-CCP run of the small 128-cell discharge; Table 1's
 stated resolution figures against the plasma formulas."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2308_13092_gb300 import inputs as I
@@ -104,3 +105,48 @@ def test_table1_resolution_figures():
     assert abs(wpe * dt - 0.087) < 0.001
     assert abs(dx_ref - 1.465e-4) < 1e-7
     assert 5100 * 4000 == 20_400_000 and 100 * 4000 == 400_000 and 4000 // 10 == 400
+
+
+def test_quiet_start_positions_velocities_and_zero_field():
+    """Quiet start: X_i = (i + 1/2) L / n exactly; velocities are the random
+    loader's (same Philox block); an evenly spaced load with whole particles
+    per cell on a uniform periodic grid deposits the same charge on every
+    node, so the initial field and field energy vanish."""
+    cfg = I.periodic_plasma(N=32, dx_lambda=4.0, ppc=16, dt_wpe=0.1, seed=7)
+    rnd = oracle_from_config(cfg)
+    cfg.quiet = True
+    q = oracle_from_config(cfg)
+    pr, pq = rnd.get_particles(0), q.get_particles(0)
+    n = pq["X"].size
+    L = cfg.edges[-1]
+    assert np.array_equal(pq["X"], (np.arange(n) + 0.5) / n * L)
+    for k in ("vx", "vy", "vz", "id"):
+        assert np.array_equal(pq[k], pr[k]), k
+    ke, fe = q.energy()
+    f = q.fields()
+    assert np.max(np.abs(f["E"])) < 1e-9 * np.max(np.abs(rnd.fields()["E"]))
+    assert fe <= 1e-20 * (0.5 * I.ME * cfg.species[0].w * np.sum(pq["vx"] ** 2))
+    with pytest.raises(RuntimeError):
+        q.set_quiet_start(False)  # only before init
+
+
+def test_quiet_start_app_b_mc_heats_ec_conserves():
+    """App. B on the oracle with a quiet start: at dx = 8 lambda_De the MC
+    scheme's total energy grows by tens of per cent in 2500 steps (grid
+    heating) while EC's stays within 0.2 %; at dx = lambda_De both stay small."""
+    out = {}
+    for r in (1.0, 8.0):
+        for sch in (I.EC, I.MC):
+            c = I.periodic_plasma(N=128, dx_lambda=r, ppc=64, dt_wpe=0.1, seed=3, scheme=sch,
+                                  n0=7e15, Te=2.585, quiet=True)
+            o = oracle_from_config(c)
+            o.step(1)
+            ke, fe = o.energy()
+            w0 = ke.sum() + fe
+            o.step(2500)
+            ke, fe = o.energy()
+            out[(r, sch)] = (ke.sum() + fe) / w0 - 1.0
+            o.close()
+    assert abs(out[(8.0, I.EC)]) < 2e-3, out
+    assert out[(8.0, I.MC)] > 0.1, out
+    assert abs(out[(1.0, I.EC)]) < 2e-3 and abs(out[(1.0, I.MC)]) < 5e-3, out
