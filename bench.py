@@ -295,6 +295,44 @@ def one_by_one_block(ecpic, cfgs, stream, device, n_runs=12, steps=200):
             "what": "sampled runs of the batched manifest, each alone (wall clock per run)"}
 
 
+def appendix_b_block(ecpic, stream, device, steps=100_000, chunks=10):
+    """App. B sweep as one batch: EC and MC, collisionless periodic Table 1
+    plasma on 2048 cells of dx/lambda_De = 0.5..16, dt = 0.1/w_pe, 10,000/w_pe.
+    Heating = relative change of the total energy W = KE + FE from the first
+    sample (t = 100/w_pe); KE alone beside it.  Wall clock of the whole batch."""
+    cfgs = I.appendix_b_sweep(steps=steps, sample_every=steps // (10 * chunks))
+    eng = ecpic.Engine(device=device, stream=stream.cuda_stream, max_slots=len(cfgs),
+                       max_cells=2048, species_per_run=1)
+    tks = [eng.submit(c) for c in cfgs]
+    eng.pump(0)
+    W0, K0, dK, series = {}, {}, {}, {c.name: [] for c in cfgs}
+    t0 = time.perf_counter()
+    ps0 = eng.stats()["particle_steps"]
+    done = 0
+    first = steps // (10 * chunks)
+    for k in range(chunks + 1):
+        n = first if k == 0 else steps // chunks - (first if k == 1 else 0)
+        eng.pump(n)
+        done += n
+        for c, tk in zip(cfgs, tks):
+            d = eng.poll(tk, diagnostics=True)["diag"]
+            w, ke = float(d["ke"].sum() + d["fe"]), float(d["ke"].sum())
+            if k == 0:
+                W0[c.name], K0[c.name] = w, ke
+            else:
+                series[c.name].append(round(w / W0[c.name] - 1.0, 6))
+            if k == chunks:
+                dK[c.name] = round(ke / K0[c.name] - 1.0, 6)
+    wall = time.perf_counter() - t0
+    ps = eng.stats()["particle_steps"] - ps0
+    eng.close()
+    return {"value": ps / wall, "unit": "particle-steps/s", "runs": len(cfgs), "steps": done,
+            "cells": 2048, "ppc": 64,
+            "dW_over_W": series, "dKE_over_KE_final": dK,
+            "what": "App. B sweep (EC and MC at dx/lambda_De 0.5-16) as one batch; "
+                    "relative total-energy change every 1000/w_pe from t = 100/w_pe"}
+
+
 def served_block(ecpic, stream, device, capacity, n_req=64, rho=0.7):
     """Poisson arrivals of CCP run requests (sizes as in the batched manifest,
     5..50 RF periods at 1/10 of the steps), continuous batching vs one at a
@@ -442,6 +480,7 @@ def main():
         extras["single_run"] = single_run_block(torch, ecpic, stream, local)
         extras["one_by_one"] = one_by_one_block(ecpic, cfgs, stream, local)
         extras["served"] = served_block(ecpic, stream, local, capacity=value / max(1, world))
+        extras["appendix_b"] = appendix_b_block(ecpic, stream, local)
         e2e = e2e_block(ecpic, cfgs, stream, local, steps=200)
     else:
         e2e = None

@@ -121,6 +121,11 @@ int ecpic_set_gas(ecpic_run* run, double n_g_m3, double T_g_K, double m_g_kg);
  * receiving the ion of an ionisation (else ignored).  Copied. */
 int ecpic_add_process(ecpic_run* run, int species, int kind, double threshold_eV,
                       double dE_eV, int n, const float* sigma_m2, int product_species);
+/* Loader positions (before ecpic_init): 0 = uniform random from Philox
+ * (default), 1 = quiet start, X_i = (i + 1/2) L / n for i < n per species.
+ * The paper is silent on the loading; a quiet start keeps the initial charge
+ * noise, and the field energy it holds, near zero (App. B heating tests). */
+int ecpic_set_quiet_start(ecpic_run* run, int quiet);
 /* Load n_per_species[s] particles uniformly in [0, L) with Maxwellian
  * velocities of T_eV[s] (Sec. 2b), ids 0..n-1, from the counter-based
  * Philox4x32-10 stream keyed on `seed`; time step dt; then deposit and
@@ -212,6 +217,7 @@ typedef struct {
   uint64_t seed;
   double dt;
   int sample_every;     /* diagnostics sampling cadence (0 = off) */
+  int quiet_start;      /* 1: evenly spaced positions (ecpic_set_quiet_start) */
 } ecpic_run_config;
 
 /* max_cells bounds N of every admitted run; species_per_run bounds their
@@ -232,9 +238,10 @@ int ecpic_engine_submit(ecpic_engine* eng, const ecpic_run_config* cfg, int64_t 
  * number of runs resident after the round, *n_queued the queue length. */
 int ecpic_engine_pump(ecpic_engine* eng, int64_t max_steps, int* n_resident, int* n_queued);
 /* State of a ticket: 0 queued, 1 resident, 2 finished, < 0 an ecpic_status
- * error of that run.  When finished and out != NULL, fills its diagnostics
- * (the profile arrays of out, if not NULL, sized n_species*(N+1) / N+1).
- * *steps_done / *particle_steps (may be NULL) report its progress. */
+ * error of that run.  When finished, or resident (then read from the device:
+ * synchronises), and out != NULL, fills its diagnostics (the profile arrays
+ * of out, if not NULL, sized n_species*(N+1) / N+1).  *steps_done /
+ * *particle_steps (may be NULL) report its progress as of the last pump. */
 int ecpic_engine_poll(ecpic_engine* eng, uint64_t ticket, int* state, ecpic_diag* out,
                       int64_t* steps_done, int64_t* particle_steps);
 /* Forget a finished ticket's stored results. */

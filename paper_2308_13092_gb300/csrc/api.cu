@@ -210,6 +210,13 @@ int ecpic_add_process(ecpic_run* r, int species, int kind, double threshold_eV, 
   });
 }
 
+int ecpic_set_quiet_start(ecpic_run* r, int quiet) {
+  if (!r || (quiet != 0 && quiet != 1)) return ECPIC_ERR_ARG;
+  if (r->batch) return fail(r, ECPIC_ERR_STATE, "before init");
+  r->spec.quiet = quiet;
+  return ECPIC_OK;
+}
+
 int ecpic_init(ecpic_run* r, uint64_t seed, double dt, const int64_t* n_per_species,
                const double* T_eV) {
   if (!r) return ECPIC_ERR_ARG;

@@ -99,6 +99,11 @@ int spec_from_config(const ecpic_run_config* c, int64_t n_steps, RunSpec* s, std
   s->n_init.assign(c->n_init, c->n_init + c->n_species);
   s->T_eV.assign(c->T_eV, c->T_eV + c->n_species);
   s->sample_every = c->sample_every;
+  if (c->quiet_start != 0 && c->quiet_start != 1) {
+    *err = "quiet_start must be 0 or 1";
+    return ECPIC_ERR_ARG;
+  }
+  s->quiet = c->quiet_start;
   s->step_end = n_steps;
   const std::string v = ecpic::validate_spec(*s);
   if (!v.empty()) {
@@ -276,6 +281,14 @@ int ecpic_engine_poll(ecpic_engine* e, uint64_t ticket, int* state, ecpic_diag* 
   if (steps_done) *steps_done = tk.steps_done;
   if (particle_steps) *particle_steps = (int64_t)tk.psteps;
   if (out && (tk.state == 2 || tk.state < 0) && tk.diag.N > 0) ecpic::fill_diag(tk.diag, tk.spec, out);
+  if (out && tk.state == 1 && e->batch->slot_active(tk.slot)) {
+    // a resident run: its current diagnostics, read from the device
+    ecpic::Diag d;
+    std::string err;
+    const int rc = e->batch->diag(tk.slot, &d, &err);
+    if (rc) return efail(e, rc, err);
+    ecpic::fill_diag(d, tk.spec, out);
+  }
   return ECPIC_OK;
 }
 

@@ -1397,7 +1397,8 @@ __global__ void k_init(BatchView b, int slot, InitParams p) {
        i += (long long)gridDim.x * blockDim.x) {
     const uint4 A = draw(R->seed, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)sp << 8) | 0x80u);
     const uint4 B = draw(R->seed, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)sp << 8) | 0x81u);
-    const double u = (double)A.x * 2.3283064365386963e-10;
+    const double u = p.quiet ? __ddiv_rn((double)i + 0.5, (double)n)
+                             : (double)A.x * 2.3283064365386963e-10;
     const double X = __dmul_rn(u, L);
     int lo = 0, hi = N;
     while (hi - lo > 1) {

@@ -24,6 +24,7 @@ struct BatchView {
 struct InitParams {
   long long n[kMaxSpecies];
   double sd[kMaxSpecies];  // sqrt(e T / m)
+  int quiet;               // positions X_i = (i + 1/2) L / n instead of Philox
 };
 
 size_t pass_smem_bytes(const BatchView& b);

@@ -466,6 +466,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   specs_[slot] = spec;
   // particles and the field of step 0
   InitParams ip{};
+  ip.quiet = spec.quiet;
   for (int s = 0; s < ns; ++s) {
     ip.n[s] = spec.n_init[s];
     ip.sd[s] = std::sqrt(kQe * spec.T_eV[s] / spec.species[s].m);

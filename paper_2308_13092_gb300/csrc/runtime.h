@@ -37,6 +37,7 @@ struct RunSpec {
   std::vector<long long> n_init;
   std::vector<double> T_eV;
   int sample_every = 0;
+  int quiet = 0;  // loader: evenly spaced positions (quiet start)
   long long step_end = LLONG_MAX;
 };
 

@@ -60,7 +60,7 @@ class ecpic_run_config(C.Structure):
         ("w", C.c_double * 4), ("capacity", C.c_int64 * 4), ("n_init", C.c_int64 * 4),
         ("T_eV", C.c_double * 4), ("n_gas", C.c_double), ("T_gas", C.c_double),
         ("m_gas", C.c_double), ("n_proc", C.c_int), ("procs", C.c_void_p), ("seed", C.c_uint64),
-        ("dt", C.c_double), ("sample_every", C.c_int),
+        ("dt", C.c_double), ("sample_every", C.c_int), ("quiet_start", C.c_int),
     ]
 
 
@@ -80,6 +80,7 @@ SIGNATURES = {
     "ecpic_engine_profile": (i32, [vp, i64, vp, vp]),
     "ecpic_engine_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_autotune": (i32, [vp, i64, vp, vp, vp]),
+    "ecpic_set_quiet_start": (i32, [vp, i32]),
     "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
     "ecpic_destroy": (None, [vp]),
     "ecpic_last_error": (C.c_char_p, [vp]),
@@ -204,6 +205,8 @@ class Run:
             r.add_process(p.species, p.kind, p.threshold, p.dE, p.sigma, p.product)
         if sort_every:
             r.set_sort_every(sort_every)
+        if getattr(cfg, "quiet", False):
+            r.set_quiet_start(True)
         if init:
             r.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
             if cfg.sample_every:
@@ -279,6 +282,10 @@ class Run:
 
     def set_pass_grid(self, ctas):
         _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
+
+    def set_quiet_start(self, quiet=True):
+        _chk(self.h, self._L.ecpic_set_quiet_start(self.h, 1 if quiet else 0),
+             "ecpic_set_quiet_start")
 
     def autotune(self, steps_per_trial=64):
         k, g, ns = C.c_int(), C.c_int(), C.c_double()
@@ -428,6 +435,7 @@ class Engine:
         rc.n_proc = len(cfg.processes)
         rc.procs = C.cast(procs, C.c_void_p)
         rc.seed, rc.dt, rc.sample_every = int(cfg.seed), cfg.dt, int(cfg.sample_every)
+        rc.quiet_start = 1 if getattr(cfg, "quiet", False) else 0
         t = C.c_uint64()
         n = int(cfg.n_steps if n_steps is None else n_steps)
         self._chk(self._L.ecpic_engine_submit(self.h, C.byref(rc), n, C.byref(t)),
@@ -451,7 +459,7 @@ class Engine:
                                             C.byref(dg) if diagnostics else None,
                                             C.byref(steps), C.byref(ps)), "ecpic_engine_poll")
         out = dict(state=st.value, steps=steps.value, particle_steps=ps.value)
-        if diagnostics and st.value == self.FINISHED:
+        if diagnostics and st.value in (self.RESIDENT, self.FINISHED):
             out["diag"] = _diag_dict(dg, ns, N, arrs)
         return out
 

@@ -108,8 +108,15 @@ def _counters_match(g, o, exact_keys=("candidates",)):
     return dg, co
 
 
+def _quiet(cfg):
+    cfg.quiet = True
+    return cfg
+
+
 def test_loader_parity():
-    for cfg in (I.config_small(seed=5), _small(edges=oracle.doubling_grid(128, 0.05, 0.01, 1, 8))):
+    for cfg in (I.config_small(seed=5), _small(edges=oracle.doubling_grid(128, 0.05, 0.01, 1, 8)),
+                _quiet(I.config_small(seed=6)),
+                _quiet(I.periodic_plasma(N=64, dx_lambda=8.0, ppc=64, seed=2, ions=True))):
         g, o = _pair(cfg)
         for s, sp in enumerate(cfg.species):
             gp = g.get_particles(s)
