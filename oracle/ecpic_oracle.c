@@ -61,6 +61,10 @@ typedef struct {
   double *D, *M1, *M2;
   /* time averages */
   double *acc_n, *acc_T, *acc_M0, *acc_M1, *acc_M2;
+  /* tallies (Sec. 3a diagnostics): EEDF of the central region on sample
+   * steps (q < 0), impact energy and angle at x = 0 on every step (q > 0),
+   * J.E per cell summed over sample steps */
+  double *eedf, *iedf, *iad, *acc_P;
 } or_species;
 
 struct or_run {
@@ -82,6 +86,10 @@ struct or_run {
   int64_t step;
   int initialized;
   int quiet; /* loader: evenly spaced positions instead of random ones */
+  /* tally set-up: EEDF region centre and half-width (m), bin widths (eV),
+   * bin counts; eedf_c0..eedf_c1 the cells of the region */
+  double eedf_xc, eedf_hw, eedf_dE, iedf_dE;
+  int eedf_n, iedf_n, iad_n, eedf_c0, eedf_c1;
   double *Q, *phi, *E;
   double fe;
   int sample_every;
@@ -345,6 +353,7 @@ int oracle_doubling_grid(int n_ref, double L, double L_buff, int dx_min,
 static void or_free_species(or_species* s) {
   free(s->X); free(s->vx); free(s->vy); free(s->vz); free(s->id);
   free(s->D); free(s->M1); free(s->M2);
+  free(s->eedf); free(s->iedf); free(s->iad); free(s->acc_P);
   free(s->acc_n); free(s->acc_T); free(s->acc_M0); free(s->acc_M1);
   free(s->acc_M2);
   for (int k = 0; k < s->nproc; ++k) free(s->proc[k].sigma);
@@ -609,8 +618,36 @@ static int or_solve(or_run* r, int64_t k) {
   return oracle_field(N, r->x, r->phi, r->bc, r->scheme, r->E);
 }
 
+/* histogram bin of value v for bins of width d: floor(v / d), the last bin
+ * collecting everything above */
+static int or_bin(double v, double d, int n) {
+  double b = floor(v / d);
+  if (!(b >= 0.0)) return 0;
+  if (b >= (double)(n - 1)) return n - 1;
+  return (int)b;
+}
+
+/* an ion of species s reaching x = 0 with velocity (vx, vy, vz): energy
+ * (eV) and angle from the electrode normal (degrees, 0..90) */
+static void or_tally_impact(const or_run* r, or_species* s, double vx, double vy, double vz) {
+  double E = 0.5 * s->m * (vx * vx + vy * vy + vz * vz) / OR_QE;
+  double th = atan2(sqrt(vy * vy + vz * vz), fabs(vx)) * (180.0 / 3.14159265358979323846);
+  s->iedf[or_bin(E, r->iedf_dE, r->iedf_n)] += 1.0;
+  s->iad[or_bin(th, 90.0 / r->iad_n, r->iad_n)] += 1.0;
+}
+
 static void or_sample(or_run* r) {
   int N = r->N;
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    if (!(s->q < 0.0)) continue;
+    for (int64_t i = 0; i < s->n; ++i) {
+      int j = or_locate(r, s->X[i]);
+      if (j < r->eedf_c0 || j > r->eedf_c1) continue;
+      double E = 0.5 * s->m * (s->vx[i] * s->vx[i] + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]) / OR_QE;
+      s->eedf[or_bin(E, r->eedf_dE, r->eedf_n)] += 1.0;
+    }
+  }
   for (int si = 0; si < r->ns; ++si) {
     or_species* s = &r->sp[si];
     for (int n = 0; n <= N; ++n) {
@@ -678,6 +715,32 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
     s->ke = 0.0;
   }
   for (int si = 0; si < r->ns; ++si) or_null_rate(r, &r->sp[si]);
+  /* tallies: defaults, the EEDF region's cells (centres within the region,
+   * else the cell holding its centre), zeroed arrays */
+  if (!(r->eedf_n > 0)) {
+    r->eedf_xc = -1.0; r->eedf_hw = 0.5e-3; r->eedf_dE = 0.5; r->eedf_n = 100;
+    r->iedf_dE = 2.0; r->iedf_n = 256; r->iad_n = 90;
+  }
+  double xc = r->eedf_xc < 0.0 ? 0.5 * r->L : r->eedf_xc;
+  r->eedf_c0 = r->N;
+  r->eedf_c1 = -1;
+  for (int j = 0; j < r->N; ++j) {
+    double cj = 0.5 * (r->x[j] + r->x[j + 1]);
+    if (cj >= xc - r->eedf_hw && cj <= xc + r->eedf_hw) {
+      if (j < r->eedf_c0) r->eedf_c0 = j;
+      r->eedf_c1 = j;
+    }
+  }
+  if (r->eedf_c0 > r->eedf_c1) r->eedf_c0 = r->eedf_c1 = or_locate(r, xc < r->L ? xc : 0.0);
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    free(s->eedf); free(s->iedf); free(s->iad); free(s->acc_P);
+    s->eedf = calloc((size_t)r->eedf_n, sizeof(double));
+    s->iedf = calloc((size_t)r->iedf_n, sizeof(double));
+    s->iad = calloc((size_t)r->iad_n, sizeof(double));
+    s->acc_P = calloc((size_t)r->N, sizeof(double));
+    if (!s->eedf || !s->iedf || !s->iad || !s->acc_P) return -3;
+  }
   r->initialized = 1;
   r->fe = 0.0;
   return or_refresh(r);
@@ -901,6 +964,7 @@ static int or_step_once(or_run* r) {
   }
   r->fe = fe;
   /* steps 4-5 (Eq. 6-9), then the walls */
+  const int sampled = r->sample_every > 0 && (k + 1) % r->sample_every == 0;
   for (int si = 0; si < r->ns; ++si) {
     or_species* s = &r->sp[si];
     double qm = s->q / s->m;
@@ -915,9 +979,15 @@ static int or_step_once(or_run* r) {
       double vold = s->vx[i];
       double vnew = vold + qm * Ei * r->dt;
       ke += 0.5 * s->m * s->w * (vold * vnew + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+      /* J.E of the push: q w E_i (v^{k-1/2} + v^{k+1/2})/2 per unit volume of cell j */
+      if (sampled) s->acc_P[j] += s->q * s->w * Ei * 0.5 * (vold + vnew) / r->dx[j];
       double Xn = X + vnew * r->dt;
       if (r->bc == OR_DIRICHLET) {
-        if (Xn <= 0.0) { s->absorbed[0]++; continue; }
+        if (Xn <= 0.0) {
+          s->absorbed[0]++;
+          if (s->q > 0.0) or_tally_impact(r, s, vnew, s->vy[i], s->vz[i]);
+          continue;
+        }
         if (Xn >= r->L) { s->absorbed[1]++; continue; }
       } else {
         Xn = Xn - r->L * floor(Xn / r->L);
@@ -973,8 +1043,45 @@ int oracle_reset_averages(or_run* r, int sample_every) {
     memset(s->acc_M0, 0, sizeof(double) * nn);
     memset(s->acc_M1, 0, sizeof(double) * nn);
     memset(s->acc_M2, 0, sizeof(double) * nn);
+    if (s->eedf) memset(s->eedf, 0, sizeof(double) * (size_t)r->eedf_n);
+    if (s->iedf) memset(s->iedf, 0, sizeof(double) * (size_t)r->iedf_n);
+    if (s->iad) memset(s->iad, 0, sizeof(double) * (size_t)r->iad_n);
+    if (s->acc_P) memset(s->acc_P, 0, sizeof(double) * (size_t)r->N);
   }
   return 0;
+}
+
+int oracle_set_tallies(or_run* r, double eedf_center, double eedf_halfwidth, double eedf_dE,
+                       int eedf_bins, double iedf_dE, int iedf_bins, int iad_bins) {
+  if (!r || !(eedf_halfwidth >= 0.0) || !(eedf_dE > 0.0) || eedf_bins < 1 || !(iedf_dE > 0.0) ||
+      iedf_bins < 1 || iad_bins < 1)
+    return -1;
+  if (r->initialized) return -2;
+  r->eedf_xc = eedf_center; r->eedf_hw = eedf_halfwidth; r->eedf_dE = eedf_dE;
+  r->eedf_n = eedf_bins; r->iedf_dE = iedf_dE; r->iedf_n = iedf_bins; r->iad_n = iad_bins;
+  return 0;
+}
+
+int oracle_get_tally_shape(const or_run* r, int* shape5) {
+  if (!r || !shape5) return -1;
+  if (!r->initialized) return -2;
+  shape5[0] = r->eedf_n; shape5[1] = r->iedf_n; shape5[2] = r->iad_n;
+  shape5[3] = r->eedf_c0; shape5[4] = r->eedf_c1;
+  return 0;
+}
+
+int64_t oracle_get_tallies(const or_run* r, double* eedf, double* iedf, double* iad, double* power) {
+  if (!r) return -1;
+  if (!r->initialized) return -2;
+  double inv = r->n_samples > 0 ? 1.0 / (double)r->n_samples : 0.0;
+  for (int si = 0; si < r->ns; ++si) {
+    const or_species* s = &r->sp[si];
+    for (int b = 0; b < r->eedf_n; ++b) if (eedf) eedf[(size_t)si * r->eedf_n + b] = s->eedf[b];
+    for (int b = 0; b < r->iedf_n; ++b) if (iedf) iedf[(size_t)si * r->iedf_n + b] = s->iedf[b];
+    for (int b = 0; b < r->iad_n; ++b) if (iad) iad[(size_t)si * r->iad_n + b] = s->iad[b];
+    for (int j = 0; j < r->N; ++j) if (power) power[(size_t)si * r->N + j] = s->acc_P[j] * inv;
+  }
+  return r->n_samples;
 }
 
 int oracle_get_counters(const or_run* r, int64_t* out, int cap) {

@@ -104,6 +104,27 @@ int oracle_add_process(or_run* r, int species, int kind, double threshold_eV,
  * loading; a quiet start keeps the initial charge noise, and the field energy
  * it holds, near zero).  Before oracle_init. */
 int oracle_set_quiet_start(or_run* r, int quiet);
+/* Tallies of the paper's diagnostics (Sec. 3a, Fig. 1, Sec. 3b-c):
+ *  - EEDF: on sample steps, the kinetic energies (eV) of the particles of
+ *    every species with q < 0 in the cells whose centres lie within
+ *    eedf_center +- eedf_halfwidth (m; centre < 0: L/2), counted in
+ *    eedf_bins bins of eedf_dE, the last bin taking everything above;
+ *  - impact energy and angle: on every step, the particles of every species
+ *    with q > 0 absorbed at x = 0 (the RF electrode), energy (eV) in
+ *    iedf_bins bins of iedf_dE and angle from the normal in iad_bins bins
+ *    over 0..90 degrees, from the velocity that carried them out;
+ *  - J.E: on sample steps, q w E_i (v^{k-1/2} + v^{k+1/2}) / 2 / dx_j summed
+ *    per cell j of the particle at level k (W/m^3), averaged over samples.
+ * Before oracle_init; defaults: L/2 +- 0.5 mm, 0.5 eV x 100, 2 eV x 256, 90.
+ * reset_averages clears them. */
+int oracle_set_tallies(or_run* r, double eedf_center, double eedf_halfwidth, double eedf_dE,
+                       int eedf_bins, double iedf_dE, int iedf_bins, int iad_bins);
+/* shape5 = {eedf_bins, iedf_bins, iad_bins, first and last EEDF cell} */
+int oracle_get_tally_shape(const or_run* r, int* shape5);
+/* eedf [ns][eedf_bins], iedf [ns][iedf_bins], iad [ns][iad_bins] (counts),
+ * power [ns][N] (W/m^3, mean over samples); any may be NULL.  Returns the
+ * number of samples. */
+int64_t oracle_get_tallies(const or_run* r, double* eedf, double* iedf, double* iad, double* power);
 /* uniform positions + Maxwellian velocities from Philox; w per species is
  * the weight given to oracle_add_species. */
 int oracle_init(or_run* r, uint64_t seed, double dt,

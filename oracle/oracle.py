@@ -70,6 +70,9 @@ def _load(path):
         "oracle_add_process": (i32, [vp, i32, i32, d, d, i32, vp, i32]),
         "oracle_init": (i32, [vp, u64, d, vp, vp]),
         "oracle_set_quiet_start": (i32, [vp, i32]),
+        "oracle_set_tallies": (i32, [vp, d, d, d, i32, d, i32, i32]),
+        "oracle_get_tally_shape": (i32, [vp, vp]),
+        "oracle_get_tallies": (i64, [vp, vp, vp, vp, vp]),
         "oracle_set_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, i64]),
         "oracle_get_particles": (i32, [vp, i32, vp, vp, vp, vp, vp, i64, P(i64)]),
         "oracle_set_particles_cell": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64]),
@@ -208,6 +211,26 @@ class OracleRun:
         s = np.ascontiguousarray(sigma, dtype=np.float32)
         _chk(self._L.oracle_add_process(self.h, species, kind, threshold, dE, s.size,
                                         _ptr(s), product), "oracle_add_process")
+
+    def set_tallies(self, eedf_center=-1.0, eedf_halfwidth=0.5e-3, eedf_dE=0.5, eedf_bins=100,
+                    iedf_dE=2.0, iedf_bins=256, iad_bins=90):
+        _chk(self._L.oracle_set_tallies(self.h, eedf_center, eedf_halfwidth, eedf_dE, eedf_bins,
+                                        iedf_dE, iedf_bins, iad_bins), "oracle_set_tallies")
+
+    def tallies(self):
+        sh = np.zeros(5, dtype=np.int32)
+        _chk(self._L.oracle_get_tally_shape(self.h, _ptr(sh)), "oracle_get_tally_shape")
+        ne, ni, na = int(sh[0]), int(sh[1]), int(sh[2])
+        e = np.zeros(self.ns * ne)
+        i = np.zeros(self.ns * ni)
+        a = np.zeros(self.ns * na)
+        p = np.zeros(self.ns * self.N)
+        n = self._L.oracle_get_tallies(self.h, _ptr(e), _ptr(i), _ptr(a), _ptr(p))
+        if n < 0:
+            raise RuntimeError("oracle_get_tallies failed")
+        return dict(n_samples=int(n), eedf=e.reshape(self.ns, ne), iedf=i.reshape(self.ns, ni),
+                    iad=a.reshape(self.ns, na), power=p.reshape(self.ns, self.N),
+                    eedf_cells=(int(sh[3]), int(sh[4])))
 
     def set_quiet_start(self, quiet=True):
         _chk(self._L.oracle_set_quiet_start(self.h, 1 if quiet else 0), "oracle_set_quiet_start")
