@@ -92,6 +92,18 @@ typedef struct {
   double* phi;                  /* [n] averaged potential, V */
   double* temp_x;               /* [s][n] mean of per-sample T_x, eV */
   double* temp_x_mom;           /* [s][n] T_x of the averaged moments, eV */
+  /* Tallies since the last ecpic_reset_averages (see ecpic_set_tallies):
+   * bin counts (as doubles) of the central EEDF (species with q < 0, sample
+   * steps) and of the impact energy and angle at x = 0 (q > 0, every step);
+   * the power density J.E per cell (W/m^3), mean over samples. */
+  int eedf_bins, iedf_bins, iad_bins;         /* filled by the library */
+  int eedf_cell0, eedf_cell1;                 /* cells of the EEDF region */
+  double eedf_dE, iedf_dE;                    /* bin widths, eV (angle: 90/iad_bins deg) */
+  int64_t impacts_dropped[ECPIC_MAX_SPECIES]; /* beyond the per-step impact list */
+  double* eedf;                               /* [s][eedf_bins] or NULL */
+  double* iedf;                               /* [s][iedf_bins] or NULL */
+  double* iad;                                /* [s][iad_bins] or NULL */
+  double* power;                              /* [s][N] or NULL */
 } ecpic_diag;
 
 /* ------------------------------------------------------------------ */
@@ -126,6 +138,21 @@ int ecpic_add_process(ecpic_run* run, int species, int kind, double threshold_eV
  * The paper is silent on the loading; a quiet start keeps the initial charge
  * noise, and the field energy it holds, near zero (App. B heating tests). */
 int ecpic_set_quiet_start(ecpic_run* run, int quiet);
+/* Diagnostic tallies (Sec. 3a, Fig. 1; before ecpic_init):
+ *  - EEDF: on sample steps, kinetic energies (eV) of the particles of every
+ *    species with q < 0 in the cells whose centres lie within
+ *    eedf_center +- eedf_halfwidth (m; centre < 0: L/2; no such cell: the cell
+ *    holding the centre), eedf_bins bins of eedf_dE, the last taking the rest;
+ *  - impact energy and angle at the RF electrode: on every step, particles
+ *    of every species with q > 0 absorbed at x = 0, energy (eV) in iedf_bins
+ *    bins of iedf_dE, angle from the normal in iad_bins bins over 0..90 deg;
+ *  - power density J.E per cell: on sample steps, q w E_i (v^{k-1/2} +
+ *    v^{k+1/2}) / 2 / dx_j for each particle in cell j at level k (W/m^3).
+ * Defaults: L/2 +- 0.5 mm, 0.5 eV x 100, 2 eV x 256, 90.  Read through
+ * ecpic_diagnostics; cleared by ecpic_reset_averages. */
+int ecpic_set_tallies(ecpic_run* run, double eedf_center_m, double eedf_halfwidth_m,
+                      double eedf_dE_eV, int eedf_bins, double iedf_dE_eV, int iedf_bins,
+                      int iad_bins);
 /* Load n_per_species[s] particles uniformly in [0, L) with Maxwellian
  * velocities of T_eV[s] (Sec. 2b), ids 0..n-1, from the counter-based
  * Philox4x32-10 stream keyed on `seed`; time step dt; then deposit and
@@ -218,6 +245,11 @@ typedef struct {
   double dt;
   int sample_every;     /* diagnostics sampling cadence (0 = off) */
   int quiet_start;      /* 1: evenly spaced positions (ecpic_set_quiet_start) */
+  /* tallies as ecpic_set_tallies; eedf_bins = 0 keeps every default */
+  double eedf_center, eedf_halfwidth, eedf_dE;
+  int eedf_bins;
+  double iedf_dE;
+  int iedf_bins, iad_bins;
 } ecpic_run_config;
 
 /* max_cells bounds N of every admitted run; species_per_run bounds their

@@ -210,6 +210,21 @@ int ecpic_add_process(ecpic_run* r, int species, int kind, double threshold_eV, 
   });
 }
 
+int ecpic_set_tallies(ecpic_run* r, double center, double halfwidth, double eedf_dE, int eedf_bins,
+                      double iedf_dE, int iedf_bins, int iad_bins) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (r->batch) return fail(r, ECPIC_ERR_STATE, "before init");
+  r->spec.eedf_center = center;
+  r->spec.eedf_halfwidth = halfwidth;
+  r->spec.eedf_dE = eedf_dE;
+  r->spec.eedf_bins = eedf_bins;
+  r->spec.iedf_dE = iedf_dE;
+  r->spec.iedf_bins = iedf_bins;
+  r->spec.iad_bins = iad_bins;
+  const std::string v = ecpic::validate_tallies(r->spec);
+  return v.empty() ? ECPIC_OK : fail(r, ECPIC_ERR_ARG, v);
+}
+
 int ecpic_set_quiet_start(ecpic_run* r, int quiet) {
   if (!r || (quiet != 0 && quiet != 1)) return ECPIC_ERR_ARG;
   if (r->batch) return fail(r, ECPIC_ERR_STATE, "before init");

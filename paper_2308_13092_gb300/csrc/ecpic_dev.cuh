@@ -28,7 +28,7 @@ constexpr int kNumCtr = 16;    // counters per species, see Ctr
 // per-species counters in RunState::ctr
 enum Ctr {
   C_ABS_L = 0, C_ABS_R = 1, C_BIRTHS = 2, C_LOST = 3, C_CLAMPS = 4, C_CAND = 5,
-  C_NAN = 6, C_COLL0 = 8  // C_COLL0 + p, p < kMaxProc
+  C_NAN = 6, C_IMP_LOST = 7, C_COLL0 = 8  // C_COLL0 + p, p < kMaxProc
 };
 
 struct ProcDev {
@@ -91,6 +91,13 @@ struct RunDev {
   float* mom;           // ns * 2 * (N+1): sample-step vx moments (FP32 partials)
   double* momd;         // ns * 2 * (N+1): sample-step vx moments (FP64 totals)
   double* acc;          // diagnostics accumulators, see kAcc*
+  // tallies: EEDF of cells eedf_c0..eedf_c1 (species with q < 0, sample
+  // steps), impact energy and angle at x = 0 (q > 0, every step); per
+  // species tal[s * tal_stride + ...] = eedf | iedf | iad counts
+  unsigned long long* tal;
+  double* pw;           // ns * N: sum over samples of (v^- + v^+) E_i per cell
+  int tal_stride, eedf_n, iedf_n, iad_n, eedf_c0, eedf_c1;
+  float eedf_dEinv, iedf_dEinv, iad_binv;  // bins per eV, per eV, per degree
   SpeciesDev sp[kMaxSpecies];
 };
 
@@ -146,6 +153,10 @@ struct SegDev {
   // collision kernel
   RealRec* real;
   long long real_cap;
+  // particles of a q > 0 species absorbed at x = 0 this step (indices), for
+  // the impact tallies of the collision kernel; overflow is counted
+  int* imp;
+  long long imp_cap;
 };
 
 struct SegState {
@@ -154,6 +165,7 @@ struct SegState {
   long long n_live;     // written by the sort scan
   long long n_dead;     // slots below n_proc marked absorbed since the last sort
   long long n_real;     // records in SegDev::real this step (reset by the field kernel)
+  long long n_imp;      // entries in SegDev::imp this step (reset by the field kernel)
   int cur;              // current buffer set
   int pad;
 };
@@ -187,6 +199,19 @@ __device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t id, uint32_t step_
 __device__ __forceinline__ float u24(uint32_t r) { return (float)(r >> 8) * 5.9604644775390625e-8f; }
 __device__ __forceinline__ float u24_open(uint32_t r) {
   return (float)((r >> 8) + 1u) * 5.9604644775390625e-8f;
+}
+
+// kinetic energy (eV) from vx and vy^2 + vz^2, rounded the same way wherever
+// a tally bins it (the pass and the collision kernel must agree)
+__device__ __forceinline__ float yz2(float vy, float vz) { return __fadd_rn(__fmul_rn(vy, vy), __fmul_rn(vz, vz)); }
+__device__ __forceinline__ float kin_eV(float half_m_over_e, float vx, float yz) {
+  return __fmul_rn(half_m_over_e, __fadd_rn(__fmul_rn(vx, vx), yz));
+}
+__device__ __forceinline__ int tally_bin(float v, float inv_width, int n) {
+  const float b = floorf(__fmul_rn(v, inv_width));
+  if (!(b >= 0.0f)) return 0;
+  if (b >= (float)(n - 1)) return n - 1;
+  return (int)b;
 }
 
 // splitmix64 output function (Steele, Lea & Flood 2014)

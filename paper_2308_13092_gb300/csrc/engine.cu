@@ -104,6 +104,15 @@ int spec_from_config(const ecpic_run_config* c, int64_t n_steps, RunSpec* s, std
     return ECPIC_ERR_ARG;
   }
   s->quiet = c->quiet_start;
+  if (c->eedf_bins > 0) {
+    s->eedf_center = c->eedf_center;
+    s->eedf_halfwidth = c->eedf_halfwidth;
+    s->eedf_dE = c->eedf_dE;
+    s->eedf_bins = c->eedf_bins;
+    s->iedf_dE = c->iedf_dE;
+    s->iedf_bins = c->iedf_bins;
+    s->iad_bins = c->iad_bins;
+  }
   s->step_end = n_steps;
   const std::string v = ecpic::validate_spec(*s);
   if (!v.empty()) {

@@ -128,7 +128,7 @@ __device__ long long seg_prefix(const BatchView& b, int mode, int only, long lon
     if (s < b.nseg) {
       const int slot = b.segs[s].run;
       const long long c = !run_live(b.runs[slot], b.rst[slot], mode, only, slot) ? 0
-                          : reals ? b.sst[s].n_real
+                          : reals ? b.sst[s].n_real + b.sst[s].n_imp
                                   : (b.sst[s].n_proc + unit - 1) / unit;
       pre[s] = c;
       loc += c;
@@ -370,6 +370,10 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   const float vb = v2 * e0;
   if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1))) {
     deposit_one(R->S + (size_t)sp * (N + 1), c, f);
+    if (sample && SP->q < 0.0 && c >= R->eedf_c0 && c <= R->eedf_c1)
+      atomicAdd(R->tal + (size_t)sp * R->tal_stride +
+                    tally_bin(kin_eV(SP->half_m_over_e, vb, yz2(v2 * e1, v2 * e2)), R->eedf_dEinv, R->eedf_n),
+                1ull);
     if (sample) {
       double* md = R->momd + (size_t)sp * 2 * (N + 1);
       atomicAdd(md + c, (double)((1.0f - f) * vb));
@@ -401,6 +405,22 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
     }
   }
   return make_float3(v1 * d0, v1 * d1, v1 * d2);
+}
+
+// Impact tallies of an ion absorbed at x = 0 this step: energy (eV) and
+// angle from the electrode normal (degrees) of the velocity that carried it
+// out; the absorbed slot keeps that velocity until the next sort.
+__device__ __noinline__ void tally_impact(const BatchView& b, int s, int i) {
+  const SegDev& G = b.segs[s];
+  const RunDev* R = b.runs + G.run;
+  const int sp = G.species, cur = b.sst[s].cur;
+  if (!chk(i >= 0 && i < G.cap, 26, i, G.cap)) return;
+  const float vx = G.vx[cur][i], yz = yz2(G.vy[cur][i], G.vz[cur][i]);
+  const float E = kin_eV(R->sp[sp].half_m_over_e, vx, yz);
+  const float th = atan2f(sqrtf(yz), fabsf(vx)) * 57.295779513082323f;
+  unsigned long long* tal = R->tal + (size_t)sp * R->tal_stride + R->eedf_n;
+  atomicAdd(tal + tally_bin(E, R->iedf_dEinv, R->iedf_n), 1ull);
+  atomicAdd(tal + R->iedf_n + tally_bin(th, R->iad_binv, R->iad_n), 1ull);
 }
 
 // A real (non-null) collision as recorded by the pass (Sec. 2a step 6):
@@ -470,6 +490,16 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, const Re
   G.vx[cur][i] = vx;
   G.vy[cur][i] = vy;
   G.vz[cur][i] = vz;
+  if (sample && SP->q < 0.0 && c >= R->eedf_c0 && c <= R->eedf_c1) {
+    // the pass binned the pre-collision energy of this central particle
+    const int b0 = tally_bin(kin_eV(SP->half_m_over_e, rec.vx, yz2(rec.vy, rec.vz)), R->eedf_dEinv, R->eedf_n);
+    const int b1 = tally_bin(kin_eV(SP->half_m_over_e, vx, yz2(vy, vz)), R->eedf_dEinv, R->eedf_n);
+    if (b0 != b1) {
+      unsigned long long* tal = R->tal + (size_t)sp * R->tal_stride;
+      atomicAdd(tal + b0, ~0ull);  // minus one, modulo 2^64
+      atomicAdd(tal + b1, 1ull);
+    }
+  }
   if (sample) {
     double* md = R->momd + (size_t)sp * 2 * (N + 1);
     const float d1v = vx - vx_old, d2v = vx * vx - vx_old * vx_old;
@@ -520,13 +550,18 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   const bool yz_stream = mcc && !heavy && thr24 >= (1u << 20);
   const bool load_yz = sample || yz_stream;
   const bool walls = bc != ECPIC_PERIODIC;
+  const bool eedf_on = sample && SP->q < 0.0;
+  const bool imp_on = stepping && walls && SP->q > 0.0 && G.imp_cap > 0;
+  const int ec0 = R->eedf_c0, ec1 = R->eedf_c1;
+  unsigned long long* tal = R->tal + (size_t)sp * R->tal_stride;
+  float* Psm = Msm + 2 * (b.nmax + 1);
   const uint64_t seed = R->seed;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
 
   int my_lo = INT_MAX, my_hi = -1;
   float ke = 0.0f;
-  unsigned ncand = 0, nlive = 0, nabs_l = 0, nabs_r = 0, nnan = 0;
+  unsigned ncand = 0, nlive = 0, nabs_l = 0, nabs_r = 0, nnan = 0, nimp_lost = 0;
   // this warp's candidate ring: index, Philox word A.y, |g|^2 or vx
   int* qi = reinterpret_cast<int*>(ring) + (threadIdx.x >> 5) * (3 * kRing);
   uint32_t* qr = reinterpret_cast<uint32_t*>(qi + kRing);
@@ -566,6 +601,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         }
       }
       bool cand[4] = {false, false, false, false};
+      bool hit[4] = {false, false, false, false};  // absorbed at x = 0 (impact tallies)
 #pragma unroll
       for (int j = 0; j < 4; ++j) nlive += c[j] >= 0 ? 1u : 0u;
       if (stepping) {
@@ -586,14 +622,14 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
           if (full) {
             const float4 y4 = *reinterpret_cast<const float4*>(pvy + i0);
             const float4 z4 = *reinterpret_cast<const float4*>(pvz + i0);
-            yz[0] = y4.x * y4.x + z4.x * z4.x;
-            yz[1] = y4.y * y4.y + z4.y * z4.y;
-            yz[2] = y4.z * y4.z + z4.z * z4.z;
-            yz[3] = y4.w * y4.w + z4.w * z4.w;
+            yz[0] = yz2(y4.x, z4.x);
+            yz[1] = yz2(y4.y, z4.y);
+            yz[2] = yz2(y4.z, z4.z);
+            yz[3] = yz2(y4.w, z4.w);
           } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-              if (c[j] >= 0) yz[j] = pvy[i0 + j] * pvy[i0 + j] + pvz[i0 + j] * pvz[i0 + j];
+              if (c[j] >= 0) yz[j] = yz2(pvy[i0 + j], pvz[i0 + j]);
           }
         }
         // gather (Eq. 6-7; CIC for MC) and push (Eq. 8), branch-free over the
@@ -614,7 +650,11 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float vnew = v[j] + qm_dt * Ei[j];
-          if (sample && c[j] >= 0) ke += v[j] * vnew + yz[j];
+          if (sample && c[j] >= 0) {
+            ke += v[j] * vnew + yz[j];
+            // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
+            atomicAdd(Psm + c[j], (v[j] + vnew) * Ei[j]);
+          }
           v[j] = vnew;
         }
         // Philox block A of all four: independent chains the scheduler
@@ -650,6 +690,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
             nnan += bad ? 1u : 0u;
             nabs_r += (live && !bad && out && cj >= N) ? 1u : 0u;
             nabs_l += (live && !bad && out && cj < N) ? 1u : 0u;
+            hit[j] = imp_on && live && !bad && out && cj < N;
             c[j] = ok ? cj : -1;
             f[j] = g;
             cand[j] = mcc && ok && (r0[j] >> 8) < thr24;
@@ -669,6 +710,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
             if (walls && (cj < 0 || cj >= N || (cj == 0 && fj == 0.0f))) {
               nabs_r += cj >= N ? 1u : 0u;
               nabs_l += cj >= N ? 0u : 1u;
+              hit[j] = imp_on && cj < N;
               c[j] = -1;
               continue;
             }
@@ -689,6 +731,33 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
               pxi[i0 + j] = f[j];
               pvx[i0 + j] = v[j];
             }
+        }
+        // ions absorbed at x = 0: their indices, for the impact tallies of the
+        // collision kernel (the absorbed slot keeps its velocity until the sort)
+        if (imp_on) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const unsigned m = __ballot_sync(kFull, hit[j]);
+            if (m) {
+              const int lead = __ffs(m) - 1;
+              unsigned long long base = 0ull;
+              if (lane == lead) base = atomicAdd((unsigned long long*)&ss->n_imp, (unsigned long long)__popc(m));
+              base = __shfl_sync(kFull, base, lead);
+              if (hit[j]) {
+                const long long idx = (long long)base + __popc(m & lt_mask);
+                if (idx < G.imp_cap) G.imp[idx] = (int)(i0 + j);
+                else ++nimp_lost;
+              }
+            }
+          }
+        }
+        // EEDF of the central cells on sample steps (pre-collision; the
+        // collision kernel moves the particles that collide)
+        if (eedf_on) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (c[j] >= ec0 && c[j] <= ec1)
+              atomicAdd(tal + tally_bin(kin_eV(SP->half_m_over_e, v[j], yz[j]), R->eedf_dEinv, R->eedf_n), 1ull);
         }
         if (mcc) {
           // a candidate with Rr >= nu_bnd |g| is a null collision whatever its
@@ -826,6 +895,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   nabs_l = warp_sum(nabs_l);
   nabs_r = warp_sum(nabs_r);
   nnan = warp_sum(nnan);
+  nimp_lost = warp_sum(nimp_lost);
   if (lane == 0 && stepping && nlive) atomicAdd(&st->psteps, (unsigned long long)nlive);
   if (lane == 0) {
     if (my_hi >= 0) {
@@ -835,6 +905,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
     if (ncand) atomicAdd(&sh.ctr[C_CAND], (unsigned long long)ncand);
     if (nabs_l) atomicAdd(&sh.ctr[C_ABS_L], (unsigned long long)nabs_l);
     if (nabs_r) atomicAdd(&sh.ctr[C_ABS_R], (unsigned long long)nabs_r);
+    if (nimp_lost) atomicAdd(&sh.ctr[C_IMP_LOST], (unsigned long long)nimp_lost);
     if (nnan) {
       atomicAdd(&sh.ctr[C_NAN], (unsigned long long)nnan);
       set_status(st, ECPIC_ERR_NAN);
@@ -852,6 +923,16 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   // before forming flo + threadIdx.x, which would overflow
   if (flo < fhi) dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
   const int nbeg = flo <= fhi ? flo + (int)threadIdx.x : fhi + 1;
+  if (sample) {
+    double* pwg = R->pw + (size_t)sp * N;
+    for (int j = threadIdx.x; j < N; j += kPassBlock) {
+      const float pj = Psm[j];
+      if (pj != 0.0f) {
+        atomicAdd(pwg + j, (double)pj);
+        Psm[j] = 0.0f;
+      }
+    }
+  }
   for (int nn = nbeg; nn <= fhi && sample; nn += kPassBlock) {
     const float m1 = Msm[nn], m2 = Msm[Nm + nn];
     if (m1 != 0.0f) atomicAdd(md + nn, (double)m1);
@@ -884,7 +965,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   uint32_t* dep = reinterpret_cast<uint32_t*>(pre + b.nseg + 1);  // 3 (nmax+1): count, lo, hi
   float* Msm = reinterpret_cast<float*>(dep + 3 * (b.nmax + 1));
-  unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 2 * (b.nmax + 1));
+  unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 3 * (b.nmax + 1));  // Msm: M1 | M2 | J.E
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
     dep[i] = 0u;
@@ -892,6 +973,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     dep[2 * (b.nmax + 1) + i] = 0u;
     Msm[i] = 0.0f;
     Msm[b.nmax + 1 + i] = 0.0f;
+    Msm[2 * (b.nmax + 1) + i] = 0.0f;
   }
   if (threadIdx.x < kNumCtr) sh.ctr[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
@@ -914,8 +996,8 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
   }
 }
 
-// Real collisions recorded by this step's pass, all segments, equal records
-// per warp.  Process counters are summed over the lanes that share a
+// Real collisions recorded by this step's pass, then its impact records,
+// all segments, equal records per warp.  Process counters are summed over the lanes that share a
 // (segment, process) before one atomic each.
 __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -930,10 +1012,15 @@ __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
     int s = 0;
     RealRec rec;
     rec.chosen = -1;
+    int imp_i = -1;  // an impact record instead: the absorbed ion's index
     if (valid) {
       s = seg_find(pre, b.nseg, r);
       const long long j = r - pre[s];
-      if (chk(j >= 0 && j < b.segs[s].real_cap, 25, j, b.segs[s].real_cap)) {
+      const long long nr = b.sst[s].n_real;
+      if (j >= nr) {
+        const long long ii = j - nr;
+        if (ii < b.segs[s].imp_cap) imp_i = b.segs[s].imp[ii];
+      } else if (chk(j >= 0 && j < b.segs[s].real_cap, 25, j, b.segs[s].real_cap)) {
         const int4* src = reinterpret_cast<const int4*>(b.segs[s].real + j);  // RealRec field order
         const int4 w0 = src[0], w1 = src[1], w2 = src[2];
         rec.id = (uint64_t)(uint32_t)w0.x | ((uint64_t)(uint32_t)w0.y << 32);
@@ -956,6 +1043,7 @@ __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
       atomicAdd(&b.rst[G.run].ctr[G.species][C_COLL0 + rec.chosen], (unsigned long long)__popc(grp));
     }
     if (ok) collide_real(b, s, rec);
+    if (imp_i >= 0) tally_impact(b, s, imp_i);
   }
 }
 
@@ -1153,6 +1241,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
         ss->n_proc = n;
         ss->n_alloc = n;
         ss->n_real = 0;
+        ss->n_imp = 0;
       }
     }
   }
@@ -1490,7 +1579,7 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 // ----------------------------------------------------------------- launchers
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
-         3 * sizeof(uint32_t) * (size_t)(b.nmax + 1) + sizeof(float) * 2 * (size_t)(b.nmax + 1) +
+         3 * sizeof(uint32_t) * (size_t)(b.nmax + 1) + sizeof(float) * 3 * (size_t)(b.nmax + 1) +
          sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32);
 }
 

@@ -42,6 +42,33 @@ long long real_capacity(const HostSpecies& sp, const RunSpec& s) {
   return bound < (double)sp.cap ? (long long)bound : (long long)sp.cap;
 }
 
+// Impact records per step: absorbed ions at x = 0 are few per step in a
+// discharge; 4096 + cap/64 per species, the excess counted as dropped.
+long long impact_capacity(const HostSpecies& sp) { return sp.q > 0.0 ? 4096 + sp.cap / 64 : 0; }
+
+// cells whose centres lie within centre +- halfwidth, else the cell holding
+// the centre (the EEDF region)
+void eedf_cells(const RunSpec& s, int* c0, int* c1) {
+  const size_t N = s.edges.size() - 1;
+  const double L = s.edges[N];
+  const double xc = s.eedf_center < 0.0 ? 0.5 * L : s.eedf_center;
+  *c0 = (int)N;
+  *c1 = -1;
+  for (size_t j = 0; j < N; ++j) {
+    const double cj = 0.5 * (s.edges[j] + s.edges[j + 1]);
+    if (cj >= xc - s.eedf_halfwidth && cj <= xc + s.eedf_halfwidth) {
+      *c0 = std::min(*c0, (int)j);
+      *c1 = (int)j;
+    }
+  }
+  if (*c0 > *c1) {
+    const double x = xc < L ? xc : 0.0;
+    size_t j = 0;
+    while (j + 1 < N && s.edges[j + 1] <= x) ++j;
+    *c0 = *c1 = (int)j;
+  }
+}
+
 size_t layout_bytes(const RunSpec& s) {
   const size_t N = s.edges.size() - 1, ns = s.species.size();
   size_t b = 0;
@@ -69,6 +96,9 @@ size_t layout_bytes(const RunSpec& s) {
       add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(8 * c);
     }
   for (const auto& sp : s.species) add(sizeof(RealRec) * (size_t)real_capacity(sp, s));
+  for (const auto& sp : s.species) add(sizeof(int) * (size_t)impact_capacity(sp));
+  add(8 * ns * (size_t)(s.eedf_bins + s.iedf_bins + s.iad_bins));  // tallies
+  add(8 * ns * N);                                                  // J.E sums
   return b;
 }
 }  // namespace
@@ -83,7 +113,21 @@ std::string validate_grid(const std::vector<double>& e, int bc) {
   return "";
 }
 
+std::string validate_tallies(const RunSpec& s) {
+  if (!(s.eedf_halfwidth >= 0.0) || !std::isfinite(s.eedf_center) || !std::isfinite(s.eedf_halfwidth))
+    return "bad EEDF region";
+  if (!(s.eedf_dE > 0.0) || !(s.iedf_dE > 0.0)) return "tally bin widths must be positive";
+  if (s.eedf_bins < 1 || s.iedf_bins < 1 || s.iad_bins < 1 || s.eedf_bins > 65536 ||
+      s.iedf_bins > 65536 || s.iad_bins > 65536)
+    return "tally bin counts must be 1..65536";
+  return "";
+}
+
 std::string validate_spec(const RunSpec& s) {
+  {
+    const std::string t = validate_tallies(s);
+    if (!t.empty()) return t;
+  }
   std::string e = validate_grid(s.edges, s.bc);
   if (!e.empty()) return e;
   if (s.scheme != ECPIC_SCHEME_EC && s.scheme != ECPIC_SCHEME_MC) return "unknown scheme";
@@ -183,6 +227,32 @@ void fill_diag(const Diag& d, const RunSpec& spec, ecpic_diag* out) {
     }
   if (out->phi)
     for (size_t n = 0; n < M; ++n) out->phi[n] = d.acc[(size_t)(5 * ns) * M + n] * inv;
+  // tallies
+  out->eedf_bins = spec.eedf_bins;
+  out->iedf_bins = spec.iedf_bins;
+  out->iad_bins = spec.iad_bins;
+  out->eedf_cell0 = d.eedf_c0;
+  out->eedf_cell1 = d.eedf_c1;
+  out->eedf_dE = spec.eedf_dE;
+  out->iedf_dE = spec.iedf_dE;
+  for (int s = 0; s < kMaxSpecies; ++s)
+    out->impacts_dropped[s] = s < ns ? (int64_t)d.st.ctr[s][C_IMP_LOST] : 0;
+  const size_t stride = (size_t)spec.eedf_bins + spec.iedf_bins + spec.iad_bins;
+  if (d.tal.size() < (size_t)ns * stride || d.pw.size() < (size_t)ns * N) return;
+  for (int s = 0; s < ns; ++s) {
+    const unsigned long long* t = d.tal.data() + s * stride;
+    for (int b = 0; b < spec.eedf_bins; ++b)
+      if (out->eedf) out->eedf[(size_t)s * spec.eedf_bins + b] = (double)t[b];
+    for (int b = 0; b < spec.iedf_bins; ++b)
+      if (out->iedf) out->iedf[(size_t)s * spec.iedf_bins + b] = (double)t[spec.eedf_bins + b];
+    for (int b = 0; b < spec.iad_bins; ++b)
+      if (out->iad) out->iad[(size_t)s * spec.iad_bins + b] = (double)t[spec.eedf_bins + spec.iedf_bins + b];
+    // J.E = q w (v^- + v^+)/2 E_i / dx_j, summed per sample, mean over samples
+    const double qw = spec.species[s].q * spec.species[s].w;
+    for (int j = 0; j < N && out->power; ++j)
+      out->power[(size_t)s * N + j] =
+          0.5 * qw * d.pw[(size_t)s * N + j] / (spec.edges[j + 1] - spec.edges[j]) * inv;
+  }
 }
 
 // ------------------------------------------------------------------ Batch
@@ -333,6 +403,18 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   R.momd = cv.take<double>((size_t)ns * 2 * (N + 1));
   R.acc = cv.take<double>((size_t)acc_size(ns) * (N + 1));
   R.mom = nullptr;
+  R.eedf_n = spec.eedf_bins;
+  R.iedf_n = spec.iedf_bins;
+  R.iad_n = spec.iad_bins;
+  R.tal_stride = spec.eedf_bins + spec.iedf_bins + spec.iad_bins;
+  R.tal = cv.take<unsigned long long>((size_t)ns * R.tal_stride);
+  R.pw = cv.take<double>((size_t)ns * N);
+  eedf_cells(spec, &R.eedf_c0, &R.eedf_c1);
+  R.eedf_dEinv = (float)(1.0 / spec.eedf_dE);
+  R.iedf_dEinv = (float)(1.0 / spec.iedf_dE);
+  R.iad_binv = (float)(spec.iad_bins / 90.0);
+  cudaMemsetAsync(R.tal, 0, 8 * (size_t)ns * R.tal_stride, stream_);
+  cudaMemsetAsync(R.pw, 0, 8 * (size_t)ns * N, stream_);
   R.x = d_x;
   R.dx = d_dx;
   R.V = d_V;
@@ -443,11 +525,15 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     }
     G.real = nullptr;
     G.real_cap = 0;
+    G.imp = nullptr;
+    G.imp_cap = 0;
   }
   for (int s = 0; s < ns; ++s) {
     SegDev& G = h_segs_[R.seg0 + s];
     G.real_cap = real_capacity(spec.species[s], spec);
     G.real = cv.take<RealRec>((size_t)G.real_cap);
+    G.imp_cap = impact_capacity(spec.species[s]);
+    G.imp = cv.take<int>((size_t)G.imp_cap);
   }
   cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
                   stream_);
@@ -883,6 +969,12 @@ int Batch::diag(int slot, Diag* out, std::string* err) {
   cudaMemcpy(ss.data(), d_sst_ + slot * spc_, sizeof(SegState) * spc_, cudaMemcpyDeviceToHost);
   for (int s = 0; s < R.ns; ++s) out->n_live[s] = ss[s].n_proc - ss[s].n_dead;
   out->acc.resize((size_t)acc_size(R.ns) * (R.N + 1));
+  out->tal.resize((size_t)R.ns * R.tal_stride);
+  out->pw.resize((size_t)R.ns * R.N);
+  out->eedf_c0 = R.eedf_c0;
+  out->eedf_c1 = R.eedf_c1;
+  cudaMemcpy(out->tal.data(), R.tal, 8 * out->tal.size(), cudaMemcpyDeviceToHost);
+  cudaMemcpy(out->pw.data(), R.pw, 8 * out->pw.size(), cudaMemcpyDeviceToHost);
   return check(cudaMemcpy(out->acc.data(), R.acc, 8 * out->acc.size(), cudaMemcpyDeviceToHost),
                "diagnostics read", err);
 }
@@ -901,6 +993,8 @@ int Batch::reset_averages(int slot, int sample_every, std::string* err) {
   upload_run(slot);
   cudaMemsetAsync(R.acc, 0, 8 * (size_t)acc_size(R.ns) * (R.N + 1), stream_);
   cudaMemsetAsync(R.momd, 0, 8 * (size_t)R.ns * 2 * (R.N + 1), stream_);
+  cudaMemsetAsync(R.tal, 0, 8 * (size_t)R.ns * R.tal_stride, stream_);
+  cudaMemsetAsync(R.pw, 0, 8 * (size_t)R.ns * R.N, stream_);
   RunState st;
   cudaMemcpy(&st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
   st.n_samples = 0;

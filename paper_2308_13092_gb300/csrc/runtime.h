@@ -38,12 +38,16 @@ struct RunSpec {
   std::vector<double> T_eV;
   int sample_every = 0;
   int quiet = 0;  // loader: evenly spaced positions (quiet start)
+  // tallies: EEDF region (centre < 0: L/2) and bins, impact bins
+  double eedf_center = -1.0, eedf_halfwidth = 0.5e-3, eedf_dE = 0.5, iedf_dE = 2.0;
+  int eedf_bins = 100, iedf_bins = 256, iad_bins = 90;
   long long step_end = LLONG_MAX;
 };
 
 // argument checks of a complete run description; "" when valid
 std::string validate_grid(const std::vector<double>& edges, int bc);
 std::string validate_spec(const RunSpec& s);
+std::string validate_tallies(const RunSpec& s);
 // null-collision bound of a species (FP64, host): nu_max and the 24-bit
 // candidate threshold
 void null_rate(const HostSpecies& sp, const RunSpec& s, double* nu_max, uint32_t* thr24);
@@ -53,6 +57,9 @@ size_t run_bytes(const RunSpec& s);
 struct Diag {
   RunState st;
   std::vector<double> acc;
+  std::vector<unsigned long long> tal;  // ns * (eedf + iedf + iad bins)
+  std::vector<double> pw;               // ns * N
+  int eedf_c0 = 0, eedf_c1 = -1;
   long long n_live[kMaxSpecies] = {0, 0, 0, 0};
   int N = 0, ns = 0;
 };

@@ -43,7 +43,16 @@ class ecpic_diag(C.Structure):
         ("collisions", (C.c_int64 * 8) * 4), ("ke", C.c_double * 4), ("fe", C.c_double),
         ("n_samples", C.c_int64), ("density", C.c_void_p), ("phi", C.c_void_p),
         ("temp_x", C.c_void_p), ("temp_x_mom", C.c_void_p),
+        ("eedf_bins", C.c_int), ("iedf_bins", C.c_int), ("iad_bins", C.c_int),
+        ("eedf_cell0", C.c_int), ("eedf_cell1", C.c_int), ("eedf_dE", C.c_double),
+        ("iedf_dE", C.c_double), ("impacts_dropped", C.c_int64 * 4), ("eedf", C.c_void_p),
+        ("iedf", C.c_void_p), ("iad", C.c_void_p), ("power", C.c_void_p),
     ]
+
+
+# default tally shape: (eedf, iedf, iad) bins
+TALLY_DEFAULT = dict(eedf_center=-1.0, eedf_halfwidth=0.5e-3, eedf_dE=0.5, eedf_bins=100,
+                     iedf_dE=2.0, iedf_bins=256, iad_bins=90)
 
 
 class ecpic_process_desc(C.Structure):
@@ -61,6 +70,9 @@ class ecpic_run_config(C.Structure):
         ("T_eV", C.c_double * 4), ("n_gas", C.c_double), ("T_gas", C.c_double),
         ("m_gas", C.c_double), ("n_proc", C.c_int), ("procs", C.c_void_p), ("seed", C.c_uint64),
         ("dt", C.c_double), ("sample_every", C.c_int), ("quiet_start", C.c_int),
+        ("eedf_center", C.c_double), ("eedf_halfwidth", C.c_double), ("eedf_dE", C.c_double),
+        ("eedf_bins", C.c_int), ("iedf_dE", C.c_double), ("iedf_bins", C.c_int),
+        ("iad_bins", C.c_int),
     ]
 
 
@@ -81,6 +93,7 @@ SIGNATURES = {
     "ecpic_engine_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_set_quiet_start": (i32, [vp, i32]),
+    "ecpic_set_tallies": (i32, [vp, d, d, d, i32, d, i32, i32]),
     "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
     "ecpic_destroy": (None, [vp]),
     "ecpic_last_error": (C.c_char_p, [vp]),
@@ -191,6 +204,7 @@ class Run:
         self.ns = 0
         self.N = 0
         self.scheme = ECPIC_SCHEME_EC
+        self.tally = dict(TALLY_DEFAULT)
 
     @classmethod
     def from_config(cls, cfg, device=0, stream=None, sort_every=None, init=True):
@@ -207,6 +221,8 @@ class Run:
             r.set_sort_every(sort_every)
         if getattr(cfg, "quiet", False):
             r.set_quiet_start(True)
+        if getattr(cfg, "tallies", None):
+            r.set_tallies(**cfg.tallies)
         if init:
             r.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
             if cfg.sample_every:
@@ -287,6 +303,14 @@ class Run:
         _chk(self.h, self._L.ecpic_set_quiet_start(self.h, 1 if quiet else 0),
              "ecpic_set_quiet_start")
 
+    def set_tallies(self, **kw):
+        t = dict(TALLY_DEFAULT)
+        t.update(kw)
+        _chk(self.h, self._L.ecpic_set_tallies(self.h, t["eedf_center"], t["eedf_halfwidth"],
+                                               t["eedf_dE"], t["eedf_bins"], t["iedf_dE"],
+                                               t["iedf_bins"], t["iad_bins"]), "ecpic_set_tallies")
+        self.tally = t
+
     def autotune(self, steps_per_trial=64):
         k, g, ns = C.c_int(), C.c_int(), C.c_double()
         _chk(self.h, self._L.ecpic_autotune(self.h, int(steps_per_trial), C.byref(k), C.byref(g),
@@ -329,35 +353,17 @@ class Run:
 
     def diagnostics(self, profiles=True):
         dg = ecpic_diag()
-        arrs = {}
-        if profiles:
-            M = self.N + 1
-            arrs = dict(density=np.zeros(self.ns * M), phi=np.zeros(M),
-                        temp_x=np.zeros(self.ns * M), temp_x_mom=np.zeros(self.ns * M))
-            for k, a in arrs.items():
-                setattr(dg, k, _p(a))
+        arrs = _diag_arrays(dg, self.ns, self.N, self.tally) if profiles else None
         _chk(self.h, self._L.ecpic_diagnostics(self.h, C.byref(dg)), "ecpic_diagnostics")
-        ns = self.ns
-        out = dict(step=dg.step, time=dg.time, n_samples=dg.n_samples, fe=dg.fe,
-                   ke=np.array(dg.ke[:ns]), species=[])
-        for s in range(ns):
-            out["species"].append(dict(
-                n=dg.n_live[s], absorbed_left=dg.absorbed[s][0], absorbed_right=dg.absorbed[s][1],
-                births=dg.births[s], lost=dg.lost[s], candidates=dg.candidates[s],
-                clamps=dg.clamps[s], collisions=list(dg.collisions[s])))
-        if profiles:
-            M = self.N + 1
-            out["density"] = arrs["density"].reshape(ns, M)
-            out["phi"] = arrs["phi"]
-            out["Tx"] = arrs["temp_x"].reshape(ns, M)
-            out["Tx_mom"] = arrs["temp_x_mom"].reshape(ns, M)
-        return out
+        return _diag_dict(dg, self.ns, self.N, arrs)
 
-
-def _diag_arrays(dg, ns, N):
+def _diag_arrays(dg, ns, N, tally=None):
+    t = TALLY_DEFAULT if tally is None else tally
     M = N + 1
     arrs = dict(density=np.zeros(ns * M), phi=np.zeros(M), temp_x=np.zeros(ns * M),
-                temp_x_mom=np.zeros(ns * M))
+                temp_x_mom=np.zeros(ns * M), eedf=np.zeros(ns * t["eedf_bins"]),
+                iedf=np.zeros(ns * t["iedf_bins"]), iad=np.zeros(ns * t["iad_bins"]),
+                power=np.zeros(ns * N))
     for k, a in arrs.items():
         setattr(dg, k, _p(a))
     return arrs
@@ -371,12 +377,20 @@ def _diag_dict(dg, ns, N, arrs=None):
             n=dg.n_live[s], absorbed_left=dg.absorbed[s][0], absorbed_right=dg.absorbed[s][1],
             births=dg.births[s], lost=dg.lost[s], candidates=dg.candidates[s],
             clamps=dg.clamps[s], collisions=list(dg.collisions[s])))
+    for s in range(ns):
+        out["species"][s]["impacts_dropped"] = dg.impacts_dropped[s]
     if arrs:
         M = N + 1
         out["density"] = arrs["density"].reshape(ns, M)
         out["phi"] = arrs["phi"]
         out["Tx"] = arrs["temp_x"].reshape(ns, M)
         out["Tx_mom"] = arrs["temp_x_mom"].reshape(ns, M)
+        out["eedf"] = arrs["eedf"].reshape(ns, dg.eedf_bins)
+        out["iedf"] = arrs["iedf"].reshape(ns, dg.iedf_bins)
+        out["iad"] = arrs["iad"].reshape(ns, dg.iad_bins)
+        out["power"] = arrs["power"].reshape(ns, N)
+        out["eedf_cells"] = (dg.eedf_cell0, dg.eedf_cell1)
+        out["eedf_dE"], out["iedf_dE"] = dg.eedf_dE, dg.iedf_dE
     return out
 
 
@@ -436,11 +450,15 @@ class Engine:
         rc.procs = C.cast(procs, C.c_void_p)
         rc.seed, rc.dt, rc.sample_every = int(cfg.seed), cfg.dt, int(cfg.sample_every)
         rc.quiet_start = 1 if getattr(cfg, "quiet", False) else 0
+        tally = dict(TALLY_DEFAULT)
+        tally.update(getattr(cfg, "tallies", None) or {})
+        for k, v in tally.items():
+            setattr(rc, k, v)
         t = C.c_uint64()
         n = int(cfg.n_steps if n_steps is None else n_steps)
         self._chk(self._L.ecpic_engine_submit(self.h, C.byref(rc), n, C.byref(t)),
                   "ecpic_engine_submit")
-        self._meta[t.value] = (len(cfg.species), cfg.N)
+        self._meta[t.value] = (len(cfg.species), cfg.N, tally)
         return t.value
 
     def pump(self, max_steps):
@@ -453,8 +471,8 @@ class Engine:
         st = C.c_int()
         steps, ps = C.c_int64(), C.c_int64()
         dg = ecpic_diag()
-        ns, N = self._meta.get(ticket, (0, 0))
-        arrs = _diag_arrays(dg, ns, N) if (diagnostics and profiles) else None
+        ns, N, tally = self._meta.get(ticket, (0, 0, None))
+        arrs = _diag_arrays(dg, ns, N, tally) if (diagnostics and profiles) else None
         self._chk(self._L.ecpic_engine_poll(self.h, ticket, C.byref(st),
                                             C.byref(dg) if diagnostics else None,
                                             C.byref(steps), C.byref(ps)), "ecpic_engine_poll")

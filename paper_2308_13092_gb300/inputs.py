@@ -84,6 +84,7 @@ class RunConfig:
     n_steps: int
     sample_every: int = 0
     quiet: bool = False  # loader: evenly spaced positions (quiet start)
+    tallies: Optional[dict] = None  # diagnostic tally set-up (None: defaults)
 
     @property
     def N(self) -> int:

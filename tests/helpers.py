@@ -20,6 +20,8 @@ def oracle_from_config(cfg: I.RunConfig, init: bool = True):
         o.reset_averages(cfg.sample_every)
     if getattr(cfg, "quiet", False):
         o.set_quiet_start(True)
+    if getattr(cfg, "tallies", None):
+        o.set_tallies(**cfg.tallies)
     if init:
         o.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
     return o

@@ -1,5 +1,6 @@
-"""Full-run statistical parity with the oracle: time-averaged profiles and
-event rates of the small discharge (128 cells, 16,384 particles at start,
+"""Full-run statistical parity with the oracle: time-averaged profiles,
+diagnostic tallies (central EEDF and ion impact energies, normalised; J.E
+per cell) and event rates of the small discharge (128 cells, 16,384 particles at start,
 1200 steps of its ionisation-driven growth, averages sampled every 10 steps,
 capacity doubled so that no run fills it).
 
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 STEPS = 1200
 GPU_SEEDS = tuple(range(100, 108))
 ORACLE_SEEDS = (200, 201)
-PROFILES = ("ne", "ni", "phi", "Te", "Ti")
+PROFILES = ("ne", "ni", "phi", "Te", "Ti", "eedf", "iedf", "Pe", "Pi")
 
 
 def _cfg(seed):
@@ -34,11 +35,14 @@ def _cfg(seed):
     return c
 
 
-def _summary(avg, species):
-    """Profiles and per-step event rates of one run."""
+def _summary(avg, species, tal):
+    """Profiles, tallies and per-step event rates of one run."""
     out = dict(ne=np.asarray(avg["density"][0], float), ni=np.asarray(avg["density"][1], float),
                phi=np.asarray(avg["phi"], float), Te=np.asarray(avg["Tx"][0], float),
-               Ti=np.asarray(avg["Tx"][1], float))
+               Ti=np.asarray(avg["Tx"][1], float),
+               eedf=np.asarray(tal["eedf"][0], float) / max(1.0, float(np.sum(tal["eedf"][0]))),
+               iedf=np.asarray(tal["iedf"][1], float) / max(1.0, float(np.sum(tal["iedf"][1]))),
+               Pe=np.asarray(tal["power"][0], float), Pi=np.asarray(tal["power"][1], float))
     e, i = species[0], species[1]
     out["rates"] = np.array([e["collisions"][0], e["collisions"][1], e["collisions"][2],
                              i["collisions"][0], i["collisions"][1], e["births"],
@@ -63,13 +67,13 @@ def ensembles():
         assert res["state"] == 2
         d = res["diag"]
         assert d["step"] == STEPS
-        gpu.append(_summary(d, d["species"]))
+        gpu.append(_summary(d, d["species"], d))
     eng.close()
     ora = []
     for s in ORACLE_SEEDS:
         o = oracle_from_config(_cfg(s))
         o.step(STEPS, allow_capacity=True)
-        ora.append(_summary(o.averages(), o.counters()["species"]))
+        ora.append(_summary(o.averages(), o.counters()["species"], o.tallies()))
         o.close()
     return gpu, ora
 
