@@ -521,7 +521,12 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, const Re
 // candidate probability is 1/16 or more (its candidates then touch most
 // 32-byte sectors anyway) and on energy-sample steps; otherwise the test
 // reads them per candidate.
-__device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
+//
+// Compiled once per SAMPLE: energy-sample steps (moments, energy, EEDF, J.E)
+// are rare, and keeping their code out of the common instance keeps the
+// common loop small in the instruction cache.
+template <bool SAMPLE>
+__device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
@@ -540,7 +545,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
   const uint64_t* pid = G.id[cur];
   const long long k = st->step;
   const bool stepping = (mode == MODE_STEP);
-  const bool sample = stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0;
+  constexpr bool sample = SAMPLE;
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
   const float* __restrict__ E = R->E;
@@ -734,7 +739,7 @@ __device__ void pass_piece(const BatchView& b, int s, long long qbeg, long long 
         }
         // ions absorbed at x = 0: their indices, for the impact tallies of the
         // collision kernel (the absorbed slot keeps its velocity until the sort)
-        if (imp_on) {
+        if (imp_on && __any_sync(kFull, hit[0] || hit[1] || hit[2] || hit[3])) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const unsigned m = __ballot_sync(kFull, hit[j]);
@@ -992,7 +997,16 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const long long end = min(hi, pre[s + 1]) - pre[s];
     if (beg >= end) continue;
     if (!chk(b.segs[s].run >= 0 && b.segs[s].run < b.max_slots, 23, s, b.nseg)) continue;
-    pass_piece(b, s, beg, end, mode, dep, Msm, ring, sh);
+    // which instance: a sampled step of a stepping pass
+    const SegDev& G = b.segs[s];
+    const RunDev& R = b.runs[G.run];
+    const bool stepping = mode == MODE_STEP;
+    const long long k = b.rst[G.run].step;
+    const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
+    if (smp)
+      pass_piece<true>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    else
+      pass_piece<false>(b, s, beg, end, mode, dep, Msm, ring, sh);
   }
 }
 
