@@ -57,8 +57,8 @@ AUTOTUNE_STEPS = 64  # steps per autotuner trial (16 trials) before the warm-up
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "95172eb32cd97094baab5af01f5d8a3ffc992c2c8357648e8dcb874b907f4363",
-           "dram_bytes_per_particle_step": 525.727e6 / 14.326e6}
+TRAFFIC = {"sources_sha256": "f67a7b7eb3ec2b270af9d5602838bfcd44df1afae1938a6613e39612273eb874",
+           "dram_bytes_per_particle_step": 567.739e6 / 14.326e6}
 
 
 def kernel_sources_sha256():
@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--runs", type=int, default=N_RUNS)
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="engine defaults (sort every 16 steps, automatic grid) instead of the autotuner")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only (no single-run, one-by-one, served, e2e)")
     return ap.parse_args()
@@ -435,7 +437,11 @@ def main():
     eng.pump(0)  # admit and load everything
     # sort cadence and pass grid from the autotuner (its trials are steps of
     # the same runs, before the warm-up)
-    tuned = eng.autotune(AUTOTUNE_STEPS)
+    if args.no_autotune:
+        tuned = {"sort_every": 16, "pass_ctas": 0}
+        eng.tune(0, 16)
+    else:
+        tuned = eng.autotune(AUTOTUNE_STEPS)
     eng_sort_every = tuned["sort_every"]
     eng.pump(args.warmup)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,7 +509,8 @@ def main():
                                    f"{min(c.N for c in cfgs)}-{max(c.N for c in cfgs)}",
                        "runs_per_gpu": len(cfgs), "l2": "inputs larger than L2 (1.5 GB state)",
                        "sort_every": sort_every, "pass_ctas": tuned["pass_ctas"] or "auto",
-                       "tuning": "autotuner (sort cadence x pass grid) before the warm-up",
+                       "tuning": "defaults" if args.no_autotune else
+                                 "autotuner (sort cadence x pass grid) before the warm-up",
                        "sample_every": 40, "scheme": "EC",
                        "arithmetic": "FP32 particles, FP64 field solve"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
