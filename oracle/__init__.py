@@ -4,8 +4,8 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``.  The GPU product never imports it.
 """
 from .oracle import (  # noqa: F401
-    OracleRun, build, lib, philox4x32_10, child_id, deposit_fixed,
+    OracleRun, build, lib, philox4x32_10, child_id, deposit_fixed, deposit_fixed2,
     poisson_thomas, poisson_dense, field, doubling_grid,
     ELASTIC, EXCITATION, IONIZATION, ION_ELASTIC, CX,
-    DIRICHLET, PERIODIC, EC, MC,
+    DIRICHLET, PERIODIC, EC, MC, EC2,
 )

@@ -431,9 +431,49 @@ int oracle_set_grid(or_run* r, const double* edges, int n_edges, int bc,
   return 0;
 }
 
+static int or_uniform(const or_run* r) {
+  for (int j = 0; j < r->N; ++j)
+    if (fabs(r->dx[j] - r->dx[0]) > 1e-9 * r->dx[0]) return 0;
+  return 1;
+}
+
 int oracle_set_scheme(or_run* r, int scheme) {
-  if (!r || (scheme != OR_SCHEME_EC && scheme != OR_SCHEME_MC)) return -1;
+  if (!r || (scheme != OR_SCHEME_EC && scheme != OR_SCHEME_MC && scheme != OR_SCHEME_EC2)) return -1;
+  /* the quadratic deposit is written for uniform cells */
+  if (scheme == OR_SCHEME_EC2 && r->grid_set && !or_uniform(r)) return -1;
   r->scheme = scheme;
+  return 0;
+}
+
+/* node index of a quadratic share: folded at Dirichlet walls, wrapped when
+ * periodic (node N is node 0) */
+static int or_node2(int n, int N, int bc) {
+  if (bc == OR_PERIODIC) {
+    n %= N;
+    return n < 0 ? n + N : n;
+  }
+  return n < 0 ? 0 : (n > N ? N : n);
+}
+
+int oracle_deposit_fixed2(int N, int bc, int64_t n, const int32_t* cell, const float* xi,
+                          uint64_t* S) {
+  if (N < 1 || n < 0 || (n > 0 && (!cell || !xi)) || !S) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int j = cell[i];
+    float f = xi[i];
+    if (j < 0 || j >= N || !(f >= 0.0f) || !(f < 1.0f)) return -1;
+    uint32_t r32 = (uint32_t)((double)f * 4294967296.0); /* floor, f < 1 */
+    int n0 = r32 < 2147483648u ? j : j + 1;
+    int64_t U = r32 < 2147483648u ? (int64_t)r32 : (int64_t)r32 - 4294967296LL;
+    unsigned __int128 A = (unsigned __int128)(uint64_t)(2147483648LL - U);
+    unsigned __int128 B = (unsigned __int128)(uint64_t)(2147483648LL + U);
+    uint64_t a = (uint64_t)((A * A) >> 33), b = (uint64_t)((B * B) >> 33);
+    uint64_t m = 4294967296ull - a - b;
+    S[or_node2(n0 - 1, N, bc)] += a;
+    S[or_node2(n0, N, bc)] += m;
+    S[or_node2(n0 + 1, N, bc)] += b;
+  }
+  if (bc == OR_PERIODIC) S[N] = S[0];
   return 0;
 }
 
@@ -574,15 +614,26 @@ static void or_deposit(or_run* r) {
       int j = or_locate(r, s->X[i]);
       double xi = (s->X[i] - r->x[j]) / r->dx[j];
       double v = s->vx[i];
-      s->D[j] += 1.0 - xi;
-      s->D[j + 1] += xi;
+      if (r->scheme == OR_SCHEME_EC2) {
+        /* quadratic B-spline charge shares about the nearest node n0 */
+        int n0 = xi < 0.5 ? j : j + 1;
+        double u = xi < 0.5 ? xi : xi - 1.0;
+        double a = 0.5 * (0.5 - u) * (0.5 - u), b = 0.5 * (0.5 + u) * (0.5 + u);
+        s->D[or_node2(n0 - 1, N, r->bc)] += a;
+        s->D[or_node2(n0, N, r->bc)] += 0.75 - u * u;
+        s->D[or_node2(n0 + 1, N, r->bc)] += b;
+      } else {
+        s->D[j] += 1.0 - xi;
+        s->D[j + 1] += xi;
+      }
       s->M1[j] += (1.0 - xi) * v;
       s->M1[j + 1] += xi * v;
       s->M2[j] += (1.0 - xi) * v * v;
       s->M2[j + 1] += xi * v * v;
     }
     if (r->bc == OR_PERIODIC) {
-      s->D[0] += s->D[N]; s->D[N] = s->D[0];
+      if (r->scheme != OR_SCHEME_EC2) s->D[0] += s->D[N];
+      s->D[N] = s->D[0];
       s->M1[0] += s->M1[N]; s->M1[N] = s->M1[0];
       s->M2[0] += s->M2[N]; s->M2[N] = s->M2[0];
     }
@@ -615,7 +666,8 @@ static int or_solve(or_run* r, int64_t k) {
   int rc = oracle_poisson_thomas(N, r->x, Qs, phi0, phiN, r->phi);
   free(Qs);
   if (rc) return rc;
-  return oracle_field(N, r->x, r->phi, r->bc, r->scheme, r->E);
+  return oracle_field(N, r->x, r->phi, r->bc, r->scheme == OR_SCHEME_MC ? OR_SCHEME_MC : OR_SCHEME_EC,
+                      r->E);
 }
 
 /* histogram bin of value v for bins of width d: floor(v / d), the last bin
@@ -681,6 +733,7 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
   for (int si = 0; si < r->ns; ++si)
     if (n_per_species[si] < 0 || n_per_species[si] > r->sp[si].cap || T_eV[si] < 0)
       return -1;
+  if (r->scheme == OR_SCHEME_EC2 && !or_uniform(r)) return -1;
   r->seed = seed;
   r->dt = dt;
   r->step = 0;
@@ -952,6 +1005,26 @@ static int or_collide(or_run* r, int si, int64_t i, int64_t k) {
   return rc;
 }
 
+/* EC2 gather: linear interpolation of the face fields about the nearest node
+ * n0 (faces n0-1 at n0-1/2 and n0 at n0+1/2), the derivative of the
+ * quadratic-spline potential; the face beyond a Dirichlet wall carries no
+ * field (its ghost node is the wall node), periodic faces wrap. */
+static double or_gather2(const or_run* r, int j, double xi) {
+  int N = r->N;
+  int n0 = xi < 0.5 ? j : j + 1;
+  double u = xi < 0.5 ? xi : xi - 1.0;
+  int fl = n0 - 1, fr = n0;
+  double El, Er;
+  if (r->bc == OR_PERIODIC) {
+    El = r->E[(fl + N) % N];
+    Er = r->E[fr % N];
+  } else {
+    El = fl < 0 ? 0.0 : r->E[fl];
+    Er = fr >= N ? 0.0 : r->E[fr];
+  }
+  return (0.5 - u) * El + (0.5 + u) * Er;
+}
+
 static int or_step_once(or_run* r) {
   int64_t k = r->step;
   int N = r->N;
@@ -975,6 +1048,7 @@ static int or_step_once(or_run* r) {
       int j = or_locate(r, X);
       double xi = (X - r->x[j]) / r->dx[j];
       double Ei = (r->scheme == OR_SCHEME_EC) ? r->E[j]
+                : (r->scheme == OR_SCHEME_EC2) ? or_gather2(r, j, xi)
                                                : (1.0 - xi) * r->E[j] + xi * r->E[j + 1];
       double vold = s->vx[i];
       double vnew = vold + qm * Ei * r->dt;
@@ -1107,7 +1181,7 @@ int oracle_get_fields(const or_run* r, double* phi, double* E, double* Q) {
   if (!r || !r->grid_set) return -1;
   int N = r->N;
   if (phi) memcpy(phi, r->phi, sizeof(double) * (size_t)(N + 1));
-  if (E) memcpy(E, r->E, sizeof(double) * (size_t)(r->scheme == OR_SCHEME_EC ? N : N + 1));
+  if (E) memcpy(E, r->E, sizeof(double) * (size_t)(r->scheme == OR_SCHEME_MC ? N + 1 : N));
   if (Q) memcpy(Q, r->Q, sizeof(double) * (size_t)(N + 1));
   return 0;
 }

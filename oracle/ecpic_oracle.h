@@ -39,6 +39,7 @@ extern "C" {
 #define OR_PERIODIC 1
 #define OR_SCHEME_EC 0
 #define OR_SCHEME_MC 1
+#define OR_SCHEME_EC2 2 /* quadratic-spline deposit, linear gather of the face field */
 
 typedef struct or_run or_run;
 
@@ -58,6 +59,15 @@ uint64_t oracle_child_id(uint64_t parent, int64_t step, uint64_t tag);
  * S has N+1 entries and is accumulated into (not cleared). */
 int oracle_deposit_fixed(int N, int64_t n, const int32_t* cell,
                          const float* xi, uint64_t* S);
+/* Quadratic-spline fixed-point deposit of EC2 (uniform grid): a particle at
+ * p = cell + xi (cell units) with r = floor(xi * 2^32) has its nearest node
+ * n0 = cell (r < 2^31) or cell + 1, offset U = r or r - 2^32 (2^-32 units);
+ * nodes n0-1, n0, n0+1 receive a = floor((2^31 - U)^2 / 2^33), 2^32 - a - b,
+ * b = floor((2^31 + U)^2 / 2^33) (exact integers, the shares of the
+ * quadratic B-spline to 2^-32).  Beyond a Dirichlet wall the share folds
+ * into the wall node; periodic indices wrap (node N is node 0). */
+int oracle_deposit_fixed2(int N, int bc, int64_t n, const int32_t* cell, const float* xi,
+                          uint64_t* S);
 
 /* Finite-volume Poisson, Eq. 4 on a (possibly non-uniform) grid:
  * (phi_{n+1}-phi_n)/dx_n - (phi_n-phi_{n-1})/dx_{n-1} = -Q_n/eps0,

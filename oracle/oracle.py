@@ -20,7 +20,7 @@ _SO = os.path.join(_HERE, "libecpic_oracle.so")
 
 ELASTIC, EXCITATION, IONIZATION, ION_ELASTIC, CX = 0, 1, 2, 3, 4
 DIRICHLET, PERIODIC = 0, 1
-EC, MC = 0, 1
+EC, MC, EC2 = 0, 1, 2  # EC2: quadratic-spline deposit, linear gather of the face field
 MAX_SPECIES, MAX_PROC = 4, 8
 
 _lock = threading.Lock()
@@ -57,6 +57,7 @@ def _load(path):
         "oracle_philox4x32_10": (None, [P(u32), P(u32), P(u32)]),
         "oracle_child_id": (u64, [u64, i64, u64]),
         "oracle_deposit_fixed": (i32, [i32, i64, vp, vp, vp]),
+        "oracle_deposit_fixed2": (i32, [i32, i32, i64, vp, vp, vp]),
         "oracle_poisson_thomas": (i32, [i32, vp, vp, d, d, vp]),
         "oracle_poisson_dense": (i32, [i32, vp, vp, d, d, vp]),
         "oracle_field": (i32, [i32, vp, vp, i32, i32, vp]),
@@ -121,6 +122,16 @@ def deposit_fixed(N, cell, xi, S=None):
         S = np.zeros(N + 1, dtype=np.uint64)
     _chk(lib().oracle_deposit_fixed(N, cell.size, _ptr(cell), _ptr(xi), _ptr(S)),
          "oracle_deposit_fixed")
+    return S
+
+
+def deposit_fixed2(N, bc, cell, xi, S=None):
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    xi = np.ascontiguousarray(xi, dtype=np.float32)
+    if S is None:
+        S = np.zeros(N + 1, dtype=np.uint64)
+    _chk(lib().oracle_deposit_fixed2(N, bc, cell.size, _ptr(cell), _ptr(xi), _ptr(S)),
+         "oracle_deposit_fixed2")
     return S
 
 
