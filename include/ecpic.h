@@ -58,6 +58,10 @@ typedef enum {
 /* field/gather scheme (Sec. 2a steps 3-4) */
 #define ECPIC_SCHEME_EC 0 /* face field Eq. 5, shifted NGP gather Eq. 6-7 */
 #define ECPIC_SCHEME_MC 1 /* centred node field, CIC gather */
+/* higher-order EC (Sec. 2a: the field interpolation one order below the
+ * charge deposit): quadratic-spline deposit, linear interpolation of the face
+ * field; uniform grids; the ghost node beyond a wall is the wall node */
+#define ECPIC_SCHEME_EC2 2
 /* collision processes (Sec. 2b) */
 #define ECPIC_ELASTIC 0     /* electron-neutral elastic, neutral at rest */
 #define ECPIC_EXCITATION 1  /* electron-impact excitation */
@@ -310,6 +314,14 @@ int ecpic_doubling_grid(int n_ref, double L, double L_buff, int dx_min, int dx_m
  * Particles with cell < 0 are skipped.  Async on cuda_stream. */
 int ecpic_deposit_device(int N, int64_t n, const int32_t* d_cell, const float* d_xi,
                          uint64_t* d_S, void* cuda_stream);
+/* Quadratic-spline fixed-point deposit of ECPIC_SCHEME_EC2: with r =
+ * floor(xi 2^32), nearest node n0 = cell + (r >= 2^31) and offset U = r or
+ * r - 2^32, nodes n0-1, n0, n0+1 receive a = floor((2^31-U)^2 / 2^33),
+ * 2^32 - a - b, b = floor((2^31+U)^2 / 2^33), added to d_S (N+1 uint64).
+ * bc: Dirichlet folds shares beyond a wall into the wall node; periodic wraps
+ * (node N is node 0, and d_S[N] is set to d_S[0] afterwards).  Async. */
+int ecpic_deposit_device2(int N, int bc, int64_t n, const int32_t* d_cell, const float* d_xi,
+                          uint64_t* d_S, void* cuda_stream);
 /* Bounds-check record of a library built with -DECPIC_CHECKS: out[0] = first
  * failing check site (0 = none), out[1] = its index, out[2] = its bound,
  * out[3] = number of failed checks.  Plain builds report zeros. */

@@ -310,7 +310,7 @@ class OracleRun:
     def fields(self):
         N = self.N
         phi = np.zeros(N + 1)
-        E = np.zeros(N if self.scheme == EC else N + 1)
+        E = np.zeros(N + 1 if self.scheme == MC else N)
         Q = np.zeros(N + 1)
         _chk(self._L.oracle_get_fields(self.h, _ptr(phi), _ptr(E), _ptr(Q)),
              "oracle_get_fields")

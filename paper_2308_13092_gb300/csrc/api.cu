@@ -143,7 +143,7 @@ int ecpic_set_grid(ecpic_run* r, const double* edges, int n_edges, int bc, doubl
 
 int ecpic_set_scheme(ecpic_run* r, int scheme) {
   if (!r) return ECPIC_ERR_ARG;
-  if (scheme != ECPIC_SCHEME_EC && scheme != ECPIC_SCHEME_MC)
+  if (scheme != ECPIC_SCHEME_EC && scheme != ECPIC_SCHEME_MC && scheme != ECPIC_SCHEME_EC2)
     return fail(r, ECPIC_ERR_ARG, "unknown scheme");
   if (r->batch) return fail(r, ECPIC_ERR_STATE, "scheme is fixed after init");
   r->spec.scheme = scheme;
@@ -400,6 +400,18 @@ int ecpic_deposit_device(int N, int64_t n, const int32_t* d_cell, const float* d
   if (n == 0) return ECPIC_OK;
   ecpic::launch_deposit_device(N, n, d_cell, d_xi, reinterpret_cast<unsigned long long*>(d_S),
                                static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? ECPIC_OK : ECPIC_ERR_CUDA;
+}
+
+int ecpic_deposit_device2(int N, int bc, int64_t n, const int32_t* d_cell, const float* d_xi,
+                          uint64_t* d_S, void* stream) {
+  if (N < 1 || N > ECPIC_MAX_CELLS || n < 0 || (n > 0 && (!d_cell || !d_xi)) || !d_S ||
+      (bc != ECPIC_DIRICHLET_RF && bc != ECPIC_PERIODIC))
+    return ECPIC_ERR_ARG;
+  if (n == 0) return ECPIC_OK;
+  ecpic::launch_deposit2_device(N, bc == ECPIC_PERIODIC ? 1 : 0, n, d_cell, d_xi,
+                                reinterpret_cast<unsigned long long*>(d_S),
+                                static_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? ECPIC_OK : ECPIC_ERR_CUDA;
 }
 

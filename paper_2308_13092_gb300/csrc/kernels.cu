@@ -221,6 +221,94 @@ __device__ void dep_flush(uint32_t* dcnt, uint32_t* dlo, uint32_t* dhi, int a, i
   }
 }
 
+// ---- quadratic-spline deposit of the EC2 scheme (uniform grids) ----------
+// A particle at cell + xi with r = floor(xi 2^32) has its nearest node
+// n0 = cell + (r >= 2^31) and offset U = r or r - 2^32 (2^-32 cell units);
+// nodes n0-1, n0, n0+1 get a = floor((2^31-U)^2 / 2^33), 2^32 - a - b,
+// b = floor((2^31+U)^2 / 2^33): the quadratic B-spline weights to 2^-32,
+// exact integers summing to 2^32.
+__device__ __forceinline__ void spline2_shares(float f, int c, int* n0, unsigned* a, unsigned* b) {
+  const unsigned r = __float2uint_rz(f * 4294967296.0f);
+  const bool up = r >= 0x80000000u;
+  *n0 = c + (up ? 1 : 0);
+  const long long U = up ? (long long)r - 4294967296LL : (long long)r;
+  const unsigned long long A = (unsigned long long)(2147483648LL - U);
+  const unsigned long long B = (unsigned long long)(2147483648LL + U);
+  *a = (unsigned)((__umul64hi(A, A) << 31) | ((A * A) >> 33));
+  *b = (unsigned)((__umul64hi(B, B) << 31) | ((B * B) >> 33));
+}
+
+// node of a share beyond the cells: folded into the wall node (Dirichlet: the
+// ghost node beyond a wall is the wall node), wrapped when periodic (node N
+// and node 0 are one node for the field solve)
+__device__ __forceinline__ int node2(int n, int N, bool periodic) {
+  if (periodic) return n < 0 ? n + N : (n > N ? n - N : n);
+  return n < 0 ? 0 : (n > N ? N : n);
+}
+
+// Adds four particles to two 32-bit sums per node (the low and high 16 bits
+// of the shares it receives, after folding or wrapping); runs of equal
+// nearest node merged first.  A wall node can receive two shares of one
+// particle, and a run's middle share can reach 2^34, so the EC2 pass flushes
+// every kFlushParticles / 4 particles: no sum reaches 2^32.
+__device__ __forceinline__ void dep2_add4(uint32_t* dlo, uint32_t* dhi, int N, bool periodic,
+                                          const int c[4], const float f[4]) {
+  int n0[4];
+  unsigned long long A[4], M[4], B[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    unsigned a = 0u, b = 0u;
+    n0[j] = -1;
+    if (c[j] >= 0) spline2_shares(f[j], c[j], &n0[j], &a, &b);
+    A[j] = a;
+    B[j] = b;
+    M[j] = c[j] >= 0 ? 4294967296ull - a - b : 0ull;
+  }
+#pragma unroll
+  for (int j = 3; j >= 1; --j) {
+    if (n0[j] >= 0 && n0[j] == n0[j - 1]) {
+      A[j - 1] += A[j];
+      M[j - 1] += M[j];
+      B[j - 1] += B[j];
+      n0[j] = -1;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (n0[j] >= 0) {
+      const int nl = node2(n0[j] - 1, N, periodic), nr = node2(n0[j] + 1, N, periodic);
+      atomicAdd(dlo + nl, (unsigned)(A[j] & 0xFFFFu));
+      atomicAdd(dhi + nl, (unsigned)(A[j] >> 16));
+      atomicAdd(dlo + n0[j], (unsigned)(M[j] & 0xFFFFu));
+      atomicAdd(dhi + n0[j], (unsigned)(M[j] >> 16));
+      atomicAdd(dlo + nr, (unsigned)(B[j] & 0xFFFFu));
+      atomicAdd(dhi + nr, (unsigned)(B[j] >> 16));
+    }
+  }
+}
+
+// Adds the sums of nodes [a, e] to S and clears them; every thread of the
+// block calls it, between barriers.
+__device__ void dep2_flush(uint32_t* dlo, uint32_t* dhi, int a, int e, unsigned long long* S) {
+  for (int n = a + (int)threadIdx.x; n <= e; n += (int)blockDim.x) {
+    const unsigned long long v = ((unsigned long long)dhi[n] << 16) + dlo[n];
+    if (v) {
+      atomicAdd(S + n, v);
+      dlo[n] = 0u;
+      dhi[n] = 0u;
+    }
+  }
+}
+
+__device__ __forceinline__ void deposit2_one(unsigned long long* S, int c, float f, int N, bool periodic) {
+  int n0;
+  unsigned a, b;
+  spline2_shares(f, c, &n0, &a, &b);
+  atomicAdd(S + node2(n0 - 1, N, periodic), (unsigned long long)a);
+  atomicAdd(S + n0, 4294967296ull - a - b);
+  atomicAdd(S + node2(n0 + 1, N, periodic), (unsigned long long)b);
+}
+
 __device__ __forceinline__ void deposit_one(unsigned long long* S, int c, float f) {
   const unsigned r = __float2uint_rz(f * 4294967296.0f);
   atomicAdd(S + c, 4294967296ull - (unsigned long long)r);
@@ -369,7 +457,10 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   // secondary electron: same segment and species
   const float vb = v2 * e0;
   if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1))) {
-    deposit_one(R->S + (size_t)sp * (N + 1), c, f);
+    if (R->scheme == ECPIC_SCHEME_EC2)
+      deposit2_one(R->S + (size_t)sp * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
+    else
+      deposit_one(R->S + (size_t)sp * (N + 1), c, f);
     if (sample && SP->q < 0.0 && c >= R->eedf_c0 && c <= R->eedf_c1)
       atomicAdd(R->tal + (size_t)sp * R->tal_stride +
                     tally_bin(kin_eV(SP->half_m_over_e, vb, yz2(v2 * e1, v2 * e2)), R->eedf_dEinv, R->eedf_n),
@@ -391,7 +482,10 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
     const int pspec = SP->proc[chosen].product_species;
     const float ivx = sd * z0;
     if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
-      deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
+      if (R->scheme == ECPIC_SCHEME_EC2)
+        deposit2_one(R->S + (size_t)pspec * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
+      else
+        deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
       if (sample) {
         double* md = R->momd + (size_t)pspec * 2 * (N + 1);
         atomicAdd(md + c, (double)((1.0f - f) * ivx));
@@ -522,10 +616,12 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, const Re
 // 32-byte sectors anyway) and on energy-sample steps; otherwise the test
 // reads them per candidate.
 //
-// Compiled once per SAMPLE: energy-sample steps (moments, energy, EEDF, J.E)
-// are rare, and keeping their code out of the common instance keeps the
-// common loop small in the instruction cache.
-template <bool SAMPLE>
+// Compiled three times (KIND): 0 = ordinary steps of the linear schemes (the
+// common case), 1 = their energy-sample steps (moments, energy, EEDF, J.E),
+// 2 = the EC2 scheme with the sample decision taken at run time.  Keeping the
+// rare code out of the common instance keeps its loop small in the
+// instruction cache.
+template <int KIND>
 __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
@@ -545,7 +641,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const uint64_t* pid = G.id[cur];
   const long long k = st->step;
   const bool stepping = (mode == MODE_STEP);
-  constexpr bool sample = SAMPLE;
+  const bool sample = KIND == 1 ||
+                      (KIND == 2 && stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0);
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
   const float* __restrict__ E = R->E;
@@ -555,6 +652,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const bool yz_stream = mcc && !heavy && thr24 >= (1u << 20);
   const bool load_yz = sample || yz_stream;
   const bool walls = bc != ECPIC_PERIODIC;
+  constexpr bool order2 = KIND == 2;
   const bool eedf_on = sample && SP->q < 0.0;
   const bool imp_on = stepping && walls && SP->q > 0.0 && G.imp_cap > 0;
   const int ec0 = R->eedf_c0, ec1 = R->eedf_c1;
@@ -647,6 +745,21 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           const int cc = ok ? c[j] : 0;
           if (scheme == ECPIC_SCHEME_EC) {
             Ei[j] = __ldg(E + cc);
+          } else if (order2) {
+            // linear between the faces about the nearest node n0 (faces
+            // n0-1 and n0): the derivative of the quadratic-spline potential
+            const bool up = f[j] >= 0.5f;
+            const int n0 = cc + (up ? 1 : 0);
+            const float u = up ? f[j] - 1.0f : f[j];
+            float El, Er;
+            if (walls) {
+              El = n0 >= 1 ? __ldg(E + n0 - 1) : 0.0f;
+              Er = n0 < N ? __ldg(E + n0) : 0.0f;
+            } else {
+              El = __ldg(E + (n0 >= 1 ? n0 - 1 : N - 1));
+              Er = __ldg(E + (n0 < N ? n0 : 0));
+            }
+            Ei[j] = (0.5f - u) * El + (0.5f + u) * Er;
           } else {
             const float e0 = __ldg(E + cc), e1 = __ldg(E + cc + 1);
             Ei[j] = e0 + f[j] * (e1 - e0);
@@ -794,7 +907,10 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       }
       // fixed-point CIC deposit of the new positions (Eq. 2-3); vx moments
       // (pre-collision: the collision adds the change)
-      dep_add4(dcnt, dlo, dhi, c, f);
+      if (order2)
+        dep2_add4(dlo, dhi, N, !walls, c, f);
+      else
+        dep_add4(dcnt, dlo, dhi, c, f);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (c[j] >= 0) {
@@ -881,9 +997,12 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       }
     }
     if (!more) break;
-    if (++since_flush == kFlushIters) {
+    if (++since_flush == (order2 ? kFlushIters / 4 : kFlushIters)) {
       __syncthreads();
-      dep_flush(dcnt, dlo, dhi, 0, N, Sg);
+      if (order2)
+        dep2_flush(dlo, dhi, 0, N, Sg);
+      else
+        dep_flush(dcnt, dlo, dhi, 0, N, Sg);
       __syncthreads();
       since_flush = 0;
     }
@@ -926,7 +1045,12 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   double* md = R->momd + (size_t)sp * 2 * (N + 1);
   // an empty range (no live particle in the piece) is (INT_MAX, -1): skip it
   // before forming flo + threadIdx.x, which would overflow
-  if (flo < fhi) dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
+  if (flo < fhi) {
+    if (order2)  // shares reach one node beyond the range, or wrap
+      dep2_flush(dlo, dhi, walls ? max(flo - 1, 0) : 0, walls ? min(fhi + 1, N) : N, Sg);
+    else
+      dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
+  }
   const int nbeg = flo <= fhi ? flo + (int)threadIdx.x : fhi + 1;
   if (sample) {
     double* pwg = R->pw + (size_t)sp * N;
@@ -968,14 +1092,13 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
 __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
-  uint32_t* dep = reinterpret_cast<uint32_t*>(pre + b.nseg + 1);  // 3 (nmax+1): count, lo, hi
+  // deposit sums, 3 (nmax+1): count, lo, hi (linear); -, lo, hi per node (EC2)
+  uint32_t* dep = reinterpret_cast<uint32_t*>(pre + b.nseg + 1);
   float* Msm = reinterpret_cast<float*>(dep + 3 * (b.nmax + 1));
   unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 3 * (b.nmax + 1));  // Msm: M1 | M2 | J.E
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
-    dep[i] = 0u;
-    dep[b.nmax + 1 + i] = 0u;
-    dep[2 * (b.nmax + 1) + i] = 0u;
+    for (int q = 0; q < 3; ++q) dep[q * (b.nmax + 1) + i] = 0u;
     Msm[i] = 0.0f;
     Msm[b.nmax + 1 + i] = 0.0f;
     Msm[2 * (b.nmax + 1) + i] = 0.0f;
@@ -1003,10 +1126,12 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const bool stepping = mode == MODE_STEP;
     const long long k = b.rst[G.run].step;
     const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
-    if (smp)
-      pass_piece<true>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    if (R.scheme == ECPIC_SCHEME_EC2)
+      pass_piece<2>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    else if (smp)
+      pass_piece<1>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else
-      pass_piece<false>(b, s, beg, end, mode, dep, Msm, ring, sh);
+      pass_piece<0>(b, s, beg, end, mode, dep, Msm, ring, sh);
   }
 }
 
@@ -1200,7 +1325,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
   }
   __syncthreads();
   float* E = R->E;
-  if (R->scheme == ECPIC_SCHEME_EC) {
+  if (R->scheme != ECPIC_SCHEME_MC) {  // EC and EC2: face field
     for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-C[n]);
   } else {
     const double* w = R->mcw;
@@ -1575,6 +1700,33 @@ __global__ void __launch_bounds__(kPassBlock) k_deposit_device(int N, long long 
   dep_flush(dcnt, dlo, dhi, 0, N, S);
 }
 
+// EC2 quadratic deposit of caller-owned (cell, xi) arrays straight to S
+// (tests): the pass's integer shares; periodic node N is node 0 here and is
+// mirrored after the deposit
+__global__ void k_deposit2_device(int N, int periodic, long long n, const int* cell, const float* xi,
+                                  unsigned long long* S) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = cell[i];
+    if (c < 0 || c >= N) continue;
+    int n0;
+    unsigned a, b;
+    spline2_shares(xi[i], c, &n0, &a, &b);
+    int nodes[3] = {n0 - 1, n0, n0 + 1};
+    for (int q = 0; q < 3; ++q) {
+      int m = nodes[q];
+      if (periodic) m = ((m % N) + N) % N;
+      else m = m < 0 ? 0 : (m > N ? N : m);
+      nodes[q] = m;
+    }
+    atomicAdd(S + nodes[0], (unsigned long long)a);
+    atomicAdd(S + nodes[1], 4294967296ull - a - b);
+    atomicAdd(S + nodes[2], (unsigned long long)b);
+  }
+}
+
+__global__ void k_mirror_node(int N, unsigned long long* S) { S[N] = S[0]; }
+
 __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t* key,
                                 uint32_t* out) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -1671,6 +1823,15 @@ void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
   const size_t sm = 3 * sizeof(uint32_t) * (size_t)(N + 1);
   set_smem_attr((const void*)k_deposit_device, sm);
   k_deposit_device<<<(unsigned)blocks, kPassBlock, sm, s>>>(N, n, cell, xi, S);
+}
+
+void launch_deposit2_device(int N, int periodic, long long n, const int* cell, const float* xi,
+                            unsigned long long* S, cudaStream_t s) {
+  long long blocks = (n + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1216) blocks = 1216;
+  k_deposit2_device<<<(unsigned)blocks, 256, 0, s>>>(N, periodic, n, cell, xi, S);
+  if (periodic) k_mirror_node<<<1, 1, 0, s>>>(N, S);
 }
 
 void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,

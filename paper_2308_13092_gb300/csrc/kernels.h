@@ -41,6 +41,8 @@ void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t
 
 void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
                            unsigned long long* S, cudaStream_t s);
+void launch_deposit2_device(int N, int periodic, long long n, const int* cell, const float* xi,
+                            unsigned long long* S, cudaStream_t s);
 void read_checks(unsigned long long out[4]);
 void launch_philox_device(long long n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s);

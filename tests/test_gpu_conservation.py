@@ -5,7 +5,7 @@ periodic Maxwellians (uniform neutralising background):
   the transpose of the CIC deposit), to FP32 rounding; EC does not.
 * The EC total energy error falls about 4x when dt halves (0.2 -> 0.1/w_pe),
   as the oracle's does (second order), and stays close to the oracle's value
-  on the same seed.
+  on the same seed; likewise for the higher-order EC2 scheme.
 * At dx = 8 lambda_De the MC scheme heats while EC does not (App. B)."""
 import numpy as np
 import pytest
@@ -85,6 +85,18 @@ def test_ec_energy_second_order_in_dt():
         assert b < 1e-4, (seed, a, b)
         # same seed, same initial state: the oracle's error is of the same size
         ob = _oracle_energy_error(I.EC, 0.1, 50.0, seed)
+        assert 0.5 * ob <= b <= 2.0 * ob, (seed, b, ob)
+    assert np.mean(ratios) >= 3.0, ratios
+
+
+def test_ec2_energy_second_order_in_dt():
+    ratios = []
+    for seed in (5, 6):
+        a = _gpu_energy_error(I.EC2, 0.2, 50.0, seed)
+        b = _gpu_energy_error(I.EC2, 0.1, 50.0, seed)
+        ratios.append(a / b)
+        assert b < 1e-4, (seed, a, b)
+        ob = _oracle_energy_error(I.EC2, 0.1, 50.0, seed)
         assert 0.5 * ob <= b <= 2.0 * ob, (seed, b, ob)
     assert np.mean(ratios) >= 3.0, ratios
 

@@ -90,6 +90,30 @@ def test_deposit_device_many_flushes(E, N, order):
     assert int(got.sum(dtype=np.uint64)) == n * 2 ** 32
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("N,n,order", [(8, 3000, "random"), (256, 200001, "sorted"),
+                                       (1024, 500003, "random")])
+def test_deposit2_device_bit_exact(E, bc, N, n, order):
+    # EC2 quadratic-spline shares: the same integers as the oracle routine,
+    # folds at Dirichlet walls and periodic wrap included
+    rng = np.random.default_rng(N + n + bc)
+    cell = rng.integers(0, N, n).astype(np.int32)
+    if order == "sorted":
+        cell.sort()
+    xi = rng.random(n).astype(np.float32)
+    edge = np.array([0.0, 0.5, np.nextafter(np.float32(0.5), np.float32(0)), 1 - 2.0 ** -24,
+                     2.0 ** -30, 0.25], np.float32)
+    xi[:edge.size] = edge
+    cell[:edge.size] = [0, N - 1, 0, N - 1, N // 2, 0]
+    S = torch.zeros(N + 1, dtype=torch.int64, device="cuda")
+    dc, dx = _dev(cell), _dev(xi)
+    E.ecpic_deposit_device2(N, bc, n, dc.data_ptr(), dx.data_ptr(), S.data_ptr())
+    torch.cuda.synchronize()
+    got = S.cpu().numpy().view(np.uint64)
+    want = oracle.deposit_fixed2(N, bc, cell, xi)
+    assert np.array_equal(got, want)
+
+
 def test_deposit_device_skips_dead_and_empty(E):
     rng = np.random.default_rng(1)
     N, n = 100, 5000
