@@ -7,5 +7,5 @@ from .oracle import (  # noqa: F401
     OracleRun, build, lib, philox4x32_10, child_id, deposit_fixed, deposit_fixed2,
     poisson_thomas, poisson_dense, field, doubling_grid,
     ELASTIC, EXCITATION, IONIZATION, ION_ELASTIC, CX,
-    DIRICHLET, PERIODIC, EC, MC, EC2,
+    DIRICHLET, PERIODIC, EC, MC, EC2, MC2,
 )

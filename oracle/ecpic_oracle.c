@@ -438,9 +438,9 @@ static int or_uniform(const or_run* r) {
 }
 
 int oracle_set_scheme(or_run* r, int scheme) {
-  if (!r || (scheme != OR_SCHEME_EC && scheme != OR_SCHEME_MC && scheme != OR_SCHEME_EC2)) return -1;
+  if (!r || scheme < OR_SCHEME_EC || scheme > OR_SCHEME_MC2) return -1;
   /* the quadratic deposit is written for uniform cells */
-  if (scheme == OR_SCHEME_EC2 && r->grid_set && !or_uniform(r)) return -1;
+  if (scheme >= OR_SCHEME_EC2 && r->grid_set && !or_uniform(r)) return -1;
   r->scheme = scheme;
   return 0;
 }
@@ -614,7 +614,7 @@ static void or_deposit(or_run* r) {
       int j = or_locate(r, s->X[i]);
       double xi = (s->X[i] - r->x[j]) / r->dx[j];
       double v = s->vx[i];
-      if (r->scheme == OR_SCHEME_EC2) {
+      if (r->scheme >= OR_SCHEME_EC2) {
         /* quadratic B-spline charge shares about the nearest node n0 */
         int n0 = xi < 0.5 ? j : j + 1;
         double u = xi < 0.5 ? xi : xi - 1.0;
@@ -632,7 +632,7 @@ static void or_deposit(or_run* r) {
       s->M2[j + 1] += xi * v * v;
     }
     if (r->bc == OR_PERIODIC) {
-      if (r->scheme != OR_SCHEME_EC2) s->D[0] += s->D[N];
+      if (r->scheme < OR_SCHEME_EC2) s->D[0] += s->D[N];
       s->D[N] = s->D[0];
       s->M1[0] += s->M1[N]; s->M1[N] = s->M1[0];
       s->M2[0] += s->M2[N]; s->M2[N] = s->M2[0];
@@ -666,7 +666,8 @@ static int or_solve(or_run* r, int64_t k) {
   int rc = oracle_poisson_thomas(N, r->x, Qs, phi0, phiN, r->phi);
   free(Qs);
   if (rc) return rc;
-  return oracle_field(N, r->x, r->phi, r->bc, r->scheme == OR_SCHEME_MC ? OR_SCHEME_MC : OR_SCHEME_EC,
+  return oracle_field(N, r->x, r->phi, r->bc,
+                      (r->scheme == OR_SCHEME_MC || r->scheme == OR_SCHEME_MC2) ? OR_SCHEME_MC : OR_SCHEME_EC,
                       r->E);
 }
 
@@ -733,7 +734,7 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
   for (int si = 0; si < r->ns; ++si)
     if (n_per_species[si] < 0 || n_per_species[si] > r->sp[si].cap || T_eV[si] < 0)
       return -1;
-  if (r->scheme == OR_SCHEME_EC2 && !or_uniform(r)) return -1;
+  if (r->scheme >= OR_SCHEME_EC2 && !or_uniform(r)) return -1;
   r->seed = seed;
   r->dt = dt;
   r->step = 0;
@@ -1025,6 +1026,19 @@ static double or_gather2(const or_run* r, int j, double xi) {
   return (0.5 - u) * El + (0.5 + u) * Er;
 }
 
+/* MC2 gather: the quadratic-spline weights of the deposit applied to the
+ * centred node field (the transpose of the deposit: shares folded into a
+ * wall node read that node's field, periodic nodes wrap). */
+static double or_gather2_mc(const or_run* r, int j, double xi) {
+  int N = r->N;
+  int n0 = xi < 0.5 ? j : j + 1;
+  double u = xi < 0.5 ? xi : xi - 1.0;
+  double w[3] = {0.5 * (0.5 - u) * (0.5 - u), 0.75 - u * u, 0.5 * (0.5 + u) * (0.5 + u)};
+  double e = 0.0;
+  for (int q = 0; q < 3; ++q) e += w[q] * r->E[or_node2(n0 - 1 + q, N, r->bc)];
+  return e;
+}
+
 static int or_step_once(or_run* r) {
   int64_t k = r->step;
   int N = r->N;
@@ -1049,6 +1063,7 @@ static int or_step_once(or_run* r) {
       double xi = (X - r->x[j]) / r->dx[j];
       double Ei = (r->scheme == OR_SCHEME_EC) ? r->E[j]
                 : (r->scheme == OR_SCHEME_EC2) ? or_gather2(r, j, xi)
+                : (r->scheme == OR_SCHEME_MC2) ? or_gather2_mc(r, j, xi)
                                                : (1.0 - xi) * r->E[j] + xi * r->E[j + 1];
       double vold = s->vx[i];
       double vnew = vold + qm * Ei * r->dt;
@@ -1181,7 +1196,7 @@ int oracle_get_fields(const or_run* r, double* phi, double* E, double* Q) {
   if (!r || !r->grid_set) return -1;
   int N = r->N;
   if (phi) memcpy(phi, r->phi, sizeof(double) * (size_t)(N + 1));
-  if (E) memcpy(E, r->E, sizeof(double) * (size_t)(r->scheme == OR_SCHEME_MC ? N + 1 : N));
+  if (E) memcpy(E, r->E, sizeof(double) * (size_t)((r->scheme == OR_SCHEME_MC || r->scheme == OR_SCHEME_MC2) ? N + 1 : N));
   if (Q) memcpy(Q, r->Q, sizeof(double) * (size_t)(N + 1));
   return 0;
 }

@@ -40,6 +40,7 @@ extern "C" {
 #define OR_SCHEME_EC 0
 #define OR_SCHEME_MC 1
 #define OR_SCHEME_EC2 2 /* quadratic-spline deposit, linear gather of the face field */
+#define OR_SCHEME_MC2 3 /* quadratic-spline deposit and gather of the centred node field */
 
 typedef struct or_run or_run;
 

@@ -20,7 +20,7 @@ _SO = os.path.join(_HERE, "libecpic_oracle.so")
 
 ELASTIC, EXCITATION, IONIZATION, ION_ELASTIC, CX = 0, 1, 2, 3, 4
 DIRICHLET, PERIODIC = 0, 1
-EC, MC, EC2 = 0, 1, 2  # EC2: quadratic-spline deposit, linear gather of the face field
+EC, MC, EC2, MC2 = 0, 1, 2, 3  # EC2 / MC2: quadratic-spline deposit, linear face / quadratic node gather
 MAX_SPECIES, MAX_PROC = 4, 8
 
 _lock = threading.Lock()
@@ -310,7 +310,7 @@ class OracleRun:
     def fields(self):
         N = self.N
         phi = np.zeros(N + 1)
-        E = np.zeros(N + 1 if self.scheme == MC else N)
+        E = np.zeros(N + 1 if self.scheme in (MC, MC2) else N)
         Q = np.zeros(N + 1)
         _chk(self._L.oracle_get_fields(self.h, _ptr(phi), _ptr(E), _ptr(Q)),
              "oracle_get_fields")

@@ -33,7 +33,7 @@ TORR = 133.322368421
 
 ELASTIC, EXCITATION, IONIZATION, ION_ELASTIC, CX = 0, 1, 2, 3, 4
 DIRICHLET, PERIODIC = 0, 1
-EC, MC, EC2 = 0, 1, 2  # EC2: quadratic-spline deposit, linear gather of the face field
+EC, MC, EC2, MC2 = 0, 1, 2, 3  # EC2 / MC2: quadratic-spline deposit, linear face / quadratic node gather
 
 F_RF = 13.56e6
 L_GAP = 0.3

@@ -1,6 +1,8 @@
-"""Pins for the oracle's higher-order EC scheme (EC2: quadratic-spline charge
-deposit, field interpolated one order lower, i.e. linearly between faces; the
-EC construction of Sec. 2a carried one order up, uniform grids):
+"""Pins for the oracle's higher-order schemes on uniform grids: EC2 (quadratic-
+spline charge deposit, field interpolated one order lower, i.e. linearly
+between faces: the EC construction of Sec. 2a carried one order up) and its
+momentum-conserving partner MC2 (the same deposit and a quadratic-spline
+gather of the centred node field):
 
 * fixed-point quadratic shares: exact integers within one 2^-32 quantum of
   the B-spline weights, exactly 2^32 per particle (charge conserved also at
@@ -10,7 +12,10 @@ EC construction of Sec. 2a carried one order up, uniform grids):
   Phi(X) = sum_n phi_n S2(X/dx - n) (ghost node beyond a wall = wall node):
   the EC property that makes the scheme energy conserving;
 * energy error second order in dt on a periodic Maxwellian, no grid heating at
-  dx = 8 lambda_De where MC heats (App. B, quiet start)."""
+  dx = 8 lambda_De where MC heats (App. B, quiet start);
+* MC2 conserves total momentum on a uniform periodic grid to round-off (its
+  gather is the transpose of the deposit, folds included), EC2 does not; MC2
+  heats at dx = 8 lambda_De, less than MC, while EC2 does not."""
 import numpy as np
 import pytest
 
@@ -153,3 +158,28 @@ def test_ec2_does_not_heat_where_mc_does():
     mc = _energy_error(oracle.MC, 0.1, 250.0, 1, dx_lambda=8.0, ppc=64, N=128, quiet=True)
     assert ec2 < 2e-3, ec2
     assert mc > 0.1 and mc > 50 * ec2, (mc, ec2)
+
+
+def test_mc2_conserves_momentum_ec2_does_not():
+    masses = [I.ME, I.M_ION]
+    drift = {}
+    for scheme in (oracle.MC2, oracle.EC2):
+        cfg = I.periodic_plasma(N=32, dx_lambda=3.0, ppc=64, dt_wpe=0.2, seed=4, scheme=scheme,
+                                ions=True)
+        o = oracle_from_config(cfg)
+        v0 = [o.get_particles(k)["vx"] for k in range(2)]
+        p0 = sum(m * v.sum() for m, v in zip(masses, v0))
+        scale = sum(m * np.abs(v).sum() for m, v in zip(masses, v0))
+        o.step(60)
+        p1 = sum(m * o.get_particles(k)["vx"].sum() for k, m in enumerate(masses))
+        drift[scheme] = abs(p1 - p0) / scale
+    assert drift[oracle.MC2] <= 1e-11, drift
+    assert drift[oracle.EC2] > 1e-6, drift
+
+
+def test_mc2_heats_less_than_mc_ec2_not_at_all():
+    mc = _energy_error(oracle.MC, 0.1, 250.0, 1, dx_lambda=8.0, ppc=64, N=128, quiet=True)
+    mc2 = _energy_error(oracle.MC2, 0.1, 250.0, 1, dx_lambda=8.0, ppc=64, N=128, quiet=True)
+    ec2 = _energy_error(oracle.EC2, 0.1, 250.0, 1, dx_lambda=8.0, ppc=64, N=128, quiet=True)
+    assert mc > mc2 > 100 * ec2, (mc, mc2, ec2)
+    assert mc2 > 5e-3, mc2
