@@ -62,6 +62,9 @@ typedef enum {
  * charge deposit): quadratic-spline deposit, linear interpolation of the face
  * field; uniform grids; the ghost node beyond a wall is the wall node */
 #define ECPIC_SCHEME_EC2 2
+/* its momentum-conserving partner: the same quadratic deposit and a
+ * quadratic-spline gather of the centred node field (uniform grids) */
+#define ECPIC_SCHEME_MC2 3
 /* collision processes (Sec. 2b) */
 #define ECPIC_ELASTIC 0     /* electron-neutral elastic, neutral at rest */
 #define ECPIC_EXCITATION 1  /* electron-impact excitation */

@@ -143,7 +143,7 @@ int ecpic_set_grid(ecpic_run* r, const double* edges, int n_edges, int bc, doubl
 
 int ecpic_set_scheme(ecpic_run* r, int scheme) {
   if (!r) return ECPIC_ERR_ARG;
-  if (scheme != ECPIC_SCHEME_EC && scheme != ECPIC_SCHEME_MC && scheme != ECPIC_SCHEME_EC2)
+  if (scheme < ECPIC_SCHEME_EC || scheme > ECPIC_SCHEME_MC2)
     return fail(r, ECPIC_ERR_ARG, "unknown scheme");
   if (r->batch) return fail(r, ECPIC_ERR_STATE, "scheme is fixed after init");
   r->spec.scheme = scheme;

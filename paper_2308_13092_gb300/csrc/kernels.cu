@@ -457,7 +457,7 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   // secondary electron: same segment and species
   const float vb = v2 * e0;
   if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1))) {
-    if (R->scheme == ECPIC_SCHEME_EC2)
+    if (R->scheme >= ECPIC_SCHEME_EC2)
       deposit2_one(R->S + (size_t)sp * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
     else
       deposit_one(R->S + (size_t)sp * (N + 1), c, f);
@@ -482,7 +482,7 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
     const int pspec = SP->proc[chosen].product_species;
     const float ivx = sd * z0;
     if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
-      if (R->scheme == ECPIC_SCHEME_EC2)
+      if (R->scheme >= ECPIC_SCHEME_EC2)
         deposit2_one(R->S + (size_t)pspec * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
       else
         deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
@@ -745,6 +745,15 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           const int cc = ok ? c[j] : 0;
           if (scheme == ECPIC_SCHEME_EC) {
             Ei[j] = __ldg(E + cc);
+          } else if (order2 && scheme == ECPIC_SCHEME_MC2) {
+            // the deposit's quadratic weights on the centred node field (its
+            // transpose: folded and wrapped nodes read their field)
+            const bool up = f[j] >= 0.5f;
+            const int n0 = cc + (up ? 1 : 0);
+            const float u = up ? f[j] - 1.0f : f[j];
+            const float wl = 0.5f * (0.5f - u) * (0.5f - u), wr = 0.5f * (0.5f + u) * (0.5f + u);
+            Ei[j] = wl * __ldg(E + node2(n0 - 1, N, !walls)) + (0.75f - u * u) * __ldg(E + n0) +
+                    wr * __ldg(E + node2(n0 + 1, N, !walls));
           } else if (order2) {
             // linear between the faces about the nearest node n0 (faces
             // n0-1 and n0): the derivative of the quadratic-spline potential
@@ -1126,7 +1135,7 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const bool stepping = mode == MODE_STEP;
     const long long k = b.rst[G.run].step;
     const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
-    if (R.scheme == ECPIC_SCHEME_EC2)
+    if (R.scheme >= ECPIC_SCHEME_EC2)  // EC2, MC2
       pass_piece<2>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else if (smp)
       pass_piece<1>(b, s, beg, end, mode, dep, Msm, ring, sh);
@@ -1325,7 +1334,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
   }
   __syncthreads();
   float* E = R->E;
-  if (R->scheme != ECPIC_SCHEME_MC) {  // EC and EC2: face field
+  if (R->scheme == ECPIC_SCHEME_EC || R->scheme == ECPIC_SCHEME_EC2) {  // face field
     for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-C[n]);
   } else {
     const double* w = R->mcw;

@@ -130,13 +130,12 @@ std::string validate_spec(const RunSpec& s) {
   }
   std::string e = validate_grid(s.edges, s.bc);
   if (!e.empty()) return e;
-  if (s.scheme != ECPIC_SCHEME_EC && s.scheme != ECPIC_SCHEME_MC && s.scheme != ECPIC_SCHEME_EC2)
-    return "unknown scheme";
-  if (s.scheme == ECPIC_SCHEME_EC2) {
+  if (s.scheme < ECPIC_SCHEME_EC || s.scheme > ECPIC_SCHEME_MC2) return "unknown scheme";
+  if (s.scheme >= ECPIC_SCHEME_EC2) {
     const double dx0 = s.edges[1] - s.edges[0];
     for (size_t j = 1; j + 1 < s.edges.size(); ++j)
       if (std::fabs((s.edges[j + 1] - s.edges[j]) - dx0) > 1e-9 * dx0)
-        return "the EC2 scheme needs a uniform grid";
+        return "the EC2 and MC2 schemes need a uniform grid";
   }
   if (s.species.empty() || s.species.size() > (size_t)kMaxSpecies) return "1..4 species required";
   if (!(s.dt > 0) || !std::isfinite(s.dt)) return "dt must be positive";
@@ -955,7 +954,7 @@ int Batch::get_fields(int slot, double* phi, float* E, std::string* err) {
     cudaMemcpy(phi, R.phi, 8 * (size_t)(R.N + 1), cudaMemcpyDeviceToHost);
   }
   if (E)
-    cudaMemcpy(E, R.E, 4 * (size_t)(R.scheme == ECPIC_SCHEME_MC ? R.N + 1 : R.N),
+    cudaMemcpy(E, R.E, 4 * (size_t)((R.scheme == ECPIC_SCHEME_MC || R.scheme == ECPIC_SCHEME_MC2) ? R.N + 1 : R.N),
                cudaMemcpyDeviceToHost);
   return check(cudaGetLastError(), "get_fields", err);
 }

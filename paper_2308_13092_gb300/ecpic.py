@@ -22,7 +22,7 @@ ECPIC_ERR_ARG, ECPIC_ERR_STATE, ECPIC_ERR_NOMEM = -1, -2, -3
 ECPIC_ERR_CAPACITY, ECPIC_ERR_CUDA, ECPIC_ERR_TIMEOUT, ECPIC_ERR_NAN = -4, -5, -6, -7
 ECPIC_MAX_SPECIES, ECPIC_MAX_PROC, ECPIC_MAX_CELLS = 4, 8, 2048
 ECPIC_DIRICHLET_RF, ECPIC_PERIODIC = 0, 1
-ECPIC_SCHEME_EC, ECPIC_SCHEME_MC, ECPIC_SCHEME_EC2 = 0, 1, 2
+ECPIC_SCHEME_EC, ECPIC_SCHEME_MC, ECPIC_SCHEME_EC2, ECPIC_SCHEME_MC2 = 0, 1, 2, 3
 ECPIC_ELASTIC, ECPIC_EXCITATION, ECPIC_IONIZATION, ECPIC_ION_ELASTIC, ECPIC_CX = 0, 1, 2, 3, 4
 
 _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_STATE", -3: "ERR_NOMEM", -4: "ERR_CAPACITY",
@@ -354,7 +354,8 @@ class Run:
 
     def fields(self):
         phi = np.zeros(self.N + 1)
-        E = np.zeros(self.N + 1 if self.scheme == ECPIC_SCHEME_MC else self.N, np.float32)
+        E = np.zeros(self.N + 1 if self.scheme in (ECPIC_SCHEME_MC, ECPIC_SCHEME_MC2) else self.N,
+                     np.float32)
         _chk(self.h, self._L.ecpic_get_fields(self.h, _p(phi), _p(E)), "ecpic_get_fields")
         return dict(phi=phi, E=E)
 

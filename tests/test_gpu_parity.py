@@ -3,7 +3,7 @@
 * loader: cell indices bit-exact, xi and velocities within FP32 rounding of
   the oracle's FP64 values;
 * field of a given state: E and phi within 1e-5 of the field scale;
-* one step from an identical state (EC, MC and EC2, uniform and non-uniform,
+* one step from an identical state (EC, MC, EC2 and MC2, uniform and non-uniform,
   Dirichlet-RF and periodic, with and without collisions): cells bit-exact
   except particles within 4 FP32 ulps of a face; positions and velocities to
   relative 1e-5; collision candidates exactly equal (integer decision on the
@@ -132,7 +132,7 @@ def test_loader_parity():
 
 @pytest.mark.parametrize("scheme,grid", [(I.EC, "uniform"), (I.EC, "doubling"), (I.EC, "tanh"),
                                          (I.MC, "uniform"), (I.MC, "doubling"), (I.MC, "tanh"),
-                                         (I.EC2, "uniform")])
+                                         (I.EC2, "uniform"), (I.MC2, "uniform")])
 def test_field_parity(scheme, grid):
     edges = {"uniform": None, "doubling": oracle.doubling_grid(128, 0.05, 0.01, 1, 8),
              "tanh": I.tanh_edges(70, 0.05, 0.05 / 400)}[grid]
@@ -155,6 +155,7 @@ CASES = [
     ("EC", "tanh", "dirichlet", True),
     ("EC2", "uniform", "dirichlet", False), ("EC2", "uniform", "periodic", False),
     ("EC2", "uniform", "dirichlet", True),
+    ("MC2", "uniform", "dirichlet", False), ("MC2", "uniform", "periodic", False),
 ]
 
 
@@ -162,7 +163,7 @@ CASES = [
 def test_one_step_parity(scheme, grid, bc, coll):
     edges = {"uniform": None, "doubling": oracle.doubling_grid(128, 0.05, 0.01, 1, 8),
              "tanh": I.tanh_edges(70, 0.05, 0.05 / 400)}[grid]
-    cfg = _small(scheme={"EC": I.EC, "MC": I.MC, "EC2": I.EC2}[scheme], edges=edges, collisions=coll,
+    cfg = _small(scheme={"EC": I.EC, "MC": I.MC, "EC2": I.EC2, "MC2": I.MC2}[scheme], edges=edges, collisions=coll,
                  bc={"dirichlet": I.DIRICHLET, "periodic": I.PERIODIC}[bc], n=6000)
     g, o = _pair(cfg)
     before = _set_same_state(cfg, g, o)
