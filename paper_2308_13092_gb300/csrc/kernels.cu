@@ -645,7 +645,14 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
                       (KIND == 2 && stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0);
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
-  const float* __restrict__ E = R->E;
+  // the run's field staged in shared memory for the gather (after the rings)
+  float* Esm = reinterpret_cast<float*>(ring + sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32));
+  {
+    const int ne = (scheme == ECPIC_SCHEME_MC || scheme == ECPIC_SCHEME_MC2) ? N + 1 : N;
+    for (int q = threadIdx.x; q < ne; q += kPassBlock) Esm[q] = R->E[q];
+    __syncthreads();
+  }
+  const float* E = Esm;
   const uint32_t thr24 = SP->thr24;
   const bool mcc = stepping && SP->nproc > 0 && thr24 > 0;
   const bool heavy = SP->heavy != 0;
@@ -744,7 +751,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           if (!ok) c[j] = -1;
           const int cc = ok ? c[j] : 0;
           if (scheme == ECPIC_SCHEME_EC) {
-            Ei[j] = __ldg(E + cc);
+            Ei[j] = E[cc];
           } else if (order2 && scheme == ECPIC_SCHEME_MC2) {
             // the deposit's quadratic weights on the centred node field (its
             // transpose: folded and wrapped nodes read their field)
@@ -752,8 +759,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
             const int n0 = cc + (up ? 1 : 0);
             const float u = up ? f[j] - 1.0f : f[j];
             const float wl = 0.5f * (0.5f - u) * (0.5f - u), wr = 0.5f * (0.5f + u) * (0.5f + u);
-            Ei[j] = wl * __ldg(E + node2(n0 - 1, N, !walls)) + (0.75f - u * u) * __ldg(E + n0) +
-                    wr * __ldg(E + node2(n0 + 1, N, !walls));
+            Ei[j] = wl * E[node2(n0 - 1, N, !walls)] + (0.75f - u * u) * E[n0] +
+                    wr * E[node2(n0 + 1, N, !walls)];
           } else if (order2) {
             // linear between the faces about the nearest node n0 (faces
             // n0-1 and n0): the derivative of the quadratic-spline potential
@@ -762,15 +769,15 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
             const float u = up ? f[j] - 1.0f : f[j];
             float El, Er;
             if (walls) {
-              El = n0 >= 1 ? __ldg(E + n0 - 1) : 0.0f;
-              Er = n0 < N ? __ldg(E + n0) : 0.0f;
+              El = n0 >= 1 ? E[n0 - 1] : 0.0f;
+              Er = n0 < N ? E[n0] : 0.0f;
             } else {
-              El = __ldg(E + (n0 >= 1 ? n0 - 1 : N - 1));
-              Er = __ldg(E + (n0 < N ? n0 : 0));
+              El = E[n0 >= 1 ? n0 - 1 : N - 1];
+              Er = E[n0 < N ? n0 : 0];
             }
             Ei[j] = (0.5f - u) * El + (0.5f + u) * Er;
           } else {
-            const float e0 = __ldg(E + cc), e1 = __ldg(E + cc + 1);
+            const float e0 = E[cc], e1 = E[cc + 1];
             Ei[j] = e0 + f[j] * (e1 - e0);
           }
         }
@@ -1755,7 +1762,7 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
          3 * sizeof(uint32_t) * (size_t)(b.nmax + 1) + sizeof(float) * 3 * (size_t)(b.nmax + 1) +
-         sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32);
+         sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32) + sizeof(float) * (size_t)(b.nmax + 1);
 }
 
 size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }

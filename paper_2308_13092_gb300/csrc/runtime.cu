@@ -629,7 +629,7 @@ int Batch::ensure_graphs(std::string* err) {
     const int steps = which == 0 ? sort_every_ : 1;
     for (int t = 0; t < steps; ++t) {
       launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
-      launch_collide(b, pass_grid_, stream_);
+      launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
       launch_field(b, 1, -1, stream_);
     }
     if (which == 0) launch_sort(b, pass_grid_, stream_);
@@ -666,7 +666,7 @@ int Batch::step(long long n, std::string* err) {
       if (rc) return rc;
     } else {
       launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
-      launch_collide(b, pass_grid_, stream_);
+      launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
       launch_field(b, 1, -1, stream_);
     }
     --n;
@@ -695,7 +695,7 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
     launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
     cudaEventRecord(ev[1], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[1]), "pass kernel", err))) break;
-    launch_collide(b, pass_grid_, stream_);
+    launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
     cudaEventRecord(ev[4], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[4]), "collision kernel", err))) break;
     launch_field(b, 1, -1, stream_);
