@@ -1218,41 +1218,67 @@ __device__ __forceinline__ double recip(double D) {
 // fix g_0 = (phi_N - phi_0 + sum_n dx_n C_n / eps0) / L.  This is the exact
 // solution of the same tridiagonal system that a Thomas sweep solves.  The
 // prefix sums of the fixed-point deposit are taken in 64-bit integers (exact),
-// so FP64 enters only once per node and species.  EC field E_j = -g_j (Eq. 5).
-// One CTA per run; the potential and the field energy are formed only on the
-// steps that sample them (and on refresh).
-__global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance, int only) {
+// so FP64 enters only once per node.  EC field E_j = -g_j (Eq. 5).
+// One CTA per run; each thread owns a run of consecutive nodes and all
+// species are scanned together, so that a step costs a few barriers and
+// global round trips (FP64 is slow on this part: the node loop keeps its
+// FP64 operations few).  The potential and the field energy are formed only
+// on the steps that sample them (and on refresh).
+__global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advance, int only) {
   const int slot = blockIdx.x;
   if (slot >= b.max_slots) return;
   const RunDev* R = b.runs + slot;
-  if (!R->active) return;
   RunState* st = b.rst + slot;
+  // every scalar this kernel needs, loaded before the first branch so that
+  // the loads travel together
+  const int active = R->active;
+  const int status0 = st->status;
+  const long long step0 = st->step, step_end = st->step_end;
+  const int N = R->N, ns = R->ns, seg0 = R->seg0;
+  const int se = R->sample_every;
+  const bool periodic = (R->bc == ECPIC_PERIODIC);
+  const bool face = R->scheme == ECPIC_SCHEME_EC || R->scheme == ECPIC_SCHEME_EC2;
+  const double* dx = R->dx;
+  unsigned long long* Sall = R->S;
+  const double inv_L = R->inv_L;
+  double qw[kMaxSpecies];
+#pragma unroll
+  for (int s = 0; s < kMaxSpecies; ++s) qw[s] = R->sp[s].q * R->sp[s].w;
+  if (!active) return;
   if (advance) {
-    if (st->status != 0 || st->step >= st->step_end) return;
+    if (status0 != 0 || step0 >= step_end) return;
   } else if (only >= 0 && slot != only) {
     return;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* C = reinterpret_cast<double*>(smem_raw);                        // N+1
-  unsigned long long* P = reinterpret_cast<unsigned long long*>(C + b.nmax + 1);  // N+1
+  double* C = reinterpret_cast<double*>(smem_raw);  // N+1
   __shared__ double dsm[32];
-  __shared__ unsigned long long usm[32];
+  __shared__ unsigned long long wtot[kFieldBlock / 32][kMaxSpecies];
   __shared__ double phi0_sh;
-  const int N = R->N, ns = R->ns;
-  const int tid = threadIdx.x;
-  const long long kn = advance ? st->step + 1 : st->step;
-  const int se = R->sample_every;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long long kn = advance ? step0 + 1 : step0;
   const bool sample = advance && se > 0 && (kn % se) == 0;
   // the push of level kn samples the energy when (kn + 1) % se == 0
   const bool want_fe = !advance || (se > 0 && ((kn + 1) % se) == 0);
   const bool want_phi = !advance || sample;
-  const bool periodic = (R->bc == ECPIC_PERIODIC);
-  const double* dx = R->dx;
   constexpr double kInvEps0 = 1.0 / kEps0;
   constexpr double kInvQe = 1.0 / 1.602176634e-19;
   constexpr double k2m32 = 2.3283064365386963e-10;  // 2^-32
+  double cw[kMaxSpecies];
+#pragma unroll
+  for (int s = 0; s < kMaxSpecies; ++s) cw[s] = s < ns ? qw[s] * k2m32 : 0.0;
+  // this thread's segment (species tid), for the size update at the end;
+  // nothing changes the sizes while this kernel runs
+  SegState* my_ss = nullptr;
+  long long my_cap = 0, my_alloc = 0;
+  if (advance && tid < ns) {
+    const int sg = seg0 + tid;
+    my_ss = b.sst + sg;
+    my_cap = b.segs[sg].cap;
+    my_alloc = my_ss->n_alloc;
+  }
 
-  if (tid == 0) {
+  if (tid == kFieldBlock - 1) {
     double p0 = 0.0;
     if (!periodic) {
       const double t = (double)kn * R->dt;
@@ -1267,7 +1293,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
     double* acc = R->acc;
     for (int n = tid; n <= N; n += kFieldBlock) {
       for (int s = 0; s < ns; ++s) {
-        const unsigned long long* S = R->S + (size_t)s * (N + 1);
+        const unsigned long long* S = Sall + (size_t)s * (N + 1);
         const double* md = R->momd + (size_t)s * 2 * (N + 1);
         double D, M1, M2;
         if (periodic && (n == 0 || n == N)) {
@@ -1302,55 +1328,114 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
       }
   }
 
-  // C_n = sum_s q_s w_s 2^-32 * sum_{m=1..n} S_s,m, the integer prefix exact
-  for (int n = tid; n <= N; n += kFieldBlock) C[n] = 0.0;
-  double qtot = 0.0;
-  for (int s = 0; s < ns; ++s) {
-    unsigned long long* S = R->S + (size_t)s * (N + 1);
-    for (int n = tid; n <= N; n += kFieldBlock) {
-      P[n] = (n == 0) ? 0ull : S[n];
-      if (n == 0) usm[31] = S[0];  // node 0 only enters the total
-      S[n] = 0ull;
+  // C_n = sum_s q_s w_s 2^-32 * sum_{m=1..n} S_s,m, the integer prefix exact:
+  // thread t owns nodes [beg, end); one block scan for all species
+  const int per = (N + 1 + kFieldBlock - 1) / kFieldBlock;
+  const int beg = min(N + 1, tid * per), end = min(N + 1, beg + per);
+  unsigned long long run[kMaxSpecies], s0[kMaxSpecies];
+#pragma unroll
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    run[s] = 0ull;
+    s0[s] = 0ull;
+    if (s < ns) {
+      const unsigned long long* S = Sall + (size_t)s * (N + 1);
+      unsigned long long loc = 0ull;
+      for (int n = max(beg, 1); n < end; ++n) loc += S[n];
+      s0[s] = S[0];  // node 0 only enters the total
+      const unsigned long long inc = warp_incl_scan(loc);
+      if (lane == 31) wtot[w][s] = inc;
+      run[s] = inc - loc;
     }
-    __syncthreads();
-    const unsigned long long s0 = usm[31];
-    block_incl_scan_array(P, N + 1, usm);
-    const double cw = R->sp[s].q * R->sp[s].w * k2m32;
-    for (int n = tid; n < N; n += kFieldBlock) C[n] += cw * (double)P[n];
-    qtot += cw * (double)(P[N] + s0);
-    __syncthreads();
-  }
-  if (periodic) {
-    // uniform neutralising background: Q_n -= V_n Qtot / L
-    const double a = qtot * R->inv_L;
-    for (int n = tid; n < N; n += kFieldBlock) C[n] -= a * R->cumV[n];
-    __syncthreads();
-  }
-  const double phi0 = phi0_sh;
-  double loc = 0.0;
-  for (int n = tid; n < N; n += kFieldBlock) loc += dx[n] * C[n];
-  const double A = block_sum(loc, dsm);
-  const double g0 = (A * kInvEps0 - phi0) * R->inv_L;
-  double fe = 0.0;
-  double* gst = R->g;
-  for (int n = tid; n < N; n += kFieldBlock) {
-    const double gn = g0 - C[n] * kInvEps0;
-    C[n] = gn;
-    gst[n] = gn;
-    if (want_fe) fe += gn * gn * dx[n];
   }
   __syncthreads();
-  float* E = R->E;
-  if (R->scheme == ECPIC_SCHEME_EC || R->scheme == ECPIC_SCHEME_EC2) {  // face field
-    for (int n = tid; n < N; n += kFieldBlock) E[n] = (float)(-C[n]);
+  // Species whose weights q_s w_s are all equal up to sign (electrons and an
+  // ion species of the same weight) take the signed integer sum of their
+  // prefixes first, so that one conversion to FP64 per node serves them all:
+  // C_n = cs * C'_n with cs = 2^-32 q_0 w_0 and C'_n that integer.  The sum is
+  // exact while the species' totals stay below 2^63 together.
+  unsigned long long tot[kMaxSpecies];
+  bool pm = true;
+  unsigned long long sum_tot = 0ull;
+#pragma unroll
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    tot[s] = 0ull;
+    if (s < ns) {
+      unsigned long long off = 0ull, t = 0ull;
+#pragma unroll
+      for (int q = 0; q < kFieldBlock / 32; ++q) {
+        const unsigned long long v = wtot[q][s];
+        off += q < w ? v : 0ull;
+        t += v;
+      }
+      run[s] += off;
+      tot[s] = t + s0[s];
+      pm = pm && (qw[s] == qw[0] || qw[s] == -qw[0]) && tot[s] < (1ull << 62);
+      sum_tot += tot[s] >> 2;
+    }
+  }
+  pm = pm && sum_tot < (1ull << 61) - 4ull;
+  const double cs = pm ? cw[0] : 1.0;
+  // total charge (in units of cs) for the uniform neutralising background of
+  // a periodic system: Q_n -= V_n Qtot / L
+  double qtot = 0.0;
+  if (pm) {
+    unsigned long long qi = 0ull;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s)
+      if (s < ns) qi += qw[s] == qw[0] ? tot[s] : 0ull - tot[s];
+    qtot = (double)(long long)qi;
   } else {
-    const double* w = R->mcw;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s)
+      if (s < ns) qtot += cw[s] * (double)tot[s];
+  }
+  const double a = periodic ? qtot * inv_L : 0.0;
+  double loc = 0.0;
+  for (int n = beg; n < end; ++n) {
+    double c = 0.0;
+    unsigned long long qi = 0ull;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      if (s < ns) {
+        unsigned long long* S = Sall + (size_t)s * (N + 1);
+        if (n > 0) run[s] += S[n];
+        S[n] = 0ull;
+        if (pm)
+          qi += qw[s] == qw[0] ? run[s] : 0ull - run[s];
+        else
+          c += cw[s] * (double)run[s];
+      }
+    }
+    if (pm) c = (double)(long long)qi;
+    if (n < N) {
+      if (periodic) c -= a * R->cumV[n];
+      C[n] = c;
+      loc += dx[n] * c;
+    }
+  }
+  const double A = cs * block_sum(loc, dsm);
+  const double phi0 = phi0_sh;
+  const double g0 = (A * kInvEps0 - phi0) * inv_L;
+  const double kc = cs * kInvEps0;
+  double fe = 0.0;
+  double* gst = R->g;
+  float* E = R->E;
+  for (int n = beg; n < min(end, N); ++n) {
+    const double gn = g0 - C[n] * kc;
+    C[n] = gn;
+    gst[n] = gn;
+    if (face) E[n] = (float)(-gn);  // face field
+    if (want_fe) fe += gn * gn * dx[n];
+  }
+  if (!face) {
+    __syncthreads();
+    const double* wgt = R->mcw;
     for (int n = tid; n <= N; n += kFieldBlock) {
       double e;
       if (n > 0 && n < N) {
-        e = -(C[n] * w[n] + C[n - 1] * (1.0 - w[n]));
+        e = -(C[n] * wgt[n] + C[n - 1] * (1.0 - wgt[n]));
       } else if (periodic) {
-        e = -(C[0] * w[0] + C[N - 1] * (1.0 - w[0]));
+        e = -(C[0] * wgt[0] + C[N - 1] * (1.0 - wgt[0]));
       } else {
         e = (n == 0) ? -C[0] : -C[N - 1];
       }
@@ -1369,7 +1454,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
     for (int n = tid; n <= N; n += kFieldBlock) {
       double p;
       if (n == 0) p = phi0;
-      else if (n == N) p = periodic ? 0.0 : 0.0;
+      else if (n == N) p = 0.0;
       else p = phi0 + C[n - 1];
       phi[n] = p;
       if (sample) R->acc[(size_t)(5 * ns) * (N + 1) + n] += p;
@@ -1387,18 +1472,15 @@ __global__ void __launch_bounds__(kFieldBlock) k_field(BatchView b, int advance,
       st->n_samples += 1;
     }
     if (want_fe) st->fe_field = fe_tot;
-    if (advance) {
-      st->step = kn;
-      for (int s = 0; s < ns; ++s) {
-        SegState* ss = b.sst + R->seg0 + s;
-        const long long cap = b.segs[R->seg0 + s].cap;
-        const long long n = ss->n_alloc < cap ? ss->n_alloc : cap;
-        ss->n_proc = n;
-        ss->n_alloc = n;
-        ss->n_real = 0;
-        ss->n_imp = 0;
-      }
-    }
+    if (advance) st->step = kn;
+  }
+  if (my_ss) {
+    // the step's births are kept up to the capacity; the next pass's records start empty
+    const long long n = my_alloc < my_cap ? my_alloc : my_cap;
+    my_ss->n_proc = n;
+    my_ss->n_alloc = n;
+    my_ss->n_real = 0;
+    my_ss->n_imp = 0;
   }
 }
 
@@ -1765,7 +1847,7 @@ size_t pass_smem_bytes(const BatchView& b) {
          sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32) + sizeof(float) * (size_t)(b.nmax + 1);
 }
 
-size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * 2 * (size_t)(b.nmax + 1); }
+size_t field_smem_bytes(const BatchView& b) { return sizeof(double) * (size_t)(b.nmax + 1); }
 
 static void set_smem_attr(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
