@@ -57,8 +57,8 @@ AUTOTUNE_STEPS = 64  # steps per autotuner trial (16 trials) before the warm-up
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "f67a7b7eb3ec2b270af9d5602838bfcd44df1afae1938a6613e39612273eb874",
-           "dram_bytes_per_particle_step": 567.739e6 / 14.326e6}
+TRAFFIC = {"sources_sha256": "fdb1abe31b362c77bf14a4641d7aeac91c521d03711a04cfbee0f9141c10944a",
+           "dram_bytes_per_particle_step": 568.408e6 / 14.326e6}
 
 
 def kernel_sources_sha256():
