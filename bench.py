@@ -342,6 +342,7 @@ def served_block(ecpic, stream, device, capacity, n_req=64, rho=0.7):
     reqs = I.served_stream(n_req, seed=1, rate=1.0)
     for r in reqs:
         r.config.n_steps = max(40, r.config.n_steps // 10)
+        I.with_headroom(r.config, I.growth_headroom(r.config.n_steps))
         r.config.sample_every = 40
     work = np.mean([r.config.n_particles * r.config.n_steps for r in reqs])
     rate = rho * capacity / work
@@ -484,10 +485,12 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         extras["single_run"] = single_run_block(torch, ecpic, stream, local)
-        extras["one_by_one"] = one_by_one_block(ecpic, cfgs, stream, local)
+        # 200-step jobs: configs sized for 200 steps
+        short = manifest(rank, args, 200)
+        extras["one_by_one"] = one_by_one_block(ecpic, short, stream, local)
         extras["served"] = served_block(ecpic, stream, local, capacity=value / max(1, world))
         extras["appendix_b"] = appendix_b_block(ecpic, stream, local)
-        e2e = e2e_block(ecpic, cfgs, stream, local, steps=200)
+        e2e = e2e_block(ecpic, short, stream, local, steps=200)
     else:
         e2e = None
     cpu = None

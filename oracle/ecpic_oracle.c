@@ -1118,6 +1118,17 @@ int oracle_step(or_run* r, int64_t n_steps) {
   return rc;
 }
 
+/* Move the run to time level k: the electrode potential (Sec. 2a, the RF
+ * bias at t = k dt) and the random stream (keyed on the level) follow it,
+ * so a state taken from the middle of a run continues from its own level.
+ * The field is formed again for level k. */
+int oracle_set_step(or_run* r, int64_t k) {
+  if (!r || k < 0) return -1;
+  if (!r->initialized) return -2;
+  r->step = k;
+  return or_refresh(r);
+}
+
 int oracle_reset_averages(or_run* r, int sample_every) {
   if (!r || sample_every < 0) return -1;
   if (!r->grid_set) return -2;

@@ -157,6 +157,8 @@ int oracle_set_particles_cell(or_run* r, int species, const int32_t* cell,
 int oracle_get_particles_cell(or_run* r, int species, int32_t* cell,
                               double* xi, int64_t cap, int64_t* n);
 int oracle_step(or_run* r, int64_t n_steps);
+/* Time level k (RF phase and random stream follow it); field formed again. */
+int oracle_set_step(or_run* r, int64_t k);
 int oracle_reset_averages(or_run* r, int sample_every);
 
 /* counters: out[0]=step, then per species s (OR_MAX_SPECIES slots of 16):

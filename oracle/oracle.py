@@ -79,6 +79,7 @@ def _load(path):
         "oracle_set_particles_cell": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64]),
         "oracle_get_particles_cell": (i32, [vp, i32, vp, vp, i64, P(i64)]),
         "oracle_step": (i32, [vp, i64]),
+        "oracle_set_step": (i32, [vp, i64]),
         "oracle_reset_averages": (i32, [vp, i32]),
         "oracle_get_counters": (i32, [vp, vp, i32]),
         "oracle_get_fields": (i32, [vp, vp, vp, vp]),
@@ -291,6 +292,10 @@ class OracleRun:
             return rc
         _chk(rc, "oracle_step")
         return rc
+
+    def set_step(self, k):
+        """Time level k: the RF phase and the random stream follow it."""
+        _chk(self._L.oracle_set_step(self.h, int(k)), "oracle_set_step")
 
     def reset_averages(self, sample_every):
         _chk(self._L.oracle_reset_averages(self.h, sample_every), "oracle_reset_averages")

@@ -213,12 +213,32 @@ def _log_uniform(rng, lo, hi, size=None):
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size))
 
 
+def growth_headroom(steps: int) -> float:
+    """Particle capacity per species, as a multiple of the initial load, for a
+    manifest run of ``steps`` steps.  The discharges grow by ionisation from
+    n0 = 1e14; the fastest of the 256-run manifest has 1.1x its electrons
+    after 256 steps, 2.05x after 1024 and 2.9x after 2048, so 2 + steps/500
+    (at most 8) keeps about twice that margin."""
+    return min(8.0, 2.0 + steps / 500.0)
+
+
+def with_headroom(cfg: RunConfig, headroom: float) -> RunConfig:
+    """Resize every species' capacity to ``headroom`` x its initial load
+    (plus the loader's 4096 spare slots)."""
+    for sp in cfg.species:
+        sp.capacity = int(headroom * sp.n0) + 4096
+    return cfg
+
+
 def batched_manifest(n_runs: int = 256, seed: int = 0, steps: int = 4400,
-                     scale: float = 1.0) -> List[RunConfig]:
+                     scale: float = 1.0, headroom: Optional[float] = None) -> List[RunConfig]:
     """Independent CCP runs: cells ~ logU[64,1024], particles ~ logU[1e4,1e6]
     (split evenly between species), V0 ~ logU[100,500] V, p ~ logU[10,100] mTorr,
     dx ~ U[0.5,1.0] mm, n0 = 1e14, dt = 1/(400 f).  ``scale`` shrinks particle
-    counts for quick tests."""
+    counts for quick tests.  Capacity: ``headroom`` x the initial load, by
+    default ``growth_headroom(steps)`` so that no run fills it in ``steps``."""
+    if headroom is None:
+        headroom = growth_headroom(steps)
     rng = np.random.default_rng(seed)
     runs = []
     for r in range(n_runs):
@@ -231,7 +251,7 @@ def batched_manifest(n_runs: int = 256, seed: int = 0, steps: int = 4400,
         nps = max(npart // 2, 16)
         cfg = ccp(f"batch-{r}", N=N, n0=1e14, dt=1.0 / (400 * F_RF), ppc=0, v0=v0,
                   p_mtorr=p, n_steps=steps, seed=seed * 1000003 + r, L=L,
-                  n_per_species=nps)
+                  n_per_species=nps, headroom=headroom)
         runs.append(cfg)
     return runs
 
@@ -275,7 +295,7 @@ def served_stream(n_requests: int = 2000, seed: int = 1, rate: float = 1.0,
     for i in range(n_requests):
         t += rng.exponential(1.0 / rate)
         periods = int(rng.integers(period_range[0], period_range[1] + 1))
-        cfg = base[i]
+        cfg = with_headroom(base[i], growth_headroom(400 * periods))
         cfg.n_steps = 400 * periods
         cfg.name = f"req-{i}"
         out.append(Request(arrival=t, config=cfg))

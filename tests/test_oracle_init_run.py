@@ -150,3 +150,36 @@ def test_quiet_start_app_b_mc_heats_ec_conserves():
     assert abs(out[(8.0, I.EC)]) < 2e-3, out
     assert out[(8.0, I.MC)] > 0.1, out
     assert abs(out[(1.0, I.EC)]) < 2e-3 and abs(out[(1.0, I.MC)]) < 5e-3, out
+
+
+def test_set_step_continues_a_state_from_its_own_level():
+    """A colliding RF discharge stepped to level 7, its particles copied into a
+    fresh run moved to level 7: one more step gives the same particles bit for
+    bit (the RF bias and the random stream follow the level); left at level 0
+    the copy diverges."""
+    cfg = I.config_small(seed=4)
+    a = oracle_from_config(cfg)
+    a.step(7)
+    st = [a.get_particles(s) for s in range(2)]
+
+    def copy(level):
+        b = oracle_from_config(cfg)
+        if level:
+            b.set_step(level)
+        for s in range(2):
+            p = st[s]
+            b.set_particles(s, p["X"], p["vx"], p["vy"], p["vz"], p["id"])
+        b.step(1)
+        return b
+
+    a.step(1)
+    b, c = copy(7), copy(0)
+    assert b.counters()["step"] == 8
+    for s in range(2):
+        pa, pb, pc = a.get_particles(s), b.get_particles(s), c.get_particles(s)
+        ia, ib = np.argsort(pa["id"]), np.argsort(pb["id"])
+        for k in ("X", "vx", "vy", "vz", "id"):
+            assert np.array_equal(pa[k][ia], pb[k][ib]), (s, k)
+        ic = np.argsort(pc["id"])
+        if pc["id"].size == pa["id"].size and np.array_equal(pc["id"][ic], pa["id"][ia]):
+            assert not np.array_equal(pa["vx"][ia], pc["vx"][ic])
