@@ -621,6 +621,12 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, const Re
 // 2 = the EC2 scheme with the sample decision taken at run time.  Keeping the
 // rare code out of the common instance keeps its loop small in the
 // instruction cache.
+// L2 prefetch of a byte range (one bulk instruction; 16-byte aligned start,
+// size a multiple of 16)
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int KIND>
 __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {
@@ -688,6 +694,28 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   for (long long base = qbeg;; base += kPassBlock) {
     const bool more = base < qend;
     if (more) {
+      if (threadIdx.x == 0) {
+        // the next iteration's particle records into L2
+        const long long nb = base + kPassBlock;
+        if (nb < qend) {
+          const long long p0 = 4 * nb;
+          long long p1 = 4 * min(qend, nb + kPassBlock);
+          p1 = min(p1, n);
+          if (p1 > p0) {
+            const unsigned b4 = (unsigned)(((p1 - p0) * 4) & ~15ll);
+            if (b4) {
+              l2_prefetch(pc + p0, b4);
+              l2_prefetch(pxi + p0, b4);
+              l2_prefetch(pvx + p0, b4);
+              if (load_yz) {
+                l2_prefetch(pvy + p0, b4);
+                l2_prefetch(pvz + p0, b4);
+              }
+              if (mcc) l2_prefetch(pid + p0, (unsigned)(((p1 - p0) * 8) & ~15ll));
+            }
+          }
+        }
+      }
       const long long q = base + (long long)threadIdx.x;
       const long long i0 = 4 * q;
       const bool inq = q < qend && chk(i0 < G.cap, 2, i0, G.cap);
