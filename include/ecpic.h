@@ -194,6 +194,20 @@ int ecpic_nu_max(ecpic_run* run, int species, double* nu_max, uint32_t* threshol
 int ecpic_set_sort_every(ecpic_run* run, int sort_every);
 /* Force a counting sort by cell now (compacts absorbed particles). */
 int ecpic_sort_now(ecpic_run* run);
+/* Particle memory grows with ionisation (Sec. 3a, the discharge's density
+ * build-up): raise the capacity of one species of an initialised run to at
+ * least `capacity` particles (< 2^31; never shrinks), keeping the run's
+ * state.  A new device block is allocated on the run's stream, the run's
+ * arrays are copied into it and the old block is freed; the call
+ * synchronises the stream and belongs between steps.  ECPIC_ERR_NOMEM leaves
+ * the run as it was.  The trajectory does not depend on the capacity. */
+int ecpic_reserve(ecpic_run* run, int species, int64_t capacity);
+/* on = 1: after every chunk of about 64 steps (whole sort cycles) ecpic_step
+ * doubles the capacity of any species filled beyond 3/4 of it (as
+ * ecpic_reserve), synchronising the stream at each chunk; on = 0 (the
+ * default): ecpic_step stays asynchronous and a full species fails the run
+ * with ECPIC_ERR_CAPACITY.  The engine always grows its runs this way. */
+int ecpic_set_auto_grow(ecpic_run* run, int on);
 /* Measurement: advance n_steps with plain launches (no graph), bracketing
  * each kernel phase with CUDA events on the run's stream; synchronises.
  * ms[0..3] = summed device time of the particle pass, the field solve, the
@@ -272,8 +286,9 @@ const char* ecpic_engine_last_error(const ecpic_engine* eng);
 int ecpic_engine_submit(ecpic_engine* eng, const ecpic_run_config* cfg, int64_t n_steps,
                         uint64_t* ticket);
 /* One scheduling round: admit queued runs that fit, advance every resident
- * run by up to max_steps steps (runs stop at their own step count), wait, and
- * retire the runs that finished.  *n_resident (may be NULL) receives the
+ * run by up to max_steps steps (runs stop at their own step count; every
+ * about 64 steps, a species filled beyond 3/4 of its capacity has it doubled,
+ * see ecpic_set_auto_grow), wait, and retire the runs that finished.  *n_resident (may be NULL) receives the
  * number of runs resident after the round, *n_queued the queue length. */
 int ecpic_engine_pump(ecpic_engine* eng, int64_t max_steps, int* n_resident, int* n_queued);
 /* State of a ticket: 0 queued, 1 resident, 2 finished, < 0 an ecpic_status

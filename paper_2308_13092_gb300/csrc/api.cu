@@ -22,6 +22,7 @@ struct ecpic_run {
   std::unique_ptr<Batch> batch;
   std::string err;
   int sort_every = 16;
+  bool auto_grow = false;
 };
 
 namespace {
@@ -249,6 +250,7 @@ int ecpic_init(ecpic_run* r, uint64_t seed, double dt, const int64_t* n_per_spec
     const int N = (int)r->spec.edges.size() - 1;
     std::unique_ptr<Batch> b(new Batch(r->device, r->stream, 1, (int)ns, N));
     b->set_sort_every(r->sort_every);
+    b->set_auto_grow(r->auto_grow);
     std::string err;
     const int rc = b->admit(0, r->spec, &err);
     if (rc) return fail(r, rc, err);
@@ -346,6 +348,31 @@ int ecpic_set_sort_every(ecpic_run* r, int k) {
   if (k < 1) return fail(r, ECPIC_ERR_ARG, "sort cadence must be >= 1");
   r->sort_every = k;
   if (r->batch) r->batch->set_sort_every(k);
+  return ECPIC_OK;
+}
+
+int ecpic_reserve(ecpic_run* r, int species, int64_t capacity) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  if (species < 0 || species >= (int)r->spec.species.size()) return fail(r, ECPIC_ERR_ARG, "unknown species");
+  if (capacity < 1) return fail(r, ECPIC_ERR_ARG, "capacity must be >= 1");
+  return guarded(r, [&]() -> int {
+    long long cap[ecpic::kMaxSpecies] = {0, 0, 0, 0};
+    const RunSpec& cur = r->batch->spec(0);
+    for (size_t s = 0; s < cur.species.size(); ++s) cap[s] = cur.species[s].cap;
+    if (capacity > cap[species]) cap[species] = capacity;
+    std::string err;
+    const int rc = r->batch->reserve(0, cap, &err);
+    if (rc) return fail(r, rc, err);
+    for (size_t s = 0; s < cur.species.size(); ++s) r->spec.species[s].cap = r->batch->spec(0).species[s].cap;
+    return ECPIC_OK;
+  });
+}
+
+int ecpic_set_auto_grow(ecpic_run* r, int on) {
+  if (!r || (on != 0 && on != 1)) return ECPIC_ERR_ARG;
+  r->auto_grow = on != 0;
+  if (r->batch) r->batch->set_auto_grow(r->auto_grow);
   return ECPIC_OK;
 }
 

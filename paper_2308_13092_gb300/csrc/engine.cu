@@ -181,6 +181,7 @@ int ecpic_engine_create(ecpic_engine** out, int device, void* cuda_stream, size_
     e->max_cells = max_cells;
     e->spc = species_per_run;
     e->batch.reset(new Batch(device, e->stream, max_slots, species_per_run, max_cells));
+    e->batch->set_auto_grow(true);  // runs that grow by ionisation get room as they fill
     e->slot_ticket.assign(max_slots, 0);
   } catch (...) {
     delete e;

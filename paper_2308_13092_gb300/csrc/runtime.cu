@@ -101,6 +101,79 @@ size_t layout_bytes(const RunSpec& s) {
   add(8 * ns * N);                                                  // J.E sums
   return b;
 }
+
+// Pointers of every array of one run inside its device block, in a fixed
+// order: the arrays that do not depend on the particle capacities come first
+// (grid, field, deposit, accumulators, tallies, cross-section tables), so a
+// block carved again with larger capacities keeps their offsets.  Sets the
+// pointer fields of R and of the run's spc segment descriptors; returns the
+// size of that capacity-independent prefix and, in *total, of the whole.
+size_t carve_layout(const RunSpec& spec, char* base, RunDev* R, SegDev* segs, int spc,
+                    size_t* total) {
+  Carve cv{base};
+  const size_t N = spec.edges.size() - 1, ns = spec.species.size();
+  R->x = cv.take<double>(N + 1);
+  R->dx = cv.take<double>(N);
+  R->V = cv.take<double>(N + 1);
+  R->invV = cv.take<double>(N + 1);
+  R->mcw = cv.take<double>(N + 1);
+  R->cumV = cv.take<double>(N + 1);
+  R->g = cv.take<double>(N);
+  R->dtdx = cv.take<float>(N);
+  R->rp = cv.take<float>(N);
+  R->rm = cv.take<float>(N);
+  R->E = cv.take<float>(N + 1);
+  R->phi = cv.take<double>(N + 1);
+  R->S = cv.take<unsigned long long>(ns * (N + 1));
+  R->momd = cv.take<double>(ns * 2 * (N + 1));
+  R->acc = cv.take<double>((size_t)acc_size((int)ns) * (N + 1));
+  R->mom = nullptr;
+  R->tal = cv.take<unsigned long long>(ns * (size_t)(spec.eedf_bins + spec.iedf_bins + spec.iad_bins));
+  R->pw = cv.take<double>(ns * N);
+  for (size_t s = 0; s < ns; ++s) {
+    const HostSpecies& hs = spec.species[s];
+    R->sp[s].sig4 = nullptr;
+    if (!hs.procs.empty())
+      R->sp[s].sig4 = cv.take<float4>(hs.procs[0].sigma.size() * ((hs.procs.size() + 3) / 4));
+  }
+  const size_t prefix = cv.off;
+  for (int s = 0; s < spc; ++s) {
+    SegDev& G = segs[s];
+    if (s < (int)ns) {
+      const size_t c = (size_t)spec.species[s].cap;
+      for (int buf = 0; buf < 2; ++buf) {
+        G.cell[buf] = cv.take<int32_t>(c);
+        G.xi[buf] = cv.take<float>(c);
+        G.vx[buf] = cv.take<float>(c);
+        G.vy[buf] = cv.take<float>(c);
+        G.vz[buf] = cv.take<float>(c);
+        G.id[buf] = cv.take<uint64_t>(c);
+      }
+      G.cap = (long long)c;
+    } else {
+      std::memset(G.cell, 0, sizeof(G.cell));
+      std::memset(G.xi, 0, sizeof(G.xi));
+      std::memset(G.vx, 0, sizeof(G.vx));
+      std::memset(G.vy, 0, sizeof(G.vy));
+      std::memset(G.vz, 0, sizeof(G.vz));
+      std::memset(G.id, 0, sizeof(G.id));
+      G.cap = 0;
+    }
+    G.real = nullptr;
+    G.real_cap = 0;
+    G.imp = nullptr;
+    G.imp_cap = 0;
+  }
+  for (size_t s = 0; s < ns; ++s) {
+    SegDev& G = segs[s];
+    G.real_cap = real_capacity(spec.species[s], spec);
+    G.real = cv.take<RealRec>((size_t)G.real_cap);
+    G.imp_cap = impact_capacity(spec.species[s]);
+    G.imp = cv.take<int>((size_t)G.imp_cap);
+  }
+  *total = cv.off;
+  return prefix;
+}
 }  // namespace
 
 std::string validate_grid(const std::vector<double>& e, int bc) {
@@ -352,8 +425,14 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   void* mem = nullptr;
   int rc = check(cudaMallocAsync(&mem, bytes, stream_), "device allocation", err);
   if (rc) return rc;
-  Carve cv{static_cast<char*>(mem)};
   RunDev R{};
+  size_t total = 0;
+  carve_layout(spec, static_cast<char*>(mem), &R, &h_segs_[slot * spc_], spc_, &total);
+  if (total > bytes) {
+    cudaFreeAsync(mem, stream_);
+    if (err) *err = "internal: run layout exceeds its block";
+    return ECPIC_ERR_CUDA;
+  }
   R.active = 1;
   R.N = N;
   R.bc = spec.bc;
@@ -393,44 +472,26 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   }
   R.uniform = uniform ? 1 : 0;
   R.dtdx_u = (float)(spec.dt / dxu);
-  double* d_x = cv.take<double>(N + 1);
-  double* d_dx = cv.take<double>(N);
-  double* d_V = cv.take<double>(N + 1);
-  double* d_invV = cv.take<double>(N + 1);
-  double* d_mcw = cv.take<double>(N + 1);
-  double* d_cumV = cv.take<double>(N + 1);
-  R.g = cv.take<double>(N);
-  float* d_dtdx = cv.take<float>(N);
-  float* d_rp = cv.take<float>(N);
-  float* d_rm = cv.take<float>(N);
-  R.E = cv.take<float>(N + 1);
-  R.phi = cv.take<double>(N + 1);
-  R.S = cv.take<unsigned long long>((size_t)ns * (N + 1));
-  R.momd = cv.take<double>((size_t)ns * 2 * (N + 1));
-  R.acc = cv.take<double>((size_t)acc_size(ns) * (N + 1));
-  R.mom = nullptr;
+  double* d_x = const_cast<double*>(R.x);
+  double* d_dx = const_cast<double*>(R.dx);
+  double* d_V = const_cast<double*>(R.V);
+  double* d_invV = const_cast<double*>(R.invV);
+  double* d_mcw = const_cast<double*>(R.mcw);
+  double* d_cumV = const_cast<double*>(R.cumV);
+  float* d_dtdx = const_cast<float*>(R.dtdx);
+  float* d_rp = const_cast<float*>(R.rp);
+  float* d_rm = const_cast<float*>(R.rm);
   R.eedf_n = spec.eedf_bins;
   R.iedf_n = spec.iedf_bins;
   R.iad_n = spec.iad_bins;
   R.tal_stride = spec.eedf_bins + spec.iedf_bins + spec.iad_bins;
-  R.tal = cv.take<unsigned long long>((size_t)ns * R.tal_stride);
-  R.pw = cv.take<double>((size_t)ns * N);
   eedf_cells(spec, &R.eedf_c0, &R.eedf_c1);
   R.eedf_dEinv = (float)(1.0 / spec.eedf_dE);
   R.iedf_dEinv = (float)(1.0 / spec.iedf_dE);
   R.iad_binv = (float)(spec.iad_bins / 90.0);
   cudaMemsetAsync(R.tal, 0, 8 * (size_t)ns * R.tal_stride, stream_);
   cudaMemsetAsync(R.pw, 0, 8 * (size_t)ns * N, stream_);
-  R.x = d_x;
-  R.dx = d_dx;
-  R.V = d_V;
-  R.invV = d_invV;
-  R.mcw = d_mcw;
-  R.cumV = d_cumV;
   R.inv_L = 1.0 / R.L;
-  R.dtdx = d_dtdx;
-  R.rp = d_rp;
-  R.rm = d_rm;
   cudaMemcpyAsync(d_x, spec.edges.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_dx, dx.data(), 8 * N, cudaMemcpyHostToDevice, stream_);
   cudaMemcpyAsync(d_V, V.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
@@ -485,7 +546,6 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
       D.nu_bnd = (float)((spec.gas ? spec.ng : 0.0) * smax * (1.0 + 1.0 / 65536.0));
     }
     D.np4 = (D.nproc + 3) / 4;
-    D.sig4 = nullptr;
     for (int p = 0; p < kMaxProc; ++p) D.thr_all[p] = FLT_MAX;
     if (D.nproc > 0) {
       // node-major interleaving: one 16-byte load per node serves four processes
@@ -493,9 +553,8 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
       std::vector<float> il(nt * g4 * 4, 0.0f);
       for (int p = 0; p < D.nproc; ++p)
         for (size_t i = 0; i < nt; ++i) il[(i * g4 + p / 4) * 4 + p % 4] = hs.procs[p].sigma[i];
-      float4* tab = cv.take<float4>(nt * g4);
-      cudaMemcpyAsync(tab, il.data(), 16 * nt * g4, cudaMemcpyHostToDevice, stream_);
-      D.sig4 = tab;
+      cudaMemcpyAsync(const_cast<float4*>(D.sig4), il.data(), 16 * nt * g4, cudaMemcpyHostToDevice,
+                      stream_);
     }
     for (int p = 0; p < D.nproc; ++p) {
       const HostProc& hp = hs.procs[p];
@@ -511,35 +570,8 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   // particle segments
   std::vector<SegState> sst(spc_);
   for (int s = 0; s < spc_; ++s) {
-    SegDev& G = h_segs_[R.seg0 + s];
     std::memset(sst.data() + s, 0, sizeof(SegState));
-    if (s < ns) {
-      const size_t c = (size_t)spec.species[s].cap;
-      for (int buf = 0; buf < 2; ++buf) {
-        G.cell[buf] = cv.take<int32_t>(c);
-        G.xi[buf] = cv.take<float>(c);
-        G.vx[buf] = cv.take<float>(c);
-        G.vy[buf] = cv.take<float>(c);
-        G.vz[buf] = cv.take<float>(c);
-        G.id[buf] = cv.take<uint64_t>(c);
-      }
-      G.cap = (long long)c;
-      sst[s].n_proc = sst[s].n_alloc = spec.n_init[s];
-    } else {
-      std::memset(G.cell, 0, sizeof(G.cell));
-      G.cap = 0;
-    }
-    G.real = nullptr;
-    G.real_cap = 0;
-    G.imp = nullptr;
-    G.imp_cap = 0;
-  }
-  for (int s = 0; s < ns; ++s) {
-    SegDev& G = h_segs_[R.seg0 + s];
-    G.real_cap = real_capacity(spec.species[s], spec);
-    G.real = cv.take<RealRec>((size_t)G.real_cap);
-    G.imp_cap = impact_capacity(spec.species[s]);
-    G.imp = cv.take<int>((size_t)G.imp_cap);
+    if (s < ns) sst[s].n_proc = sst[s].n_alloc = spec.n_init[s];
   }
   cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
                   stream_);
@@ -572,6 +604,117 @@ void Batch::refresh(int slot) {
   const BatchView b = view();
   launch_pass(b, std::max(1, std::min(choose_grid(), sm_count_ * 2)), MODE_REFRESH, slot, stream_);
   launch_field(b, 0, slot, stream_);
+}
+
+int Batch::reserve(int slot, const long long* cap, std::string* err) {
+  if (!slot_active(slot)) {
+    if (err) *err = "no run in this slot";
+    return ECPIC_ERR_STATE;
+  }
+  RunSpec spec = specs_[slot];
+  const int ns = (int)spec.species.size();
+  bool grow = false;
+  for (int s = 0; s < ns; ++s)
+    if (cap[s] > spec.species[s].cap) {
+      if (cap[s] > (long long)INT32_MAX) {
+        if (err) *err = "capacity above 2^31 - 1 particles";
+        return ECPIC_ERR_ARG;
+      }
+      spec.species[s].cap = cap[s];
+      grow = true;
+    }
+  if (!grow) return ECPIC_OK;
+  cudaSetDevice(device_);
+  const int seg0 = slot * spc_;
+  // the run's sizes and current buffer set (between steps)
+  std::vector<SegState> sst(spc_);
+  int rc = check(cudaMemcpyAsync(sst.data(), d_sst_ + seg0, sizeof(SegState) * spc_,
+                                 cudaMemcpyDeviceToHost, stream_), "read sizes", err);
+  if (rc) return rc;
+  rc = check(cudaStreamSynchronize(stream_), "read sizes", err);
+  if (rc) return rc;
+  const size_t bytes = layout_bytes(spec);
+  void* mem = nullptr;
+  rc = check(cudaMallocAsync(&mem, bytes, stream_), "device allocation", err);
+  if (rc) return rc;  // the run keeps its present capacity
+  RunDev R = h_runs_[slot];
+  std::vector<SegDev> segs(h_segs_.begin() + seg0, h_segs_.begin() + seg0 + spc_);
+  size_t total = 0, total_old = 0;
+  const size_t prefix = carve_layout(spec, static_cast<char*>(mem), &R, segs.data(), spc_, &total);
+  RunDev Rold{};
+  std::vector<SegDev> old_segs(spc_);
+  const size_t prefix_old = carve_layout(specs_[slot], static_cast<char*>(slot_mem_[slot]), &Rold,
+                                         old_segs.data(), spc_, &total_old);
+  if (prefix != prefix_old || total > bytes) {
+    cudaFreeAsync(mem, stream_);
+    if (err) *err = "internal: run layouts disagree";
+    return ECPIC_ERR_CUDA;
+  }
+  // grid, field, deposit, accumulators, tallies and tables keep their offsets
+  cudaMemcpyAsync(mem, slot_mem_[slot], prefix, cudaMemcpyDeviceToDevice, stream_);
+  for (int s = 0; s < ns; ++s) {
+    const SegDev& A = h_segs_[seg0 + s];
+    SegDev& B = segs[s];
+    const int c = sst[s].cur;
+    const size_t n = (size_t)std::min<long long>(std::max<long long>(sst[s].n_alloc, 0), A.cap);
+    if (c != 0 && c != 1) {
+      cudaFreeAsync(mem, stream_);
+      if (err) *err = "internal: bad buffer index";
+      return ECPIC_ERR_CUDA;
+    }
+    if (n == 0) continue;
+    cudaMemcpyAsync(B.cell[c], A.cell[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(B.xi[c], A.xi[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(B.vx[c], A.vx[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(B.vy[c], A.vy[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(B.vz[c], A.vz[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
+    cudaMemcpyAsync(B.id[c], A.id[c], 8 * n, cudaMemcpyDeviceToDevice, stream_);
+  }
+  // the real-collision and impact lists are empty between steps
+  for (int s = 0; s < spc_; ++s) h_segs_[seg0 + s] = segs[s];
+  cudaMemcpyAsync(d_segs_ + seg0, &h_segs_[seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
+                  stream_);
+  h_runs_[slot] = R;
+  upload_run(slot);
+  cudaFreeAsync(slot_mem_[slot], stream_);
+  bytes_in_use_ = bytes_in_use_ - slot_bytes_[slot] + bytes;
+  slot_mem_[slot] = mem;
+  slot_bytes_[slot] = bytes;
+  specs_[slot] = spec;
+  return check(cudaGetLastError(), "reserve", err);
+}
+
+int Batch::grow_full_runs(std::string* err) {
+  std::vector<SegState> sst(nseg_);
+  int rc = check(cudaMemcpyAsync(sst.data(), d_sst_, sizeof(SegState) * nseg_, cudaMemcpyDeviceToHost,
+                                 stream_), "read sizes", err);
+  if (rc) return rc;
+  rc = check(cudaStreamSynchronize(stream_), "read sizes", err);
+  if (rc) return rc;
+  for (int slot = 0; slot < max_slots_; ++slot) {
+    if (!slot_active(slot)) continue;
+    const int ns = (int)specs_[slot].species.size();
+    long long cap[kMaxSpecies] = {0, 0, 0, 0};
+    bool grow = false;
+    for (int s = 0; s < ns; ++s) {
+      const long long c = h_segs_[slot * spc_ + s].cap;
+      cap[s] = c;
+      if ((double)sst[slot * spc_ + s].n_alloc > grow_at_ * (double)c) {
+        cap[s] = std::min<long long>((long long)INT32_MAX, 2 * c);
+        grow = grow || cap[s] > c;
+      }
+    }
+    if (!grow) continue;
+    std::string e;
+    rc = reserve(slot, cap, &e);
+    // a failed allocation leaves the run as it was: it may still fill up and
+    // then fails alone with ECPIC_ERR_CAPACITY
+    if (rc && rc != ECPIC_ERR_NOMEM) {
+      if (err) *err = e;
+      return rc;
+    }
+  }
+  return ECPIC_OK;
 }
 
 void Batch::release(int slot) {
@@ -649,6 +792,21 @@ int Batch::step(long long n, std::string* err) {
     if (err) *err = "negative step count";
     return ECPIC_ERR_ARG;
   }
+  if (!auto_grow_) return step_chunk(n, err);
+  // growth checks between chunks of whole sort cycles
+  const long long chunk = std::max<long long>(sort_every_, (64 / sort_every_) * sort_every_);
+  while (n > 0) {
+    const long long m = std::min(n, chunk);
+    int rc = step_chunk(m, err);
+    if (rc) return rc;
+    n -= m;
+    rc = grow_full_runs(err);
+    if (rc) return rc;
+  }
+  return ECPIC_OK;
+}
+
+int Batch::step_chunk(long long n, std::string* err) {
   cudaSetDevice(device_);
   int rc = ensure_graphs(err);
   if (rc) return rc;

@@ -79,7 +79,16 @@ class Batch {
   void release(int slot);
   bool slot_active(int slot) const { return slot >= 0 && slot < max_slots_ && active_[slot]; }
 
-  int step(long long n, std::string* err);  // async
+  int step(long long n, std::string* err);  // async unless growth is on
+  // grow species' capacities to at least cap[s] (never shrinks), keeping the
+  // run's state; between steps, synchronises the stream
+  int reserve(int slot, const long long* cap, std::string* err);
+  // double the capacity of any species filled beyond `at` of it, checked
+  // after every chunk of about 64 steps (synchronises there)
+  void set_auto_grow(bool on, double at = 0.75) {
+    auto_grow_ = on;
+    grow_at_ = at;
+  }
   int profile_step(long long n, double* ms, long long* launches, std::string* err);
   int sort_now(std::string* err);
   int sync(std::string* err);
@@ -118,6 +127,8 @@ class Batch {
   void invalidate_graphs();
   int ensure_graphs(std::string* err);
   int choose_grid() const;
+  int step_chunk(long long n, std::string* err);
+  int grow_full_runs(std::string* err);
   int check(cudaError_t e, const char* what, std::string* err);
 
   int device_;
@@ -140,6 +151,8 @@ class Batch {
   int sort_every_ = 16;
   int since_sort_ = 0;
   bool use_graphs_ = true;
+  bool auto_grow_ = false;
+  double grow_at_ = 0.75;
   int pass_grid_ = 0;
   int pass_grid_override_ = 0;
   cudaGraphExec_t graph_k_ = nullptr;

@@ -113,6 +113,8 @@ SIGNATURES = {
     "ecpic_nu_max": (i32, [vp, i32, C.POINTER(d), C.POINTER(u32)]),
     "ecpic_set_sort_every": (i32, [vp, i32]),
     "ecpic_sort_now": (i32, [vp]),
+    "ecpic_reserve": (i32, [vp, i32, i64]),
+    "ecpic_set_auto_grow": (i32, [vp, i32]),
     "ecpic_profile_step": (i32, [vp, i64, vp, vp]),
     "ecpic_set_pass_grid": (i32, [vp, i32]),
     "ecpic_doubling_grid": (i32, [i32, d, d, i32, i32, vp, i32]),
@@ -294,6 +296,14 @@ class Run:
 
     def sort_now(self):
         _chk(self.h, self._L.ecpic_sort_now(self.h), "ecpic_sort_now")
+
+    def reserve(self, species, capacity):
+        """Raise one species' particle capacity (keeps the run's state)."""
+        _chk(self.h, self._L.ecpic_reserve(self.h, int(species), int(capacity)), "ecpic_reserve")
+
+    def set_auto_grow(self, on=True):
+        """Double a species' capacity when it is 3/4 full (checked every ~64 steps)."""
+        _chk(self.h, self._L.ecpic_set_auto_grow(self.h, 1 if on else 0), "ecpic_set_auto_grow")
 
     def profile_step(self, n):
         ms = np.zeros(4)
