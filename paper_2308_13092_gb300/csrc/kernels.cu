@@ -118,8 +118,12 @@ __device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int
 
 // exclusive prefix of the work of all segments (particles, groups of `unit`
 // particles, or recorded real collisions): pre[0..nseg]
+// (with meta: per segment its run slot, buffer index and real-collision
+// count, meta[3 s .. 3 s + 2], so that the records' consumers need no
+// dependent global loads for them)
 __device__ long long seg_prefix(const BatchView& b, int mode, int only, long long* pre,
-                                long long* wsm, int unit = 1, bool reals = false) {
+                                long long* wsm, int unit = 1, bool reals = false,
+                                int* meta = nullptr) {
   const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
   const int s0 = threadIdx.x * per;
   long long loc = 0;
@@ -127,11 +131,20 @@ __device__ long long seg_prefix(const BatchView& b, int mode, int only, long lon
     const int s = s0 + k;
     if (s < b.nseg) {
       const int slot = b.segs[s].run;
-      const long long c = !run_live(b.runs[slot], b.rst[slot], mode, only, slot) ? 0
-                          : reals ? b.sst[s].n_real + b.sst[s].n_imp
+      const bool live = run_live(b.runs[slot], b.rst[slot], mode, only, slot);
+      // records past a list's capacity were never written (the pass failed
+      // the run with ECPIC_ERR_CAPACITY): only the stored ones count
+      const long long nr = reals ? min(b.sst[s].n_real, b.segs[s].real_cap) : 0;
+      const long long c = !live ? 0
+                          : reals ? nr + min(b.sst[s].n_imp, b.segs[s].imp_cap)
                                   : (b.sst[s].n_proc + unit - 1) / unit;
       pre[s] = c;
       loc += c;
+      if (meta) {
+        meta[3 * s] = slot;
+        meta[3 * s + 1] = b.sst[s].cur;
+        meta[3 * s + 2] = live ? (int)nr : 0;
+      }
     }
   }
   long long total;
@@ -504,10 +517,10 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
 // Impact tallies of an ion absorbed at x = 0 this step: energy (eV) and
 // angle from the electrode normal (degrees) of the velocity that carried it
 // out; the absorbed slot keeps that velocity until the next sort.
-__device__ __noinline__ void tally_impact(const BatchView& b, int s, int i) {
+__device__ __noinline__ void tally_impact(const BatchView& b, int s, int slot, int cur, int i) {
   const SegDev& G = b.segs[s];
-  const RunDev* R = b.runs + G.run;
-  const int sp = G.species, cur = b.sst[s].cur;
+  const RunDev* R = b.runs + slot;
+  const int sp = G.species;
   if (!chk(i >= 0 && i < G.cap, 26, i, G.cap)) return;
   const float vx = G.vx[cur][i], yz = yz2(G.vy[cur][i], G.vz[cur][i]);
   const float E = kin_eV(R->sp[sp].half_m_over_e, vx, yz);
@@ -523,15 +536,15 @@ __device__ __noinline__ void tally_impact(const BatchView& b, int s, int i) {
 // and, for heavy species, block B (the target neutral's velocity), scatters
 // and writes the new velocity.  On sample steps the pass has already added
 // the pre-collision vx moments; the change is added here.
-__device__ __forceinline__ void collide_real(const BatchView& b, int s, const RealRec& rec) {
+__device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot, int cur,
+                                             const RealRec& rec) {
   const int i = rec.i, chosen = rec.chosen;
   const float En = rec.En, gm = rec.gm;
   const SegDev& G = b.segs[s];
-  const int slot = G.run, sp = G.species;
+  const int sp = G.species;
   const RunDev* R = b.runs + slot;
   const RunState* st = b.rst + slot;
   const SpeciesDev* SP = &R->sp[sp];
-  const int cur = b.sst[s].cur;
   const long long k = st->step;
   const bool sample = R->sample_every > 0 && ((k + 1) % R->sample_every) == 0;
   const int N = R->N;
@@ -1185,21 +1198,24 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
 __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
+  int* meta = reinterpret_cast<int*>(pre + b.nseg + 1);  // slot, buffer, reals per segment
   __shared__ long long wsm[32];
-  const long long T = seg_prefix(b, MODE_STEP, -1, pre, wsm, 1, true);
+  const long long T = seg_prefix(b, MODE_STEP, -1, pre, wsm, 1, true, meta);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * kCollideBlock;
   for (long long w0 = (long long)blockIdx.x * kCollideBlock + (threadIdx.x & ~31); w0 < T; w0 += stride) {
     const long long r = w0 + lane;
     const bool valid = r < T;
-    int s = 0;
+    int s = 0, slot = 0, cur = 0;
     RealRec rec;
     rec.chosen = -1;
     int imp_i = -1;  // an impact record instead: the absorbed ion's index
     if (valid) {
       s = seg_find(pre, b.nseg, r);
+      slot = meta[3 * s];
+      cur = meta[3 * s + 1];
       const long long j = r - pre[s];
-      const long long nr = b.sst[s].n_real;
+      const long long nr = meta[3 * s + 2];
       if (j >= nr) {
         const long long ii = j - nr;
         if (ii < b.segs[s].imp_cap) imp_i = b.segs[s].imp[ii];
@@ -1223,10 +1239,10 @@ __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
     const unsigned grp = __match_any_sync(kFull, key);
     if (ok && lane == __ffs(grp) - 1) {
       const SegDev& G = b.segs[s];
-      atomicAdd(&b.rst[G.run].ctr[G.species][C_COLL0 + rec.chosen], (unsigned long long)__popc(grp));
+      atomicAdd(&b.rst[slot].ctr[G.species][C_COLL0 + rec.chosen], (unsigned long long)__popc(grp));
     }
-    if (ok) collide_real(b, s, rec);
-    if (imp_i >= 0) tally_impact(b, s, imp_i);
+    if (ok) collide_real(b, s, slot, cur, rec);
+    if (imp_i >= 0) tally_impact(b, s, slot, cur, imp_i);
   }
 }
 
@@ -1896,7 +1912,7 @@ void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t 
 }
 
 void launch_collide(const BatchView& b, int grid, cudaStream_t s) {
-  const size_t sm = sizeof(long long) * (size_t)(b.nseg + 1);
+  const size_t sm = sizeof(long long) * (size_t)(b.nseg + 1) + 3 * sizeof(int) * (size_t)b.nseg;
   set_smem_attr((const void*)k_collide, sm);
   k_collide<<<grid, kCollideBlock, sm, s>>>(b);
 }
