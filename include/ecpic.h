@@ -275,7 +275,8 @@ typedef struct {
 
 /* max_cells bounds N of every admitted run; species_per_run bounds their
  * species count; mem_budget_bytes bounds the particle and grid memory of the
- * resident runs (0 = no limit). */
+ * resident runs at admission (0 = no limit; a resident run whose particle
+ * capacity grows may take the total past it). */
 int ecpic_engine_create(ecpic_engine** out, int device, void* cuda_stream,
                         size_t mem_budget_bytes, int max_slots, int max_cells,
                         int species_per_run);
