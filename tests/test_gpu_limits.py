@@ -1,0 +1,81 @@
+"""Parity at the limits of the boundary: the largest grid a run may have
+(ECPIC_MAX_CELLS cells) and the largest species count (ECPIC_MAX_SPECIES).
+
+* 2048 cells, EC and MC, Dirichlet and periodic: field and one collisional
+  step from an identical state against the oracle, as in the small cases;
+* four species (electrons and 4 amu ions with their collisions, plus 40 amu
+  positive and negative ions without any), all of one weight (the field
+  solve sums the species' integer deposits before converting them) and of
+  different weights (each species converted on its own): field and one step
+  against the oracle."""
+import numpy as np
+import pytest
+
+from paper_2308_13092_gb300 import inputs as I
+from helpers import gpu_from_config, oracle_from_config, require_gpu
+from test_gpu_parity import RTOL, _compare, _set_same_state
+
+pytestmark = pytest.mark.gpu
+
+MAX_CELLS = 2048
+MAX_SPECIES = 4
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _field_close(g, o):
+    fg, fo = g.fields(), o.fields()
+    Es = np.max(np.abs(fo["E"]))
+    assert np.max(np.abs(fg["E"] - fo["E"])) <= RTOL * Es
+    ps = np.max(np.abs(fo["phi"])) + 1.0
+    assert np.max(np.abs(fg["phi"] - fo["phi"])) <= RTOL * ps
+
+
+def _one_step(cfg, coll):
+    g, o = gpu_from_config(cfg), oracle_from_config(cfg)
+    before = _set_same_state(cfg, g, o)
+    _field_close(g, o)
+    g.step(1)
+    g.sync()
+    o.step(1)
+    rep = _compare(cfg, g, o, before)
+    dg = g.diagnostics(profiles=False)["species"]
+    co = o.counters()["species"]
+    for s, r in rep.items():
+        assert dg[s]["candidates"] == co[s]["candidates"], (s, dg[s], co[s])
+        limit = 0 if not coll else max(2, int(2e-3 * max(1, co[s]["candidates"])))
+        assert r["n"] > 0.8 * cfg.species[s].n0, (s, r)
+        assert r["bad"] <= limit, (s, r)
+        assert r["only"] <= (0 if not coll else limit) + 2, (s, r)
+    _field_close(g, o)
+    g.close()
+    o.close()
+
+
+@pytest.mark.parametrize("scheme,bc,coll", [(I.EC, I.DIRICHLET, True), (I.MC, I.DIRICHLET, True),
+                                            (I.EC, I.PERIODIC, False), (I.MC, I.PERIODIC, False)])
+def test_max_cells_one_step(scheme, bc, coll):
+    cfg = I.ccp("max-cells", N=MAX_CELLS, n0=5e13, dt=1.0 / (400 * I.F_RF), ppc=0, v0=300.0,
+                p_mtorr=60.0, n_steps=1, seed=3, scheme=scheme, L=0.05, collisions=coll,
+                n_per_species=16 * MAX_CELLS)
+    cfg.bc = bc
+    assert cfg.N == MAX_CELLS
+    _one_step(cfg, coll)
+
+
+@pytest.mark.parametrize("weights", ["equal", "unequal"])
+@pytest.mark.parametrize("scheme", [I.EC, I.MC])
+def test_max_species_one_step(weights, scheme):
+    cfg = I.ccp("max-species", N=64, n0=5e13, dt=1.0 / (400 * I.F_RF), ppc=0, v0=300.0,
+                p_mtorr=60.0, n_steps=1, seed=5, scheme=scheme, L=0.05, collisions=True,
+                n_per_species=4000)
+    w = cfg.species[0].w
+    m40 = 40 * 1.66053906660e-27
+    f2, f3 = (1.0, 1.0) if weights == "equal" else (2.0, 0.5)
+    cfg.species.append(I.Species(I.QE, m40, w * f2, 6000, 2000, 0.05))
+    cfg.species.append(I.Species(-I.QE, m40, w * f3, 6000, 2000, 0.05))
+    assert len(cfg.species) == MAX_SPECIES
+    _one_step(cfg, True)
