@@ -138,6 +138,8 @@ int eguarded(ecpic_engine* e, F&& f) {
 // retire finished or failed runs; returns 0 or a CUDA-level error
 int retire(ecpic_engine* e, const std::vector<RunState>& st) {
   std::string err;
+  std::vector<int> done;
+  std::vector<ecpic::Diag*> outs;
   for (int s = 0; s < e->max_slots; ++s) {
     const uint64_t t = e->slot_ticket[s];
     if (!t) continue;
@@ -147,8 +149,16 @@ int retire(ecpic_engine* e, const std::vector<RunState>& st) {
     tk.psteps = r.psteps;
     const bool failed = r.status != 0;
     if (!failed && r.step < tk.steps_target) continue;
-    int rc = e->batch->diag(s, &tk.diag, &err);
-    if (rc) return efail(e, rc, err);
+    done.push_back(s);
+    outs.push_back(&tk.diag);
+  }
+  int rc = e->batch->diag_many(done, outs, &err);
+  if (rc) return efail(e, rc, err);
+  for (int s : done) {
+    const uint64_t t = e->slot_ticket[s];
+    auto& tk = e->tickets[t];
+    const RunState& r = st[s];
+    const bool failed = r.status != 0;
     e->batch->release(s);
     e->slot_ticket[s] = 0;
     tk.slot = -1;

@@ -104,24 +104,34 @@ size_t layout_bytes(const RunSpec& s) {
 
 // Pointers of every array of one run inside its device block, in a fixed
 // order: the arrays that do not depend on the particle capacities come first
-// (grid, field, deposit, accumulators, tallies, cross-section tables), so a
-// block carved again with larger capacities keeps their offsets.  Sets the
-// pointer fields of R and of the run's spc segment descriptors; returns the
-// size of that capacity-independent prefix and, in *total, of the whole.
+// (the host-built grid arrays and cross-section tables, ending at *data_end,
+// then the field, deposit, accumulators and tallies that start from zero),
+// so a block carved again with larger capacities keeps their offsets.  Sets
+// the pointer fields of R and of the run's spc segment descriptors; returns
+// the size of that capacity-independent prefix and, in *total, of the whole.
 size_t carve_layout(const RunSpec& spec, char* base, RunDev* R, SegDev* segs, int spc,
-                    size_t* total) {
+                    size_t* total, size_t* data_end = nullptr) {
   Carve cv{base};
   const size_t N = spec.edges.size() - 1, ns = spec.species.size();
+  // uploaded from the host: grid, cell-walk factors, cross-section tables
   R->x = cv.take<double>(N + 1);
   R->dx = cv.take<double>(N);
   R->V = cv.take<double>(N + 1);
   R->invV = cv.take<double>(N + 1);
   R->mcw = cv.take<double>(N + 1);
   R->cumV = cv.take<double>(N + 1);
-  R->g = cv.take<double>(N);
   R->dtdx = cv.take<float>(N);
   R->rp = cv.take<float>(N);
   R->rm = cv.take<float>(N);
+  for (size_t s = 0; s < ns; ++s) {
+    const HostSpecies& hs = spec.species[s];
+    R->sp[s].sig4 = nullptr;
+    if (!hs.procs.empty())
+      R->sp[s].sig4 = cv.take<float4>(hs.procs[0].sigma.size() * ((hs.procs.size() + 3) / 4));
+  }
+  if (data_end) *data_end = cv.off;
+  // starting from zero: field, deposit, moments, accumulators, tallies
+  R->g = cv.take<double>(N);
   R->E = cv.take<float>(N + 1);
   R->phi = cv.take<double>(N + 1);
   R->S = cv.take<unsigned long long>(ns * (N + 1));
@@ -130,12 +140,6 @@ size_t carve_layout(const RunSpec& spec, char* base, RunDev* R, SegDev* segs, in
   R->mom = nullptr;
   R->tal = cv.take<unsigned long long>(ns * (size_t)(spec.eedf_bins + spec.iedf_bins + spec.iad_bins));
   R->pw = cv.take<double>(ns * N);
-  for (size_t s = 0; s < ns; ++s) {
-    const HostSpecies& hs = spec.species[s];
-    R->sp[s].sig4 = nullptr;
-    if (!hs.procs.empty())
-      R->sp[s].sig4 = cv.take<float4>(hs.procs[0].sigma.size() * ((hs.procs.size() + 3) / 4));
-  }
   const size_t prefix = cv.off;
   for (int s = 0; s < spc; ++s) {
     SegDev& G = segs[s];
@@ -344,6 +348,16 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
     own_stream_ = true;
   }
   cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, device_);
+  // freed run blocks stay in the device's stream-ordered pool for the next
+  // admissions instead of going back to the driver at each synchronisation
+  {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device_) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   cudaMalloc(&d_runs_, sizeof(RunDev) * max_slots_);
   cudaMalloc(&d_rst_, sizeof(RunState) * max_slots_);
   cudaMalloc(&d_segs_, sizeof(SegDev) * nseg_);
@@ -371,6 +385,10 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
 Batch::~Batch() {
   cudaSetDevice(device_);
   cudaStreamSynchronize(stream_);
+  if (stage_ring_) {
+    for (int k = 0; k < kStageSlots; ++k) cudaEventDestroy(stage_ev_[k]);
+    cudaFreeHost(stage_ring_);
+  }
   invalidate_graphs();
   for (int s = 0; s < max_slots_; ++s)
     if (slot_mem_[s]) cudaFree(slot_mem_[s]);
@@ -386,6 +404,31 @@ int Batch::check(cudaError_t e, const char* what, std::string* err) {
   if (e == cudaSuccess) return ECPIC_OK;
   if (err) *err = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? ECPIC_ERR_NOMEM : ECPIC_ERR_CUDA;
+}
+
+char* Batch::stage_slot(size_t bytes, int* slot) {
+  *slot = -1;
+  if (bytes > kStageBytes) return nullptr;
+  if (!stage_ring_) {
+    if (cudaMallocHost(&stage_ring_, kStageSlots * kStageBytes) != cudaSuccess) {
+      cudaGetLastError();
+      stage_ring_ = nullptr;
+      return nullptr;  // the caller falls back to pageable memory
+    }
+    for (int k = 0; k < kStageSlots; ++k) cudaEventCreateWithFlags(&stage_ev_[k], cudaEventDisableTiming);
+  }
+  const int k = stage_next_;
+  stage_next_ = (stage_next_ + 1) % kStageSlots;
+  if (stage_used_[k]) cudaEventSynchronize(stage_ev_[k]);  // its last copy has left
+  stage_used_[k] = false;
+  *slot = k;
+  return stage_ring_ + (size_t)k * kStageBytes;
+}
+
+void Batch::stage_done(int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(stage_ev_[slot], stream_);
+  stage_used_[slot] = true;
 }
 
 BatchView Batch::view() const {
@@ -427,7 +470,21 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   if (rc) return rc;
   RunDev R{};
   size_t total = 0;
-  carve_layout(spec, static_cast<char*>(mem), &R, &h_segs_[slot * spc_], spc_, &total);
+  size_t data_end = 0;
+  const size_t prefix = carve_layout(spec, static_cast<char*>(mem), &R, &h_segs_[slot * spc_], spc_,
+                                     &total, &data_end);
+  // the host-built arrays are assembled in pinned staging memory and uploaded
+  // in one asynchronous copy; the arrays that start from zero are one memset
+  int ks = -1;
+  char* img = stage_slot(data_end, &ks);
+  std::vector<char> img_pageable;
+  if (!img) {
+    img_pageable.resize(data_end);
+    img = img_pageable.data();
+  }
+  auto put = [&](const void* dev, const void* host, size_t nbytes) {
+    std::memcpy(img + (static_cast<const char*>(dev) - static_cast<const char*>(mem)), host, nbytes);
+  };
   if (total > bytes) {
     cudaFreeAsync(mem, stream_);
     if (err) *err = "internal: run layout exceeds its block";
@@ -489,30 +546,22 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   R.eedf_dEinv = (float)(1.0 / spec.eedf_dE);
   R.iedf_dEinv = (float)(1.0 / spec.iedf_dE);
   R.iad_binv = (float)(spec.iad_bins / 90.0);
-  cudaMemsetAsync(R.tal, 0, 8 * (size_t)ns * R.tal_stride, stream_);
-  cudaMemsetAsync(R.pw, 0, 8 * (size_t)ns * N, stream_);
   R.inv_L = 1.0 / R.L;
-  cudaMemcpyAsync(d_x, spec.edges.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_dx, dx.data(), 8 * N, cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_V, V.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  put(d_x, spec.edges.data(), 8 * (N + 1));
+  put(d_dx, dx.data(), 8 * N);
+  put(d_V, V.data(), 8 * (N + 1));
   std::vector<double> invV(N + 1), mcw(N + 1, 0.5);
   for (int n = 0; n <= N; ++n) invV[n] = 1.0 / V[n];
   for (int n = 1; n < N; ++n) mcw[n] = dx[n] / (dx[n - 1] + dx[n]);
   if (spec.bc == ECPIC_PERIODIC) mcw[0] = mcw[N] = dx[0] / (dx[N - 1] + dx[0]);
-  cudaMemcpyAsync(d_invV, invV.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_mcw, mcw.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
+  put(d_invV, invV.data(), 8 * (N + 1));
+  put(d_mcw, mcw.data(), 8 * (N + 1));
   std::vector<double> cumV(N + 1, 0.0);
   for (int n = 1; n <= N; ++n) cumV[n] = cumV[n - 1] + V[n];
-  cudaMemcpyAsync(d_cumV, cumV.data(), 8 * (N + 1), cudaMemcpyHostToDevice, stream_);
-  cudaMemsetAsync(R.g, 0, 8 * N, stream_);
-  cudaMemcpyAsync(d_dtdx, dtdx.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_rp, rp.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_rm, rm.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
-  cudaMemsetAsync(R.E, 0, 4 * (N + 1), stream_);
-  cudaMemsetAsync(R.phi, 0, 8 * (N + 1), stream_);
-  cudaMemsetAsync(R.S, 0, 8 * (size_t)ns * (N + 1), stream_);
-  cudaMemsetAsync(R.momd, 0, 8 * (size_t)ns * 2 * (N + 1), stream_);
-  cudaMemsetAsync(R.acc, 0, 8 * (size_t)acc_size(ns) * (N + 1), stream_);
+  put(d_cumV, cumV.data(), 8 * (N + 1));
+  put(d_dtdx, dtdx.data(), 4 * N);
+  put(d_rp, rp.data(), 4 * N);
+  put(d_rm, rm.data(), 4 * N);
   // species
   for (int s = 0; s < ns; ++s) {
     const HostSpecies& hs = spec.species[s];
@@ -553,8 +602,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
       std::vector<float> il(nt * g4 * 4, 0.0f);
       for (int p = 0; p < D.nproc; ++p)
         for (size_t i = 0; i < nt; ++i) il[(i * g4 + p / 4) * 4 + p % 4] = hs.procs[p].sigma[i];
-      cudaMemcpyAsync(const_cast<float4*>(D.sig4), il.data(), 16 * nt * g4, cudaMemcpyHostToDevice,
-                      stream_);
+      put(D.sig4, il.data(), 16 * nt * g4);
     }
     for (int p = 0; p < D.nproc; ++p) {
       const HostProc& hp = hs.procs[p];
@@ -573,6 +621,9 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     std::memset(sst.data() + s, 0, sizeof(SegState));
     if (s < ns) sst[s].n_proc = sst[s].n_alloc = spec.n_init[s];
   }
+  cudaMemcpyAsync(mem, img, data_end, cudaMemcpyHostToDevice, stream_);
+  stage_done(ks);
+  cudaMemsetAsync(static_cast<char*>(mem) + data_end, 0, prefix - data_end, stream_);
   cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
                   stream_);
   cudaMemcpyAsync(d_sst_ + R.seg0, sst.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
@@ -1118,29 +1169,62 @@ int Batch::get_fields(int slot, double* phi, float* E, std::string* err) {
 }
 
 int Batch::diag(int slot, Diag* out, std::string* err) {
-  if (!slot_active(slot)) {
-    if (err) *err = "bad slot";
-    return ECPIC_ERR_ARG;
-  }
+  return diag_many(std::vector<int>{slot}, std::vector<Diag*>{out}, err);
+}
+
+// Every slot's state in two copies; per run its accumulators, tallies and
+// power sums, consecutive in its block, in one copy.
+int Batch::diag_many(const std::vector<int>& slots, const std::vector<Diag*>& out, std::string* err) {
+  for (int slot : slots)
+    if (!slot_active(slot)) {
+      if (err) *err = "bad slot";
+      return ECPIC_ERR_ARG;
+    }
+  if (slots.empty()) return ECPIC_OK;
   cudaSetDevice(device_);
   int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
   if (rc) return rc;
-  const RunDev& R = h_runs_[slot];
-  out->N = R.N;
-  out->ns = R.ns;
-  cudaMemcpy(&out->st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
-  std::vector<SegState> ss(spc_);
-  cudaMemcpy(ss.data(), d_sst_ + slot * spc_, sizeof(SegState) * spc_, cudaMemcpyDeviceToHost);
-  for (int s = 0; s < R.ns; ++s) out->n_live[s] = ss[s].n_proc - ss[s].n_dead;
-  out->acc.resize((size_t)acc_size(R.ns) * (R.N + 1));
-  out->tal.resize((size_t)R.ns * R.tal_stride);
-  out->pw.resize((size_t)R.ns * R.N);
-  out->eedf_c0 = R.eedf_c0;
-  out->eedf_c1 = R.eedf_c1;
-  cudaMemcpy(out->tal.data(), R.tal, 8 * out->tal.size(), cudaMemcpyDeviceToHost);
-  cudaMemcpy(out->pw.data(), R.pw, 8 * out->pw.size(), cudaMemcpyDeviceToHost);
-  return check(cudaMemcpy(out->acc.data(), R.acc, 8 * out->acc.size(), cudaMemcpyDeviceToHost),
-               "diagnostics read", err);
+  std::vector<RunState> st(max_slots_);
+  std::vector<SegState> ss(nseg_);
+  rc = check(cudaMemcpy(st.data(), d_rst_, sizeof(RunState) * max_slots_, cudaMemcpyDeviceToHost),
+             "state read", err);
+  if (rc) return rc;
+  rc = check(cudaMemcpy(ss.data(), d_sst_, sizeof(SegState) * nseg_, cudaMemcpyDeviceToHost),
+             "state read", err);
+  if (rc) return rc;
+  std::vector<char> buf;
+  for (size_t k = 0; k < slots.size(); ++k) {
+    const int slot = slots[k];
+    Diag* o = out[k];
+    const RunDev& R = h_runs_[slot];
+    o->N = R.N;
+    o->ns = R.ns;
+    o->st = st[slot];
+    for (int s = 0; s < R.ns; ++s) {
+      const SegState& q = ss[(size_t)slot * spc_ + s];
+      o->n_live[s] = q.n_proc - q.n_dead;
+    }
+    o->acc.resize((size_t)acc_size(R.ns) * (R.N + 1));
+    o->tal.resize((size_t)R.ns * R.tal_stride);
+    o->pw.resize((size_t)R.ns * R.N);
+    o->eedf_c0 = R.eedf_c0;
+    o->eedf_c1 = R.eedf_c1;
+    const char* a0 = reinterpret_cast<const char*>(R.acc);
+    const char* a1 = reinterpret_cast<const char*>(R.pw + o->pw.size());
+    const char* t0 = reinterpret_cast<const char*>(R.tal);
+    const char* p0 = reinterpret_cast<const char*>(R.pw);
+    if (!(a0 < t0 && t0 < p0 && p0 < a1)) {
+      if (err) *err = "internal: diagnostics layout";
+      return ECPIC_ERR_CUDA;
+    }
+    buf.resize((size_t)(a1 - a0));
+    rc = check(cudaMemcpy(buf.data(), a0, buf.size(), cudaMemcpyDeviceToHost), "diagnostics read", err);
+    if (rc) return rc;
+    std::memcpy(o->acc.data(), buf.data(), 8 * o->acc.size());
+    std::memcpy(o->tal.data(), buf.data() + (t0 - a0), 8 * o->tal.size());
+    std::memcpy(o->pw.data(), buf.data() + (p0 - a0), 8 * o->pw.size());
+  }
+  return ECPIC_OK;
 }
 
 int Batch::reset_averages(int slot, int sample_every, std::string* err) {

@@ -101,6 +101,8 @@ class Batch {
                     std::string* err);
   int get_fields(int slot, double* phi, float* E, std::string* err);
   int diag(int slot, Diag* out, std::string* err);
+  // several slots at once (one synchronisation, a copy per run)
+  int diag_many(const std::vector<int>& slots, const std::vector<Diag*>& out, std::string* err);
   int reset_averages(int slot, int sample_every, std::string* err);
   int set_step_end(int slot, long long step_end, std::string* err);
   // synchronise and read every slot's RunState (engine scheduling)
@@ -128,6 +130,13 @@ class Batch {
   int ensure_graphs(std::string* err);
   int choose_grid() const;
   int step_chunk(long long n, std::string* err);
+  // pinned host staging for uploads: a ring of kStageSlots buffers, each
+  // reused once the copy recorded after its last use has left (an event);
+  // nullptr (and *slot = -1) for larger images or without pinned memory
+  static constexpr int kStageSlots = 8;
+  static constexpr size_t kStageBytes = (size_t)512 << 10;
+  char* stage_slot(size_t bytes, int* slot);
+  void stage_done(int slot);  // after the copy from the slot is enqueued
   int grow_full_runs(std::string* err);
   int check(cudaError_t e, const char* what, std::string* err);
 
@@ -152,6 +161,10 @@ class Batch {
   int since_sort_ = 0;
   bool use_graphs_ = true;
   bool auto_grow_ = false;
+  char* stage_ring_ = nullptr;
+  cudaEvent_t stage_ev_[kStageSlots] = {};
+  bool stage_used_[kStageSlots] = {};
+  int stage_next_ = 0;
   double grow_at_ = 0.75;
   int pass_grid_ = 0;
   int pass_grid_override_ = 0;
