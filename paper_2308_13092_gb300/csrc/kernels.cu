@@ -640,7 +640,7 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <int KIND>
+template <int KIND, bool STAGE>
 __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {
   const SegDev& G = b.segs[s];
@@ -666,12 +666,14 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
   // the run's field staged in shared memory for the gather (after the rings)
   float* Esm = reinterpret_cast<float*>(ring + sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32));
-  {
+  // (launches whose CTAs take only an iteration or two read the field from
+  // L1/L2 instead: the staging's barrier and round trip would not pay)
+  if (STAGE) {
     const int ne = (scheme == ECPIC_SCHEME_MC || scheme == ECPIC_SCHEME_MC2) ? N + 1 : N;
     for (int q = threadIdx.x; q < ne; q += kPassBlock) Esm[q] = R->E[q];
     __syncthreads();
   }
-  const float* E = Esm;
+  const float* E = STAGE ? Esm : R->E;
   const uint32_t thr24 = SP->thr24;
   const bool mcc = stepping && SP->nproc > 0 && thr24 > 0;
   const bool heavy = SP->heavy != 0;
@@ -1146,6 +1148,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   __syncthreads();
 }
 
+template <bool STAGE>
 __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
@@ -1184,11 +1187,11 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const long long k = b.rst[G.run].step;
     const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
     if (R.scheme >= ECPIC_SCHEME_EC2)  // EC2, MC2
-      pass_piece<2>(b, s, beg, end, mode, dep, Msm, ring, sh);
+      pass_piece<2, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else if (smp)
-      pass_piece<1>(b, s, beg, end, mode, dep, Msm, ring, sh);
+      pass_piece<1, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else
-      pass_piece<0>(b, s, beg, end, mode, dep, Msm, ring, sh);
+      pass_piece<0, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
   }
 }
 
@@ -1899,16 +1902,22 @@ static void set_smem_attr(const void* fn, size_t bytes) {
 
 int pass_max_ctas_per_sm(const BatchView& b) {
   const size_t sm = pass_smem_bytes(b);
-  set_smem_attr((const void*)k_pass, sm);
+  set_smem_attr((const void*)k_pass<true>, sm);
+  set_smem_attr((const void*)k_pass<false>, sm);
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass, kPassBlock, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<true>, kPassBlock, sm);
   return n > 0 ? n : 1;
 }
 
-void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s) {
+void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s, bool stage_field) {
   const size_t sm = pass_smem_bytes(b);
-  set_smem_attr((const void*)k_pass, sm);
-  k_pass<<<grid, kPassBlock, sm, s>>>(b, mode, only);
+  if (stage_field) {
+    set_smem_attr((const void*)k_pass<true>, sm);
+    k_pass<true><<<grid, kPassBlock, sm, s>>>(b, mode, only);
+  } else {
+    set_smem_attr((const void*)k_pass<false>, sm);
+    k_pass<false><<<grid, kPassBlock, sm, s>>>(b, mode, only);
+  }
 }
 
 void launch_collide(const BatchView& b, int grid, cudaStream_t s) {

@@ -31,7 +31,10 @@ size_t pass_smem_bytes(const BatchView& b);
 size_t field_smem_bytes(const BatchView& b);
 int pass_max_ctas_per_sm(const BatchView& b);
 
-void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s);
+// stage_field: each CTA copies its run's field into shared memory first
+// (pays when a CTA runs several iterations)
+void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s,
+                 bool stage_field = true);
 void launch_collide(const BatchView& b, int grid, cudaStream_t s);
 void launch_field(const BatchView& b, int advance, int only, cudaStream_t s);
 void launch_phi(const BatchView& b, int slot, cudaStream_t s);

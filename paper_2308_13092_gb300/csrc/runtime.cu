@@ -653,7 +653,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
 
 void Batch::refresh(int slot) {
   const BatchView b = view();
-  launch_pass(b, std::max(1, std::min(choose_grid(), sm_count_ * 2)), MODE_REFRESH, slot, stream_);
+  launch_pass(b, std::max(1, std::min(choose_grid(), sm_count_ * 2)), MODE_REFRESH, slot, stream_, false);
   launch_field(b, 0, slot, stream_);
 }
 
@@ -809,12 +809,19 @@ void Batch::invalidate_graphs() {
   graph_k_ = graph_1_ = nullptr;
 }
 
+// Staging the run's field in shared memory pays only when a pass CTA runs
+// several iterations (quads per CTA >= 2 x kPassBlock).
+bool Batch::stage_field(int grid) const {
+  return grid > 0 && live_estimate() / 4 >= 2LL * kPassBlock * grid;
+}
+
 int Batch::ensure_graphs(std::string* err) {
   if (!use_graphs_) return ECPIC_OK;
   const int g = choose_grid();
-  if (graph_k_ && graph_1_ && g == pass_grid_) return ECPIC_OK;
+  if (graph_k_ && graph_1_ && g == pass_grid_ && stage_field(g) == graph_stage_) return ECPIC_OK;
   invalidate_graphs();
   pass_grid_ = g;
+  graph_stage_ = stage_field(g);
   const BatchView b = view();
   for (int which = 0; which < 2; ++which) {
     cudaGraph_t graph = nullptr;
@@ -822,7 +829,7 @@ int Batch::ensure_graphs(std::string* err) {
     if (rc) return rc;
     const int steps = which == 0 ? sort_every_ : 1;
     for (int t = 0; t < steps; ++t) {
-      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
       launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
       launch_field(b, 1, -1, stream_);
     }
@@ -874,7 +881,7 @@ int Batch::step_chunk(long long n, std::string* err) {
       rc = check(cudaGraphLaunch(graph_1_, stream_), "graph launch", err);
       if (rc) return rc;
     } else {
-      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
       launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
       launch_field(b, 1, -1, stream_);
     }
@@ -901,7 +908,7 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
   const bool each = sp && sp[0] == '1';
   for (long long t = 0; t < n && rc == ECPIC_OK; ++t) {
     cudaEventRecord(ev[0], stream_);
-    launch_pass(b, pass_grid_, MODE_STEP, -1, stream_);
+    launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
     cudaEventRecord(ev[1], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[1]), "pass kernel", err))) break;
     launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);

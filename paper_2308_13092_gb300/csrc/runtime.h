@@ -129,6 +129,7 @@ class Batch {
   void invalidate_graphs();
   int ensure_graphs(std::string* err);
   int choose_grid() const;
+  bool stage_field(int grid) const;
   int step_chunk(long long n, std::string* err);
   // pinned host staging for uploads: a ring of kStageSlots buffers, each
   // reused once the copy recorded after its last use has left (an event);
@@ -168,6 +169,7 @@ class Batch {
   double grow_at_ = 0.75;
   int pass_grid_ = 0;
   int pass_grid_override_ = 0;
+  bool graph_stage_ = true;
   cudaGraphExec_t graph_k_ = nullptr;
   cudaGraphExec_t graph_1_ = nullptr;
 };
