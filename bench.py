@@ -57,8 +57,8 @@ AUTOTUNE_STEPS = 64  # steps per autotuner trial (16 trials) before the warm-up
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "dcd485c8e616f436d2126b38e541c823f34c8d204babaa6b3d335b48637a7793",
-           "dram_bytes_per_particle_step": 568.914e6 / 14.326e6}
+TRAFFIC = {"sources_sha256": "b373cca53d44b32af2fb32008aba0fde29fac74de218251660dd60107f71cd0f",
+           "dram_bytes_per_particle_step": 569.518e6 / 14.326e6}
 
 
 def kernel_sources_sha256():
