@@ -216,7 +216,7 @@ int ecpic_set_auto_grow(ecpic_run* run, int on);
 int ecpic_profile_step(ecpic_run* run, int64_t n_steps, double* ms, int64_t* launches);
 /* Pass-kernel grid size override (0 = automatic); for tuning. */
 int ecpic_set_pass_grid(ecpic_run* run, int ctas);
-/* Autotuner (SURVEY plan: sort cadence K, particles per CTA): times the
+/* Autotuner over the sort cadence K and the particles per CTA: times the
  * graph-replayed step for each candidate pair of counting-sort cadence K in
  * {8, 16, 32, 64} and pass grid (automatic, one wave at full or half
  * occupancy, two waves), steps_per_trial steps each (at least 2K), and keeps

@@ -453,11 +453,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     if (err) *err = "slot unavailable";
     return ECPIC_ERR_STATE;
   }
-  const std::string v = validate_spec(spec);
-  if (!v.empty()) {
-    if (err) *err = v;
-    return ECPIC_ERR_ARG;
-  }
+  // the spec was validated by its caller (ecpic_init, ecpic_engine_submit)
   const int N = (int)spec.edges.size() - 1, ns = (int)spec.species.size();
   if (N > nmax_ || ns > spc_) {
     if (err) *err = "run exceeds the batch's cell or species limits";
