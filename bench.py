@@ -73,8 +73,8 @@ def kernel_sources_sha256():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=800)
-    ap.add_argument("--warmup", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=400)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--runs", type=int, default=N_RUNS)
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale")
@@ -489,6 +489,8 @@ def main():
         short = manifest(rank, args, 200)
         extras["one_by_one"] = one_by_one_block(ecpic, short, stream, local)
         extras["served"] = served_block(ecpic, stream, local, capacity=value / max(1, world))
+        extras["served_load_0.9"] = served_block(ecpic, stream, local,
+                                                 capacity=value / max(1, world), rho=0.9)
         extras["appendix_b"] = appendix_b_block(ecpic, stream, local)
         e2e = e2e_block(ecpic, short, stream, local, steps=200)
     else:
