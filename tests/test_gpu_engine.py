@@ -117,3 +117,32 @@ def test_failing_run_is_isolated():
     assert out[0]["state"] == 2 and out[2]["state"] == 2
     good, _ = _run_engine([cfgs[2]], max_slots=1)
     assert _key(good[0]["diag"]) == _key(out[2]["diag"])
+
+
+def test_runs_admitted_while_others_run_equal_alone():
+    """Continuous batching: ten runs arrive in three waves while earlier ones
+    are resident and stepping (four slots, so later runs also wait in the
+    queue for a slot to free); each finished run equals the same run alone."""
+    from paper_2308_13092_gb300 import ecpic
+    cfgs = _manifest(n=10, steps=240, seed=11)
+    eng = ecpic.Engine(max_slots=4, max_cells=1024)
+    tickets = [eng.submit(c) for c in cfgs[:3]]
+    eng.pump(50)
+    tickets += [eng.submit(c) for c in cfgs[3:7]]
+    r, q = eng.pump(50)
+    assert r == 4 and q > 0  # full slots, a queue behind them
+    tickets += [eng.submit(c) for c in cfgs[7:]]
+    for _ in range(200):
+        r, q = eng.pump(40)
+        if r == 0 and q == 0:
+            break
+    res = [eng.poll(t, diagnostics=True, profiles=True) for t in tickets]
+    eng.close()
+    assert all(o["state"] == 2 for o in res)
+    for i in (0, 4, 8, 9):
+        alone, _ = _run_engine([cfgs[i]], max_slots=1)
+        a, m = alone[0]["diag"], res[i]["diag"]
+        assert a["step"] == m["step"] == cfgs[i].n_steps
+        assert _key(a) == _key(m), i
+        for k, tol in (("density", 1e-12), ("phi", 1e-9), ("Tx", 2e-5)):
+            np.testing.assert_allclose(a[k], m[k], rtol=tol, atol=tol * np.abs(m[k]).max())
