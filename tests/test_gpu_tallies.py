@@ -2,9 +2,10 @@
 identical state (Sec. 3a diagnostics):
 
 * EEDF of the central cells and the power density J.E per cell, on a sample
-  step of a colliding discharge: EEDF counts equal up to a few bin-edge or
-  face flips (FP32 vs FP64 energies and positions), J.E within FP32 rounding
-  of the field scale;
+  step of a colliding discharge, for the linear schemes and for EC2 / MC2
+  (whose pass samples in its own instance): EEDF counts equal up to a few
+  bin-edge or face flips (FP32 vs FP64 energies and positions), J.E within
+  FP32 rounding of the field scale;
 * ion impact energy and angle at x = 0 for ions leaving through the RF
   electrode with spread energies and angles: same bins up to edge flips, and
   one count per absorbed ion."""
@@ -26,7 +27,7 @@ def _gpu():
     require_gpu()
 
 
-@pytest.mark.parametrize("scheme", [I.EC, I.MC])
+@pytest.mark.parametrize("scheme", [I.EC, I.MC, I.EC2, I.MC2])
 def test_eedf_and_power_one_step(scheme):
     cfg = _small(scheme=scheme, n=20000)
     cfg.sample_every = 1
