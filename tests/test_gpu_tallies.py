@@ -27,9 +27,11 @@ def _gpu():
     require_gpu()
 
 
-@pytest.mark.parametrize("scheme", [I.EC, I.MC, I.EC2, I.MC2])
-def test_eedf_and_power_one_step(scheme):
-    cfg = _small(scheme=scheme, n=20000)
+@pytest.mark.parametrize("scheme,grid", [(I.EC, "uniform"), (I.MC, "uniform"), (I.EC2, "uniform"),
+                                         (I.MC2, "uniform"), (I.EC, "tanh"), (I.MC, "tanh")])
+def test_eedf_and_power_one_step(scheme, grid):
+    edges = I.tanh_edges(70, 0.05, 0.05 / 400) if grid == "tanh" else None
+    cfg = _small(scheme=scheme, n=20000, edges=edges)
     cfg.sample_every = 1
     cfg.tallies = TALLY
     g, o = gpu_from_config(cfg), oracle_from_config(cfg)
@@ -52,8 +54,9 @@ def test_eedf_and_power_one_step(scheme):
         np.testing.assert_allclose(gp, op, rtol=0, atol=2e-4 * scale)
 
 
-def test_ion_impacts_one_step():
-    cfg = _small(collisions=False, n=8)
+@pytest.mark.parametrize("scheme", [I.EC, I.MC, I.EC2, I.MC2])
+def test_ion_impacts_one_step(scheme):
+    cfg = _small(scheme=scheme, collisions=False, n=8)
     cfg.sample_every = 1
     cfg.tallies = TALLY
     g, o = gpu_from_config(cfg), oracle_from_config(cfg)
