@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 
 namespace ecpic {
@@ -768,17 +769,17 @@ void Batch::release(int slot) {
   if (!slot_active(slot)) return;
   cudaSetDevice(device_);
   h_runs_[slot].active = 0;
-  upload_run(slot);
-  std::vector<SegState> z(spc_);
-  std::memset(z.data(), 0, sizeof(SegState) * spc_);
-  cudaMemcpyAsync(d_sst_ + slot * spc_, z.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
-                  stream_);
+  // descriptor inactive, segments empty, block back to the pool: all
+  // stream-ordered device-side writes, so retiring many runs needs no
+  // host round trips
+  static_assert(offsetof(RunDev, active) == 0, "RunDev::active first");
+  cudaMemsetAsync(d_runs_ + slot, 0, sizeof(int), stream_);
+  cudaMemsetAsync(d_sst_ + slot * spc_, 0, sizeof(SegState) * spc_, stream_);
   cudaFreeAsync(slot_mem_[slot], stream_);
   slot_mem_[slot] = nullptr;
   bytes_in_use_ -= slot_bytes_[slot];
   slot_bytes_[slot] = 0;
   active_[slot] = 0;
-  cudaStreamSynchronize(stream_);
 }
 
 long long Batch::live_estimate() const {
