@@ -50,7 +50,7 @@ from paper_2308_13092_gb300 import inputs as I  # noqa: E402
 BYTES_PER_PARTICLE_STEP = 40
 METRIC = "particle-steps/s"
 N_RUNS = 256
-AUTOTUNE_STEPS = 64  # steps per autotuner trial (16 trials) before the warm-up
+AUTOTUNE_STEPS = 64  # steps per autotuner trial (20 trials) before the warm-up
 
 # DRAM traffic of k_pass measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one stepping launch on the 64-run manifest, see
@@ -84,6 +84,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only (no single-run, one-by-one, served, e2e)")
     return ap.parse_args()
+
+
+def autotune_steps(per_trial, Ks=(8, 16, 32, 64), grids=5):
+    """Steps the autotuner advances the runs: per (K, grid) trial, K steps to
+    start the cadence and max(per_trial, 2K) rounded up to whole cycles."""
+    return grids * sum(K + -(-max(per_trial, 2 * K) // K) * K for K in Ks)
 
 
 def combine_ranks(ms, ps):
@@ -439,7 +445,9 @@ def main():
     ecpic.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
 
-    total = args.warmup + args.steps + 2000  # runs never retire inside the window
+    # every run outlives the autotuner's trials, the warm-up, the timed window
+    # and the profiled steps, so none retires inside them
+    total = args.warmup + args.steps + autotune_steps(AUTOTUNE_STEPS) + 64 + 256
     cfgs = manifest(rank, args, total)
     eng = ecpic.Engine(device=local, stream=stream.cuda_stream, max_slots=len(cfgs),
                        max_cells=1024)
@@ -476,6 +484,7 @@ def main():
     ps_a = eng.stats()["particle_steps"]
     prof = eng.profile(nprof)
     ps_prof = eng.stats()["particle_steps"] - ps_a
+    retired = eng.stats()["runs_finished"]  # 0: every run stepped through window and profile
     eng.close()
 
     if world > 1:
@@ -527,7 +536,8 @@ def main():
                        "tuning": "defaults" if args.no_autotune else
                                  "autotuner (sort cadence x pass grid) before the warm-up",
                        "sample_every": 40, "scheme": "EC",
-                       "arithmetic": "FP32 particles, FP64 field solve"},
+                       "arithmetic": "FP32 particles, FP64 field solve",
+                       "runs_retired_before_profile_end": retired},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "k_pass",
                          "traffic_unit": "bytes per launch (DRAM read + write)",

@@ -970,11 +970,13 @@ int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, 
     return ECPIC_ERR_ARG;
   }
   // candidates: the counting-sort cadence (8-64 steps) and the pass grid
-  // (automatic = 0, one wave at full occupancy, one at half, two waves)
+  // (automatic = 0, one wave at full occupancy, one at half, two and four
+  // waves: shorter CTAs even out the tail of the last wave)
   const int occ = pass_max_ctas_per_sm(view());
   std::vector<int> grids = {0, occ * sm_count_};
   if (occ >= 2) grids.push_back((occ / 2) * sm_count_);
   grids.push_back(2 * occ * sm_count_);
+  grids.push_back(4 * occ * sm_count_);
   const int Ks[4] = {8, 16, 32, 64};
   const int K0 = sort_every_, G0 = pass_grid_override_;
   auto psteps = [&](unsigned long long* out) -> int {

@@ -17,7 +17,9 @@ def _gpu():
 
 
 def test_run_autotune_keeps_physics_bit_identical():
-    cfg = I.config_small(seed=7)
+    # room for the discharge's growth over the ~1800 trial steps: a full
+    # species drops births in thread order, which no two runs share
+    cfg = I.with_headroom(I.config_small(seed=7), 8.0)
     a = gpu_from_config(cfg)
     b = gpu_from_config(cfg)
     t = a.autotune(16)
