@@ -531,7 +531,9 @@ def main():
             "config": {"workload": f"batched: {len(cfgs)} independent 1D3V EC-PIC RF-CCP runs "
                                    f"(seeded manifest), {n_part} initial particles, cells "
                                    f"{min(c.N for c in cfgs)}-{max(c.N for c in cfgs)}",
-                       "runs_per_gpu": len(cfgs), "l2": "inputs larger than L2 (1.5 GB state)",
+                       "runs_per_gpu": len(cfgs),
+                       "l2": f"inputs larger than L2 ({28e-9 * ps / max(1, args.steps):.1f} GB of "
+                             f"particle records live per step, 28 B each)",
                        "sort_every": sort_every, "pass_ctas": tuned["pass_ctas"] or "auto",
                        "tuning": "defaults" if args.no_autotune else
                                  "autotuner (sort cadence x pass grid) before the warm-up",
