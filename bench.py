@@ -532,8 +532,8 @@ def main():
                                    f"(seeded manifest), {n_part} initial particles, cells "
                                    f"{min(c.N for c in cfgs)}-{max(c.N for c in cfgs)}",
                        "runs_per_gpu": len(cfgs),
-                       "l2": f"inputs larger than L2 ({28e-9 * ps / max(1, args.steps):.1f} GB of "
-                             f"particle records live per step, 28 B each)",
+                       "l2": f"inputs larger than L2 ({28e-9 * ps / max(1, args.steps) / world:.1f} GB "
+                             f"of particle records live per GPU and step, 28 B each)",
                        "sort_every": sort_every, "pass_ctas": tuned["pass_ctas"] or "auto",
                        "tuning": "defaults" if args.no_autotune else
                                  "autotuner (sort cadence x pass grid) before the warm-up",
