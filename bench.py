@@ -22,9 +22,15 @@ Also reported (same JSON line):
               with p50/p99 completion latency, against one-at-a-time service;
   e2e         the batched job through the public API from host configs to
               host diagnostics.
+The timed window holds whole sort cycles: the autotuner picks the sort
+cadence K among the divisors of --steps (4..64), the warm-up runs on to a sort
+boundary, and the window's per-kernel device times come from CUDA events
+recorded inside the very graph replays that advance the runs (phase timing),
+so that pass + collision + field + sort add up to the timed step.
 For N > 1 (torchrun) each rank runs its own manifest (seed = rank); value =
 all ranks' particle-steps / max over ranks of the time.  --impl reference
-times the FP64 CPU oracle on one host core on a sample of the same workload.
+times the FP64 CPU oracle on the host cores (a thread per core, each stepping
+its own runs of a sample of the same workload).
 """
 from __future__ import annotations
 
@@ -172,71 +178,98 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_sample(cfgs, budget_s=12.0):
-    """The FP64 C oracle as it stands, one host core, over a bounded sample:
-    the first runs of the manifest for a few steps each, particle-steps/s."""
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(cfgs, threads, warmup, steps, budget_s, warm_budget_s=20.0):
+    """The FP64 C oracle as it stands, on `threads` host threads: thread t
+    steps the runs t, t + threads, ... of `cfgs` (ctypes releases the GIL
+    inside every oracle call, and runs share no state), `warmup` untimed steps,
+    then up to `steps` timed steps each, stopping once `budget_s` seconds have
+    passed.  Particle-steps count the live particles at the start of every
+    step.  Returns (particle-steps/s, particle-steps, timed steps of the
+    slowest thread, runs used, warm-up steps done)."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
     from helpers import oracle_from_config
-    t_all = 0.0
-    ps = 0
-    steps = 0
-    used = 0
-    for cfg in cfgs:
-        o = oracle_from_config(cfg)
-        used += 1
-        for _ in range(40):
-            live = sum(s["n"] for s in o.counters()["species"])
-            t0 = time.perf_counter()
-            o.step(1, allow_capacity=True)
-            t_all += time.perf_counter() - t0
-            ps += live
-            steps += 1
-        o.close()
-        if t_all > budget_s:
-            break
-    return ps / t_all, ps, used, steps
+    threads = max(1, min(threads, len(cfgs)))
+    bar = threading.Barrier(threads)
+    t0 = [0.0]
+
+    def work(t):
+        mine = [oracle_from_config(c) for c in cfgs[t::threads]]
+        tw = time.perf_counter()
+        warm = 0
+        for _ in range(warmup):
+            for o in mine:
+                o.step(1, allow_capacity=True)
+            warm += 1
+            if time.perf_counter() - tw > warm_budget_s:
+                break
+        if bar.wait() == 0:
+            t0[0] = time.perf_counter()
+        bar.wait()
+        ps, done = 0, 0
+        for _ in range(steps):
+            for o in mine:
+                ps += sum(s["n"] for s in o.counters()["species"])
+                o.step(1, allow_capacity=True)
+            done += 1
+            if time.perf_counter() - t0[0] > budget_s:
+                break
+        t1 = time.perf_counter()
+        for o in mine:
+            o.close()
+        return ps, done, t1, len(mine), warm
+
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(work, range(threads)))
+    wall = max(r[2] for r in res) - t0[0]
+    ps = sum(r[0] for r in res)
+    return (ps / wall, ps, min(r[1] for r in res), sum(r[3] for r in res),
+            min(r[4] for r in res))
+
+
+def cpu_baseline_block(cfgs, budget_s=10.0, steps=400):
+    """Oracle baseline on the manifest: all host cores (a thread each over
+    independent runs) and one core, each for about `budget_s` seconds of
+    stepping after loading."""
+    nthr = host_threads()
+    v_all, ps_all, st_all, used_all, _ = oracle_parallel(cfgs[: 2 * nthr], nthr, 0, steps, budget_s)
+    v_one, ps_one, st_one, used_one, _ = oracle_parallel(cfgs[:2], 1, 0, steps, budget_s)
+    return {"value": v_all, "unit": "particle-steps/s", "cores": nthr, "kind": "oracle",
+            "sample": f"first {used_all} runs of the batched manifest, {st_all}+ steps each "
+                      f"({ps_all:.3g} particle-steps), FP64, {nthr} host threads (one per core, "
+                      f"each stepping its own runs)",
+            "single_core": {"value": v_one, "cores": 1, "particle_steps": ps_one,
+                            "sample": f"first {used_one} runs of the manifest, {st_one} steps each"}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     cfgs = manifest(0, args, steps=args.warmup + args.steps)
-    from helpers import oracle_from_config
-    # each timed step: one step of every run of a rotating sample of the
-    # manifest (a bounded sample of the batched workload)
-    sample = cfgs[: min(8, len(cfgs))]
-    oracles = [oracle_from_config(c) for c in sample]
-    # bounded: the warm-up stops after 20 s and the timed steps after 120 s of
-    # host time, so that the default run ends within a few minutes
-    tw = time.perf_counter()
-    warm = 0
-    for _ in range(args.warmup):
-        for o in oracles:
-            o.step(1, allow_capacity=True)
-        warm += 1
-        if time.perf_counter() - tw > 20:
-            break
-    t0 = time.perf_counter()
-    ps = 0
-    done = 0
-    for _ in range(args.steps):
-        for o in oracles:
-            ps += sum(s["n"] for s in o.counters()["species"])
-            o.step(1, allow_capacity=True)
-        done += 1
-        if time.perf_counter() - t0 > 120:
-            break
-    dt = time.perf_counter() - t0
-    v = ps / dt
+    nthr = host_threads()
+    # a bounded sample: two runs per host thread, the timed steps stopping
+    # after 120 s of host time so that the default run ends within minutes
+    sample = cfgs[: min(2 * nthr, len(cfgs))]
+    v, ps, done, used, warm = oracle_parallel(sample, nthr, args.warmup, args.steps, 120.0)
+    wall_ms = ps / v * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "steps_timed": done,
             "warmup_done": warm,
-            "ms_per_step": dt * 1e3 / max(1, done), "higher_is_better": True,
+            "ms_per_step": wall_ms / max(1, done), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batched RF-CCP manifest ({len(cfgs)} runs); FP64 CPU oracle "
-                                   f"on the first {len(sample)} runs"},
-            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(sample)} runs of the batched manifest, "
-                                       f"{done} steps each after {warm} warm-up"},
+                                   f"on the first {used} runs, {nthr} host threads"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": min(nthr, used),
+                             "kind": "oracle",
+                             "sample": f"{used} runs of the batched manifest, {done} steps each "
+                                       f"after {warm} warm-up, {ps:.3g} particle-steps"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -261,10 +294,12 @@ def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
         flush.sum()
 
     with torch.cuda.stream(stream):
+        run.set_phase_timing(True)  # per-phase events inside the replayed steps
         for _ in range(warmup):
             l2_flush()
             run.step(1)
         run.sync()
+        run.phase_times()  # clear the warm-up's sums
         ps0 = run.diagnostics(profiles=False)
         n0 = sum(s["n"] for s in ps0["species"])
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -278,7 +313,7 @@ def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
         run.sync()
         n1 = sum(s["n"] for s in run.diagnostics(profiles=False)["species"])
         ms = float(sum(a.elapsed_time(b) for a, b in evs))
-        prof = run.profile_step(min(steps, 50))
+        prof = run.phase_times()  # the timed steps' own phases
     run.close()
     del flush
     v = 0.5 * (n0 + n1) * steps / (ms * 1e-3)
@@ -286,7 +321,10 @@ def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
             "workload": f"{cfg.name}: {cfg.N} uniform cells, {cfg.n_particles} particles",
             "l2": "flushed before every timed step",
             "pass_ms_avg": prof["pass_ms"] / max(1, prof["launches"][0]),
-            "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1])}
+            "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1]),
+            "collide_ms_avg": prof["collide_ms"] / max(1, prof["launches"][3]),
+            "sort_ms_per_step": prof["sort_ms"] / max(1, prof["steps"]),
+            "steps_timed": prof["steps"]}
 
 
 def one_by_one_block(ecpic, cfgs, stream, device, n_runs=12, steps=200):
@@ -430,6 +468,21 @@ def e2e_block(ecpic, cfgs, stream, device, steps):
                     "pump to completion, ecpic_engine_poll of every run's diagnostics; wall clock"}
 
 
+def sort_cadences(steps, lo=4, hi=64, want=(8, 16, 32, 64)):
+    """Sort cadences for the autotuner that divide the timed window, so that
+    it holds whole sort cycles: the divisors of `steps` in [lo, hi], at most
+    one per wanted value (the nearest on a log scale)."""
+    divs = [k for k in range(lo, min(hi, steps) + 1) if steps % k == 0]
+    if not divs:
+        return [steps] if steps <= 4096 else [hi]
+    pick = []
+    for w in want:
+        k = min(divs, key=lambda d: abs(np.log(d / w)))
+        if k not in pick:
+            pick.append(k)
+    return sorted(pick)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -445,9 +498,11 @@ def main():
     ecpic.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
 
-    # every run outlives the autotuner's trials, the warm-up, the timed window
-    # and the profiled steps, so none retires inside them
-    total = args.warmup + args.steps + autotune_steps(AUTOTUNE_STEPS) + 64 + 256
+    ks = sort_cadences(args.steps)
+    # every run outlives the autotuner's trials, the warm-up (with its
+    # alignment to a sort boundary), the timed window and the plain-graph
+    # check window, so none retires inside them
+    total = (args.warmup + max(ks) + 2 * args.steps + autotune_steps(AUTOTUNE_STEPS, Ks=ks) + 256)
     cfgs = manifest(rank, args, total)
     eng = ecpic.Engine(device=local, stream=stream.cuda_stream, max_slots=len(cfgs),
                        max_cells=1024)
@@ -457,12 +512,21 @@ def main():
     # sort cadence and pass grid from the autotuner (its trials are steps of
     # the same runs, before the warm-up)
     if args.no_autotune:
-        tuned = {"sort_every": 16, "pass_ctas": 0}
-        eng.tune(0, 16)
+        K = ks[0] if 16 not in ks else 16
+        tuned = {"sort_every": K, "pass_ctas": 0}
+        eng.tune(0, K)
     else:
-        tuned = eng.autotune(AUTOTUNE_STEPS)
-    eng_sort_every = tuned["sort_every"]
+        tuned = eng.autotune(AUTOTUNE_STEPS, ks=ks)
+    K = tuned["sort_every"]
+    # phase timing on before the warm-up, so that its graphs are built there
+    eng.set_phase_timing(True)
     eng.pump(args.warmup)
+    since = eng.sort_state()["since_sort"]
+    align = (K - since) % K
+    if align:
+        eng.pump(align)  # on to a sort boundary
+    assert eng.sort_state()["since_sort"] == 0
+    eng.phase_times()  # clear the warm-up's sums
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ps0 = eng.stats()["particle_steps"]
     if world > 1:
@@ -478,13 +542,24 @@ def main():
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     ps = eng.stats()["particle_steps"] - ps0
-
-    # per-kernel device time, same workload, same stream
-    nprof = min(args.steps, 64)
-    ps_a = eng.stats()["particle_steps"]
-    prof = eng.profile(nprof)
-    ps_prof = eng.stats()["particle_steps"] - ps_a
-    retired = eng.stats()["runs_finished"]  # 0: every run stepped through window and profile
+    ph = eng.phase_times()  # the window's own replays
+    sorts = ph["sorts"]
+    assert ph["steps"] == args.steps, ph
+    assert sorts == args.steps // K and args.steps % K == 0, (sorts, args.steps, K)
+    # the same window length with the plain graphs (no phase events), as a
+    # check that the events do not slow the steps
+    eng.set_phase_timing(False)
+    eng.pump(K)  # rebuild the plain graphs outside the check window
+    assert eng.sort_state()["since_sort"] == 0
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ps2 = eng.stats()["particle_steps"]
+    ev2.record(stream)
+    eng.pump(args.steps)
+    ev3.record(stream)
+    ev3.synchronize()
+    ms_plain = ev2.elapsed_time(ev3)
+    ps_plain = eng.stats()["particle_steps"] - ps2
+    retired = eng.stats()["runs_finished"]  # 0: every run stepped through both windows
     eng.close()
 
     if world > 1:
@@ -492,14 +567,17 @@ def main():
 
     value = ps / (ms * 1e-3)
     hbm, peak_kind = peaks()
-    pass_ms = prof["pass_ms"] / max(1, prof["launches"][0])
-    bytes_per_launch = BYTES_PER_PARTICLE_STEP * ps_prof / max(1, nprof)
+    nst = max(1, ph["launches"][0])
+    pass_ms = ph["pass_ms"] / nst
+    field_ms = ph["field_ms"] / max(1, ph["launches"][1])
+    collide_ms = ph["collide_ms"] / max(1, ph["launches"][3])
+    sort_ms_step = ph["sort_ms"] / max(1, ph["steps"])
+    phase_sum = pass_ms + field_ms + collide_ms + sort_ms_step
+    bytes_per_launch = BYTES_PER_PARTICLE_STEP * ps / max(1, args.steps) / world
     achieved = bytes_per_launch / (pass_ms * 1e-3) / 1e9
-    launches_per_step = sum(prof["launches"]) / max(1, nprof)
     traffic = None
     if kernel_sources_sha256() == TRAFFIC["sources_sha256"]:
-        traffic = TRAFFIC["dram_bytes_per_particle_step"] * ps_prof / max(1, nprof)
-    sort_every = eng_sort_every
+        traffic = TRAFFIC["dram_bytes_per_particle_step"] * ps / max(1, args.steps) / world
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -516,10 +594,7 @@ def main():
         e2e = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, psamp, used, st = oracle_sample(cfgs)
-        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {used} runs of the batched manifest, 40 steps each "
-                         f"({psamp:.3g} particle-steps), FP64, one host core"}
+        cpu = cpu_baseline_block(cfgs)
 
     if rank == 0:
         n_part = sum(c.n_particles for c in cfgs)
@@ -534,26 +609,34 @@ def main():
                        "runs_per_gpu": len(cfgs),
                        "l2": f"inputs larger than L2 ({28e-9 * ps / max(1, args.steps) / world:.1f} GB "
                              f"of particle records live per GPU and step, 28 B each)",
-                       "sort_every": sort_every, "pass_ctas": tuned["pass_ctas"] or "auto",
+                       "sort_every": K, "sort_cadences_tried": ks,
+                       "sorts_in_window": sorts,
+                       "warmup_steps_run": args.warmup + align,
+                       "pass_ctas": tuned["pass_ctas"] or "auto",
                        "tuning": "defaults" if args.no_autotune else
                                  "autotuner (sort cadence x pass grid) before the warm-up",
                        "sample_every": 40, "scheme": "EC",
                        "arithmetic": "FP32 particles, FP64 field solve",
-                       "runs_retired_before_profile_end": retired},
+                       "runs_retired_before_window_end": retired},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "kernel": "k_pass",
                          "traffic_unit": "bytes per launch (DRAM read + write)",
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
-                         "pass_ms_avg": pass_ms,
-                         "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1]),
-                         "collide_ms_avg": prof["collide_ms"] / max(1, prof["launches"][3]),
-                         "sort_ms_per_step": prof["sort_ms"] / max(1, nprof),
-                         "pass_share": prof["pass_ms"] / max(1e-9, prof["pass_ms"] + prof["field_ms"]
-                                                             + prof["sort_ms"] + prof["collide_ms"])},
+                         "timing": "CUDA events recorded by the timed window's own graph "
+                                   "replays after every kernel phase",
+                         "pass_ms_avg": pass_ms, "field_ms_avg": field_ms,
+                         "collide_ms_avg": collide_ms, "sort_ms_per_step": sort_ms_step,
+                         "phase_sum_ms_per_step": phase_sum,
+                         "phase_sum_over_step": phase_sum / (ms / args.steps),
+                         "pass_share": pass_ms / phase_sum},
+            "plain_graph_check": {"ms_per_step": ms_plain / args.steps,
+                                  "value": ps_plain / (ms_plain * 1e-3),
+                                  "what": "the next window of the same length replayed from "
+                                          "the step graphs without phase events"},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches": int(sum(ph["launches"])),
             "clocks": ck,
         }
         line.update(extras)

@@ -16,9 +16,13 @@
  *    handle that allocated it and released by its destroy call.
  *  - Pointers documented as "device" must point to memory of the handle's
  *    CUDA device; every other pointer is host memory.
- *  - Work is queued on the stream given at creation (NULL = the legacy
- *    default stream); calls marked "async" return before the GPU finishes and
- *    report device-side errors at the next ecpic_sync().
+ *  - Work is queued on the stream given at creation.  With NULL the handle
+ *    creates its own non-blocking stream (the step graphs cannot be captured
+ *    on the legacy default stream): work the caller queues on the legacy
+ *    stream is not ordered with the library's, so order it through
+ *    ecpic_sync() (or pass a stream of your own).  Calls marked "async"
+ *    return before the GPU finishes and report device-side errors at the
+ *    next ecpic_sync().
  *  - One handle must not be used from two host threads at once.
  *  - Calling out of order (for example step before init) returns
  *    ECPIC_ERR_STATE.
@@ -226,6 +230,28 @@ int ecpic_set_pass_grid(ecpic_run* run, int ctas);
  * chosen grid (0 = automatic) and its ns per particle-step.  Synchronises. */
 int ecpic_autotune(ecpic_run* run, int64_t steps_per_trial, int* sort_every, int* pass_ctas,
                    double* ns_per_particle_step);
+/* As ecpic_autotune with the sort cadences to try given explicitly: ks[0..n_ks)
+ * (1..4096 each, 1 <= n_ks <= 64), e.g. the divisors of a measurement window
+ * so that the window holds whole sort cycles. */
+int ecpic_autotune_ks(ecpic_run* run, int64_t steps_per_trial, const int* ks, int n_ks,
+                      int* sort_every, int* pass_ctas, double* ns_per_particle_step);
+/* Measurement of the stepping itself.  on = 1 captures the step graphs again
+ * with an event-record node after every kernel phase (two instances of each
+ * graph alternate, so that the host reads one while the other runs); every
+ * step that ecpic_step advances from then on adds the device time of its
+ * phases (CUDA events on the run's stream) to running sums.  The sums thus
+ * come from the very replays that advance the run, not from a separate
+ * profiling pass.  on = 0 restores the plain graphs (the sums are kept). */
+int ecpic_set_phase_timing(ecpic_run* run, int on);
+/* Read and clear the phase sums (waits for the timed steps): ms[0..3] = the
+ * particle pass, the field solve, the counting sort, the real-collision
+ * kernel; launches[0..3] their launch counts (a sort is four launches);
+ * *steps and *sorts timed.  Any pointer may be NULL. */
+int ecpic_phase_times(ecpic_run* run, double* ms, int64_t* launches, int64_t* steps,
+                      int64_t* sorts);
+/* The counting-sort cadence in steps and the steps taken since the last
+ * sort (0: the next step starts a sort cycle).  Either pointer may be NULL. */
+int ecpic_sort_state(ecpic_run* run, int* sort_every, int* since_sort);
 
 /* ------------------------------------------------------------------ */
 /* Batched and served runs.  An engine keeps up to max_slots independent
@@ -316,6 +342,14 @@ int ecpic_engine_autotune(ecpic_engine* eng, int64_t steps_per_trial, int* sort_
  * ecpic_profile_step: ms[0..3], launches[0..3]); synchronises.  No admission
  * or retirement. */
 int ecpic_engine_profile(ecpic_engine* eng, int64_t n_steps, double* ms, int64_t* launches);
+/* The engine's counterparts of ecpic_autotune_ks, ecpic_set_phase_timing,
+ * ecpic_phase_times and ecpic_sort_state, over its resident runs. */
+int ecpic_engine_autotune_ks(ecpic_engine* eng, int64_t steps_per_trial, const int* ks, int n_ks,
+                             int* sort_every, int* pass_ctas, double* ns_per_particle_step);
+int ecpic_engine_set_phase_timing(ecpic_engine* eng, int on);
+int ecpic_engine_phase_times(ecpic_engine* eng, double* ms, int64_t* launches, int64_t* steps,
+                             int64_t* sorts);
+int ecpic_engine_sort_state(ecpic_engine* eng, int* sort_every, int* since_sort);
 
 /* ------------------------------------------------------------------ */
 /* Doubling non-uniform grid (Sec. 3c rules 1-4): buffers of dx_min cells of
@@ -376,7 +410,13 @@ int ecpic_philox_device(int64_t n, const uint32_t* d_ctr, const uint32_t* d_key,
  *
  * Set-up: the first call on each device (with that device current) looks up
  * the scratch array's address and keeps it; if you capture streams, make a
- * first call on each device before any capture begins.
+ * first call on each device before any capture begins.  That first lookup
+ * also loads the library's device code, which commits the 4 MiB array (and
+ * the code) in device memory: make the first call -- a call with n == 0 does
+ * only this set-up -- before handing the device's free memory to a pool.  The
+ * address is kept for the life of the process: after cudaDeviceReset (or
+ * anything else that destroys the device's primary context) the kept address
+ * is stale and this entry point must not be called again in that process.
  *
  * Races: all calls on a device share the one scratch array.  Calls that may
  * overlap -- on different streams or from different host threads without

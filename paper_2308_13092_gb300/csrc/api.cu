@@ -404,6 +404,49 @@ int ecpic_autotune(ecpic_run* r, int64_t steps_per_trial, int* sort_every, int* 
   return rc ? fail(r, rc, err) : ECPIC_OK;
 }
 
+int ecpic_autotune_ks(ecpic_run* r, int64_t steps_per_trial, const int* ks, int n_ks, int* sort_every,
+                      int* pass_ctas, double* ns_per_particle_step) {
+  if (!r || steps_per_trial < 1 || n_ks < 1 || n_ks > 64 || !ks) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  return guarded(r, [&]() -> int {
+    std::string err;
+    const std::vector<int> K(ks, ks + n_ks);
+    const int rc = r->batch->autotune(steps_per_trial, sort_every, pass_ctas, ns_per_particle_step,
+                                      &err, K);
+    if (!rc && sort_every) r->sort_every = *sort_every;
+    return rc ? fail(r, rc, err) : ECPIC_OK;
+  });
+}
+
+int ecpic_set_phase_timing(ecpic_run* r, int on) {
+  if (!r || (on != 0 && on != 1)) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  std::string err;
+  const int rc = r->batch->set_phase_timing(on == 1, &err);
+  return rc ? fail(r, rc, err) : ECPIC_OK;
+}
+
+int ecpic_phase_times(ecpic_run* r, double* ms, int64_t* launches, int64_t* steps, int64_t* sorts) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  std::string err;
+  long long l[4] = {0, 0, 0, 0}, st = 0, so = 0;
+  const int rc = r->batch->phase_times(ms, l, &st, &so, &err);
+  if (launches)
+    for (int i = 0; i < 4; ++i) launches[i] = l[i];
+  if (steps) *steps = st;
+  if (sorts) *sorts = so;
+  return rc ? fail(r, rc, err) : ECPIC_OK;
+}
+
+int ecpic_sort_state(ecpic_run* r, int* sort_every, int* since_sort) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  if (sort_every) *sort_every = r->batch->sort_every();
+  if (since_sort) *since_sort = r->batch->since_sort();
+  return ECPIC_OK;
+}
+
 int ecpic_set_pass_grid(ecpic_run* r, int ctas) {
   if (!r || ctas < 0) return ECPIC_ERR_ARG;
   if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");

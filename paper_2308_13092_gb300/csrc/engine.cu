@@ -362,6 +362,45 @@ int ecpic_engine_autotune(ecpic_engine* e, int64_t steps_per_trial, int* sort_ev
   return rc ? efail(e, rc, err) : ECPIC_OK;
 }
 
+int ecpic_engine_autotune_ks(ecpic_engine* e, int64_t steps_per_trial, const int* ks, int n_ks,
+                             int* sort_every, int* pass_ctas, double* ns_per_particle_step) {
+  if (!e || steps_per_trial < 1 || n_ks < 1 || n_ks > 64 || !ks) return ECPIC_ERR_ARG;
+  return eguarded(e, [&]() -> int {
+    std::string err;
+    const std::vector<int> K(ks, ks + n_ks);
+    const int rc = e->batch->autotune(steps_per_trial, sort_every, pass_ctas, ns_per_particle_step,
+                                      &err, K);
+    return rc ? efail(e, rc, err) : ECPIC_OK;
+  });
+}
+
+int ecpic_engine_set_phase_timing(ecpic_engine* e, int on) {
+  if (!e || (on != 0 && on != 1)) return ECPIC_ERR_ARG;
+  std::string err;
+  const int rc = e->batch->set_phase_timing(on == 1, &err);
+  return rc ? efail(e, rc, err) : ECPIC_OK;
+}
+
+int ecpic_engine_phase_times(ecpic_engine* e, double* ms, int64_t* launches, int64_t* steps,
+                             int64_t* sorts) {
+  if (!e) return ECPIC_ERR_ARG;
+  std::string err;
+  long long l[4] = {0, 0, 0, 0}, st = 0, so = 0;
+  const int rc = e->batch->phase_times(ms, l, &st, &so, &err);
+  if (launches)
+    for (int i = 0; i < 4; ++i) launches[i] = l[i];
+  if (steps) *steps = st;
+  if (sorts) *sorts = so;
+  return rc ? efail(e, rc, err) : ECPIC_OK;
+}
+
+int ecpic_engine_sort_state(ecpic_engine* e, int* sort_every, int* since_sort) {
+  if (!e) return ECPIC_ERR_ARG;
+  if (sort_every) *sort_every = e->batch->sort_every();
+  if (since_sort) *since_sort = e->batch->since_sort();
+  return ECPIC_OK;
+}
+
 int ecpic_engine_tune(ecpic_engine* e, int pass_ctas, int sort_every) {
   if (!e || pass_ctas < 0 || sort_every < 1) return ECPIC_ERR_ARG;
   e->batch->set_pass_grid(pass_ctas);

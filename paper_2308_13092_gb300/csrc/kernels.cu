@@ -691,7 +691,11 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const unsigned lt_mask = (1u << lane) - 1u;
 
   int my_lo = INT_MAX, my_hi = -1;
-  float ke = 0.0f;
+  // kinetic energy of sample steps: each quad's four terms in FP32, the
+  // quads summed in FP64 (one FP64 add per four particles: FP64 is slow on
+  // this part), so the error per particle is a few FP32 roundings whatever
+  // the number of particles a thread handles
+  double ke = 0.0;
   unsigned ncand = 0, nlive = 0, nabs_l = 0, nabs_r = 0, nnan = 0, nimp_lost = 0;
   // this warp's candidate ring: index, Philox word A.y, |g|^2 or vx
   int* qi = reinterpret_cast<int*>(ring) + (threadIdx.x >> 5) * (3 * kRing);
@@ -824,16 +828,18 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
             Ei[j] = e0 + f[j] * (e1 - e0);
           }
         }
+        float keq = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float vnew = v[j] + qm_dt * Ei[j];
           if (sample && c[j] >= 0) {
-            ke += v[j] * vnew + yz[j];
+            keq += v[j] * vnew + yz[j];
             // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
             atomicAdd(Psm + c[j], (v[j] + vnew) * Ei[j]);
           }
           v[j] = vnew;
         }
+        if (sample) ke += (double)keq;
         // Philox block A of all four: independent chains the scheduler
         // interleaves; A.x decides the candidate, A.y selects the process
         uint32_t r0[4] = {0u, 0u, 0u, 0u}, ry[4] = {0u, 0u, 0u, 0u};
@@ -1095,7 +1101,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
     }
   }
   if (sample) {
-    const double kes = block_sum((double)ke, sh.dsm);
+    const double kes = block_sum(ke, sh.dsm);
     if (threadIdx.x == 0) atomicAdd(&st->ke_acc[sp], 0.5 * SP->m * SP->w * kes);
   }
   __syncthreads();

@@ -33,7 +33,9 @@ static_assert((size_t)(ECPIC_NOALLOC_MAX_CELLS + 1) <= kNaWords, "scratch must h
 // to start at zero and no call clears it.
 static __device__ __align__(256) unsigned long long g_na_scratch[kNaWords];
 
-// scratch address per device, looked up at the first call on that device
+// scratch address per device, looked up at the first call on that device and
+// kept for the life of the process (a device reset makes it stale: see the
+// header)
 std::mutex g_na_mu;
 void* g_na_ptr[kMaxDevices] = {};
 
@@ -114,7 +116,9 @@ extern "C" int ecpic_deposit_device_noalloc(int N, int64_t n, const int32_t* d_c
   if (nrows > kNaMaxRows) nrows = kNaMaxRows;
   if (nrows > per_row) nrows = per_row;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t smem = sizeof(unsigned long long) * (size_t)(N + 1);  // <= 16 KiB
+  // one row of N + 1 sums: at most 8 x 2049 = 16,392 B (N = 2048), within the
+  // 48 KiB a launch gets without an opt-in
+  const size_t smem = sizeof(unsigned long long) * (size_t)(N + 1);
   k_na_rows<<<(unsigned)nrows, kNaBlock, smem, s>>>(N, (long long)n, d_cell, d_xi, rows);
   k_na_sum<<<(unsigned)((N + 1 + kNaBlock - 1) / kNaBlock), kNaBlock, 0, s>>>(
       N, (int)nrows, rows, reinterpret_cast<unsigned long long*>(d_S));

@@ -768,12 +768,12 @@ int Batch::grow_full_runs(std::string* err) {
 void Batch::release(int slot) {
   if (!slot_active(slot)) return;
   cudaSetDevice(device_);
-  h_runs_[slot].active = 0;
-  // descriptor inactive, segments empty, block back to the pool: all
-  // stream-ordered device-side writes, so retiring many runs needs no
-  // host round trips
+  h_runs_[slot] = RunDev{};
+  // descriptor cleared (inactive, and no pointer into the freed block left
+  // behind), segments empty, block back to the pool: all stream-ordered
+  // device-side writes, so retiring many runs needs no host round trips
   static_assert(offsetof(RunDev, active) == 0, "RunDev::active first");
-  cudaMemsetAsync(d_runs_ + slot, 0, sizeof(int), stream_);
+  cudaMemsetAsync(d_runs_ + slot, 0, sizeof(RunDev), stream_);
   cudaMemsetAsync(d_sst_ + slot * spc_, 0, sizeof(SegState) * spc_, stream_);
   cudaFreeAsync(slot_mem_[slot], stream_);
   slot_mem_[slot] = nullptr;
@@ -804,6 +804,133 @@ void Batch::invalidate_graphs() {
   if (graph_k_) cudaGraphExecDestroy(graph_k_);
   if (graph_1_) cudaGraphExecDestroy(graph_1_);
   graph_k_ = graph_1_ = nullptr;
+  // timed instances: their pending sums are kept before they go
+  for (int i = 0; i < 2; ++i) {
+    for (TimedGraph* tg : {&tk_[i], &t1_[i], &ts_[i]}) {
+      harvest(tg, nullptr);
+      drop_timed(tg);
+    }
+  }
+  tk_next_ = t1_next_ = ts_next_ = 0;
+}
+
+void Batch::drop_timed(TimedGraph* tg) {
+  if (tg->exec) cudaGraphExecDestroy(tg->exec);
+  for (cudaEvent_t e : tg->ev) cudaEventDestroy(e);
+  tg->exec = nullptr;
+  tg->ev.clear();
+  tg->ph.clear();
+  tg->pending = false;
+}
+
+// Adds the phase intervals of a launched timed graph to the sums once its
+// last event has completed (waits for it).
+int Batch::harvest(TimedGraph* tg, std::string* err) {
+  if (!tg->pending) return ECPIC_OK;
+  tg->pending = false;
+  int rc = check(cudaEventSynchronize(tg->ev.back()), "phase timing", err);
+  if (rc) return rc;
+  for (size_t i = 0; i + 1 < tg->ev.size(); ++i) {
+    float ms = 0.0f;
+    rc = check(cudaEventElapsedTime(&ms, tg->ev[i], tg->ev[i + 1]), "phase timing", err);
+    if (rc) return rc;
+    const int p = tg->ph[i];
+    tsum_[p] += ms;
+    tcnt_[p] += (p == 2) ? 4 : 1;  // the sort is four launches
+    if (p == 0) ++tsteps_;
+    if (p == 2) ++tsorts_;
+  }
+  return ECPIC_OK;
+}
+
+// Captures `steps` steps (and a counting sort after them when `sort`) into a
+// graph.  With tg, an event-record node follows every phase: ev[0] before the
+// first launch, then pass (0), collision (3), field (1) per step, sort (2).
+int Batch::capture(int steps, bool sort, TimedGraph* tg, cudaGraphExec_t* out, std::string* err) {
+  const BatchView b = view();
+  auto mark = [&](int phase) -> int {
+    cudaEvent_t e = nullptr;
+    int rc = check(cudaEventCreate(&e), "phase event", err);
+    if (rc) return rc;
+    tg->ev.push_back(e);
+    if (phase >= 0) tg->ph.push_back(phase);
+    return check(cudaEventRecordWithFlags(e, stream_, cudaEventRecordExternal), "phase event", err);
+  };
+  cudaGraph_t graph = nullptr;
+  int rc = check(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "capture", err);
+  if (rc) return rc;
+  if (tg) rc = mark(-1);
+  for (int t = 0; t < steps && rc == ECPIC_OK; ++t) {
+    launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
+    if (tg && (rc = mark(0))) break;
+    launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
+    if (tg && (rc = mark(3))) break;
+    launch_field(b, 1, -1, stream_);
+    if (tg && (rc = mark(1))) break;
+  }
+  if (sort && rc == ECPIC_OK) {
+    launch_sort(b, pass_grid_, stream_);
+    if (tg) rc = mark(2);
+  }
+  const int rc_end = check(cudaStreamEndCapture(stream_, &graph), "capture end", err);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (rc_end) return rc_end;
+  cudaGraphExec_t exec = nullptr;
+  rc = check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate", err);
+  cudaGraphDestroy(graph);
+  if (rc) return rc;
+  if (tg) tg->exec = exec;
+  else *out = exec;
+  return ECPIC_OK;
+}
+
+// Launches the next of two alternating timed instances, first reading the
+// events of its previous launch (the other instance keeps the GPU busy).
+int Batch::launch_timed(TimedGraph* pair, int* next, std::string* err) {
+  TimedGraph& tg = pair[*next];
+  int rc = harvest(&tg, err);
+  if (rc) return rc;
+  rc = check(cudaGraphLaunch(tg.exec, stream_), "graph launch", err);
+  if (rc) return rc;
+  tg.pending = true;
+  *next ^= 1;
+  return ECPIC_OK;
+}
+
+int Batch::set_phase_timing(bool on, std::string* err) {
+  if (on == timing_) return ECPIC_OK;
+  if (on && !use_graphs_) {
+    if (err) *err = "phase timing needs the step graphs";
+    return ECPIC_ERR_STATE;
+  }
+  cudaSetDevice(device_);
+  invalidate_graphs();
+  timing_ = on;
+  return ECPIC_OK;
+}
+
+int Batch::phase_times(double* ms, long long* launches, long long* steps, long long* sorts,
+                       std::string* err) {
+  cudaSetDevice(device_);
+  for (int i = 0; i < 2; ++i) {
+    int rc = harvest(&tk_[i], err);
+    if (!rc) rc = harvest(&t1_[i], err);
+    if (!rc) rc = harvest(&ts_[i], err);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < 4; ++i) {
+    if (ms) ms[i] = tsum_[i];
+    if (launches) launches[i] = tcnt_[i];
+    tsum_[i] = 0.0;
+    tcnt_[i] = 0;
+  }
+  if (steps) *steps = tsteps_;
+  if (sorts) *sorts = tsorts_;
+  tsteps_ = tsorts_ = 0;
+  return ECPIC_OK;
 }
 
 // Staging the run's field in shared memory pays only when a pass CTA runs
@@ -815,31 +942,26 @@ bool Batch::stage_field(int grid) const {
 int Batch::ensure_graphs(std::string* err) {
   if (!use_graphs_) return ECPIC_OK;
   const int g = choose_grid();
-  if (graph_k_ && graph_1_ && g == pass_grid_ && stage_field(g) == graph_stage_) return ECPIC_OK;
+  const bool built = timing_ ? (tk_[0].exec && tk_[1].exec && t1_[0].exec && t1_[1].exec &&
+                                ts_[0].exec && ts_[1].exec)
+                             : (graph_k_ && graph_1_);
+  if (built && g == pass_grid_ && stage_field(g) == graph_stage_) return ECPIC_OK;
   invalidate_graphs();
   pass_grid_ = g;
   graph_stage_ = stage_field(g);
-  const BatchView b = view();
-  for (int which = 0; which < 2; ++which) {
-    cudaGraph_t graph = nullptr;
-    int rc = check(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal), "capture", err);
-    if (rc) return rc;
-    const int steps = which == 0 ? sort_every_ : 1;
-    for (int t = 0; t < steps; ++t) {
-      launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
-      launch_collide(b, std::min(pass_grid_, 2 * sm_count_), stream_);
-      launch_field(b, 1, -1, stream_);
+  int rc = ECPIC_OK;
+  if (timing_) {
+    for (int i = 0; i < 2 && rc == ECPIC_OK; ++i) {
+      rc = capture(sort_every_, true, &tk_[i], nullptr, err);
+      if (!rc) rc = capture(1, false, &t1_[i], nullptr, err);
+      if (!rc) rc = capture(0, true, &ts_[i], nullptr, err);
     }
-    if (which == 0) launch_sort(b, pass_grid_, stream_);
-    rc = check(cudaStreamEndCapture(stream_, &graph), "capture end", err);
-    if (rc) return rc;
-    cudaGraphExec_t exec = nullptr;
-    rc = check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate", err);
-    cudaGraphDestroy(graph);
-    if (rc) return rc;
-    (which == 0 ? graph_k_ : graph_1_) = exec;
+  } else {
+    rc = capture(sort_every_, true, nullptr, &graph_k_, err);
+    if (!rc) rc = capture(1, false, nullptr, &graph_1_, err);
   }
-  return ECPIC_OK;
+  if (rc) invalidate_graphs();
+  return rc;
 }
 
 int Batch::step(long long n, std::string* err) {
@@ -869,13 +991,15 @@ int Batch::step_chunk(long long n, std::string* err) {
   if (!use_graphs_) pass_grid_ = choose_grid();
   while (n > 0) {
     if (use_graphs_ && since_sort_ == 0 && n >= sort_every_) {
-      rc = check(cudaGraphLaunch(graph_k_, stream_), "graph launch", err);
+      rc = timing_ ? launch_timed(tk_, &tk_next_, err)
+                   : check(cudaGraphLaunch(graph_k_, stream_), "graph launch", err);
       if (rc) return rc;
       n -= sort_every_;
       continue;
     }
     if (use_graphs_) {
-      rc = check(cudaGraphLaunch(graph_1_, stream_), "graph launch", err);
+      rc = timing_ ? launch_timed(t1_, &t1_next_, err)
+                   : check(cudaGraphLaunch(graph_1_, stream_), "graph launch", err);
       if (rc) return rc;
     } else {
       launch_pass(b, pass_grid_, MODE_STEP, -1, stream_, stage_field(pass_grid_));
@@ -884,7 +1008,12 @@ int Batch::step_chunk(long long n, std::string* err) {
     }
     --n;
     if (++since_sort_ >= sort_every_) {
-      launch_sort(b, pass_grid_, stream_);
+      if (use_graphs_ && timing_) {
+        rc = launch_timed(ts_, &ts_next_, err);
+        if (rc) return rc;
+      } else {
+        launch_sort(b, pass_grid_, stream_);
+      }
       since_sort_ = 0;
     }
   }
@@ -963,7 +1092,8 @@ int Batch::sort_now(std::string* err) {
   return check(cudaGetLastError(), "sort", err);
 }
 
-int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, std::string* err) {
+int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, std::string* err,
+                    const std::vector<int>& Ks_in) {
   cudaSetDevice(device_);
   if (steps < 1) {
     if (err) *err = "steps per trial must be positive";
@@ -977,7 +1107,13 @@ int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, 
   if (occ >= 2) grids.push_back((occ / 2) * sm_count_);
   grids.push_back(2 * occ * sm_count_);
   grids.push_back(4 * occ * sm_count_);
-  const int Ks[4] = {8, 16, 32, 64};
+  std::vector<int> Ks = Ks_in;
+  if (Ks.empty()) Ks = {8, 16, 32, 64};
+  for (int K : Ks)
+    if (K < 1 || K > 4096) {
+      if (err) *err = "sort cadence candidates must lie in 1..4096";
+      return ECPIC_ERR_ARG;
+    }
   const int K0 = sort_every_, G0 = pass_grid_override_;
   auto psteps = [&](unsigned long long* out) -> int {
     std::vector<RunState> st;

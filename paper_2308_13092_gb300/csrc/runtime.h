@@ -90,6 +90,16 @@ class Batch {
     grow_at_ = at;
   }
   int profile_step(long long n, double* ms, long long* launches, std::string* err);
+  // Phase timing of the replayed steps: with it on, the step graphs carry an
+  // event-record node after every kernel phase (two instances of each graph
+  // alternate, so that one is read while the other runs) and every step the
+  // batch advances adds its phases' device times to the sums; phase_times
+  // waits for the pending graphs, returns the sums (ms and launches per phase:
+  // pass, field, sort, collide; steps and sorts) and clears them.
+  int set_phase_timing(bool on, std::string* err);
+  int phase_times(double* ms, long long* launches, long long* steps, long long* sorts,
+                  std::string* err);
+  int since_sort() const { return since_sort_; }
   int sort_now(std::string* err);
   int sync(std::string* err);
   int slot_status(int slot);  // synchronises
@@ -111,8 +121,9 @@ class Batch {
   void set_pass_grid(int g) { pass_grid_override_ = g; invalidate_graphs(); }
   // measure (sort cadence, pass grid) candidates on the resident runs and
   // keep the fastest per particle-step; advances the runs (synchronises)
+  // (Ks: the sort cadences tried; empty = 8, 16, 32, 64)
   int autotune(long long steps_per_trial, int* sort_every, int* pass_ctas, double* ns_per_pstep,
-               std::string* err);
+               std::string* err, const std::vector<int>& Ks = {});
   int pass_grid() const { return pass_grid_; }
   int sort_every() const { return sort_every_; }
   void set_use_graphs(bool on) { use_graphs_ = on; }
@@ -140,6 +151,17 @@ class Batch {
   void stage_done(int slot);  // after the copy from the slot is enqueued
   int grow_full_runs(std::string* err);
   int check(cudaError_t e, const char* what, std::string* err);
+  // a step graph instance with phase events: ev[i] -> ev[i+1] is phase ph[i]
+  struct TimedGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ph;
+    bool pending = false;  // launched, its events not yet read
+  };
+  int capture(int steps, bool sort, TimedGraph* tg, cudaGraphExec_t* out, std::string* err);
+  int launch_timed(TimedGraph* pair, int* next, std::string* err);
+  int harvest(TimedGraph* tg, std::string* err);
+  void drop_timed(TimedGraph* tg);
 
   int device_;
   cudaStream_t stream_;
@@ -172,6 +194,13 @@ class Batch {
   bool graph_stage_ = true;
   cudaGraphExec_t graph_k_ = nullptr;
   cudaGraphExec_t graph_1_ = nullptr;
+  bool timing_ = false;
+  // sort-cycle, single-step and sort-only graphs with phase events
+  TimedGraph tk_[2], t1_[2], ts_[2];
+  int tk_next_ = 0, t1_next_ = 0, ts_next_ = 0;
+  double tsum_[4] = {0, 0, 0, 0};
+  long long tcnt_[4] = {0, 0, 0, 0};
+  long long tsteps_ = 0, tsorts_ = 0;
 };
 
 }  // namespace ecpic

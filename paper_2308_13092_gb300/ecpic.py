@@ -91,6 +91,14 @@ SIGNATURES = {
     "ecpic_engine_tune": (i32, [vp, i32, i32]),
     "ecpic_engine_profile": (i32, [vp, i64, vp, vp]),
     "ecpic_engine_autotune": (i32, [vp, i64, vp, vp, vp]),
+    "ecpic_engine_autotune_ks": (i32, [vp, i64, vp, i32, vp, vp, vp]),
+    "ecpic_engine_set_phase_timing": (i32, [vp, i32]),
+    "ecpic_engine_phase_times": (i32, [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)]),
+    "ecpic_engine_sort_state": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
+    "ecpic_autotune_ks": (i32, [vp, i64, vp, i32, vp, vp, vp]),
+    "ecpic_set_phase_timing": (i32, [vp, i32]),
+    "ecpic_phase_times": (i32, [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)]),
+    "ecpic_sort_state": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "ecpic_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_set_quiet_start": (i32, [vp, i32]),
     "ecpic_set_tallies": (i32, [vp, d, d, d, i32, d, i32, i32]),
@@ -150,6 +158,15 @@ def lib(build_if_missing: bool = True):
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _phase_times(call):
+    ms = np.zeros(4)
+    cnt = np.zeros(4, np.int64)
+    st, so = C.c_int64(), C.c_int64()
+    call(_p(ms), _p(cnt), C.byref(st), C.byref(so))
+    return dict(pass_ms=float(ms[0]), field_ms=float(ms[1]), sort_ms=float(ms[2]),
+                collide_ms=float(ms[3]), launches=cnt.tolist(), steps=st.value, sorts=so.value)
 
 
 def _chk(h, rc, what):
@@ -316,6 +333,19 @@ class Run:
     def set_pass_grid(self, ctas):
         _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
 
+    def set_phase_timing(self, on=True):
+        _chk(self.h, self._L.ecpic_set_phase_timing(self.h, 1 if on else 0), "ecpic_set_phase_timing")
+
+    def phase_times(self):
+        """Read and clear the per-phase device times of the timed steps."""
+        return _phase_times(lambda *a: _chk(self.h, self._L.ecpic_phase_times(self.h, *a),
+                                            "ecpic_phase_times"))
+
+    def sort_state(self):
+        k, since = C.c_int(), C.c_int()
+        _chk(self.h, self._L.ecpic_sort_state(self.h, C.byref(k), C.byref(since)), "ecpic_sort_state")
+        return dict(sort_every=k.value, since_sort=since.value)
+
     def set_quiet_start(self, quiet=True):
         _chk(self.h, self._L.ecpic_set_quiet_start(self.h, 1 if quiet else 0),
              "ecpic_set_quiet_start")
@@ -328,10 +358,16 @@ class Run:
                                                t["iedf_bins"], t["iad_bins"]), "ecpic_set_tallies")
         self.tally = t
 
-    def autotune(self, steps_per_trial=64):
+    def autotune(self, steps_per_trial=64, ks=None):
         k, g, ns = C.c_int(), C.c_int(), C.c_double()
-        _chk(self.h, self._L.ecpic_autotune(self.h, int(steps_per_trial), C.byref(k), C.byref(g),
-                                            C.byref(ns)), "ecpic_autotune")
+        if ks is None:
+            _chk(self.h, self._L.ecpic_autotune(self.h, int(steps_per_trial), C.byref(k), C.byref(g),
+                                                C.byref(ns)), "ecpic_autotune")
+        else:
+            kk = np.ascontiguousarray(ks, dtype=np.int32)
+            _chk(self.h, self._L.ecpic_autotune_ks(self.h, int(steps_per_trial), _p(kk), int(kk.size),
+                                                   C.byref(k), C.byref(g), C.byref(ns)),
+                 "ecpic_autotune_ks")
         return dict(sort_every=k.value, pass_ctas=g.value, ns_per_particle_step=ns.value)
 
     def nu_max(self, species):
@@ -517,11 +553,32 @@ class Engine:
         return dict(pass_ms=ms[0], field_ms=ms[1], sort_ms=ms[2], collide_ms=ms[3],
                     launches=cnt.tolist())
 
-    def autotune(self, steps_per_trial=64):
+    def autotune(self, steps_per_trial=64, ks=None):
         k, g, ns = C.c_int(), C.c_int(), C.c_double()
-        self._chk(self._L.ecpic_engine_autotune(self.h, int(steps_per_trial), C.byref(k),
-                                                C.byref(g), C.byref(ns)), "ecpic_engine_autotune")
+        if ks is None:
+            self._chk(self._L.ecpic_engine_autotune(self.h, int(steps_per_trial), C.byref(k),
+                                                    C.byref(g), C.byref(ns)), "ecpic_engine_autotune")
+        else:
+            kk = np.ascontiguousarray(ks, dtype=np.int32)
+            self._chk(self._L.ecpic_engine_autotune_ks(self.h, int(steps_per_trial), _p(kk),
+                                                       int(kk.size), C.byref(k), C.byref(g),
+                                                       C.byref(ns)), "ecpic_engine_autotune_ks")
         return dict(sort_every=k.value, pass_ctas=g.value, ns_per_particle_step=ns.value)
+
+    def set_phase_timing(self, on=True):
+        self._chk(self._L.ecpic_engine_set_phase_timing(self.h, 1 if on else 0),
+                  "ecpic_engine_set_phase_timing")
+
+    def phase_times(self):
+        """Read and clear the per-phase device times of the timed steps."""
+        return _phase_times(lambda *a: self._chk(self._L.ecpic_engine_phase_times(self.h, *a),
+                                                 "ecpic_engine_phase_times"))
+
+    def sort_state(self):
+        k, since = C.c_int(), C.c_int()
+        self._chk(self._L.ecpic_engine_sort_state(self.h, C.byref(k), C.byref(since)),
+                  "ecpic_engine_sort_state")
+        return dict(sort_every=k.value, since_sort=since.value)
 
     def tune(self, pass_ctas=0, sort_every=16):
         self._chk(self._L.ecpic_engine_tune(self.h, int(pass_ctas), int(sort_every)),

@@ -1,13 +1,16 @@
 """Allocation-free deposit entry point (ecpic_deposit_device_noalloc) through
 the C ABI.  On the same seeded (cell, xi) input it must give the sums of
-ecpic_deposit_device; the fixed-point sums are integers, so the tolerance is
-zero.  Checked on two calls in a row, with the device's free memory not
-shrinking across them.  The file name puts it last in the suite, so it runs
-both alone and after the other tests."""
+ecpic_deposit_device and of the oracle's fixed-point rule (Eq. 2-3 in units of
+2^-32 particle); the sums are integers, so the tolerance is zero.  Checked on
+two calls in a row, with the device's free memory not shrinking across them.
+The file name puts it last in the suite, so it runs both alone and after the
+other tests."""
 import gc
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -64,10 +67,15 @@ def test_noalloc_deposit_equals_deposit_device_two_calls(E):
         gc.enable()
     assert free_after >= free_before
     assert torch.equal(warm, refs[0])
-    for (_, N, n), (c, _), S, R in zip(cases, inputs, outs, refs):
+    for (_, N, n), (c, x), S, R in zip(cases, inputs, outs, refs):
         assert torch.equal(S, R)
         live = int((c >= 0).sum())
         assert int(S.sum()) == live * 2 ** 32
+        # the oracle's fixed-point rule on the same input (absorbed skipped)
+        ch, xh = c.cpu().numpy(), x.cpu().numpy()
+        keep = ch >= 0
+        So = oracle.deposit_fixed(N, ch[keep], xh[keep])
+        assert np.array_equal(S.cpu().numpy().view(np.uint64), So)
 
 
 def test_noalloc_deposit_accumulates_and_limits(E):
