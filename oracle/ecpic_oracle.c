@@ -45,9 +45,11 @@ typedef struct {
 
 typedef struct {
   double q, m, w;
+  double wb;        /* base weight: a particle of multiplier k weighs k * wb */
   int64_t cap, n;
   double *X, *vx, *vy, *vz;
   uint64_t* id;
+  uint32_t* mw;     /* weight multipliers (all 1 without rebalancing) */
   int nproc;
   or_process proc[OR_MAX_PROC];
   int heavy;        /* has ion-neutral processes: sample the neutral */
@@ -56,6 +58,7 @@ typedef struct {
   /* counters */
   int64_t absorbed[2], births, lost, clamps, candidates;
   int64_t coll[OR_MAX_PROC];
+  int64_t rb_merged, rb_split, rb_skipped; /* groups merged, particles split, cells skipped */
   double ke;
   /* per-node deposit and moments at the current step */
   double *D, *M1, *M2;
@@ -95,6 +98,11 @@ struct or_run {
   int sample_every;
   int64_t n_samples;
   double* acc_phi;
+  /* particle rebalancing (set before init): every rb_every steps; merge in
+   * cells holding more than rb_hi particles of a species, split in cells
+   * holding fewer than rb_lo; aim rb_target; loaded multiplier rb_m0 */
+  int rb_every, rb_target, rb_lo, rb_hi;
+  uint32_t rb_m0;
 };
 
 /* ------------------------------------------------------------------ */
@@ -351,7 +359,7 @@ int oracle_doubling_grid(int n_ref, double L, double L_buff, int dx_min,
 
 /* ------------------------------------------------------------------ */
 static void or_free_species(or_species* s) {
-  free(s->X); free(s->vx); free(s->vy); free(s->vz); free(s->id);
+  free(s->X); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->mw);
   free(s->D); free(s->M1); free(s->M2);
   free(s->eedf); free(s->iedf); free(s->iad); free(s->acc_P);
   free(s->acc_n); free(s->acc_T); free(s->acc_M0); free(s->acc_M1);
@@ -364,6 +372,7 @@ int oracle_create(or_run** out) {
   if (!out) return -1;
   or_run* r = calloc(1, sizeof(or_run));
   if (!r) return -3;
+  r->rb_m0 = 1;
   *out = r;
   return 0;
 }
@@ -484,14 +493,15 @@ int oracle_add_species(or_run* r, double q, double m, double w,
   if (r->ns >= OR_MAX_SPECIES) return -1;
   or_species* s = &r->sp[r->ns];
   memset(s, 0, sizeof(*s));
-  s->q = q; s->m = m; s->w = w; s->cap = capacity;
+  s->q = q; s->m = m; s->w = w; s->wb = w; s->cap = capacity;
   size_t c = (size_t)capacity;
   s->X = malloc(sizeof(double) * c);
   s->vx = malloc(sizeof(double) * c);
   s->vy = malloc(sizeof(double) * c);
   s->vz = malloc(sizeof(double) * c);
   s->id = malloc(sizeof(uint64_t) * c);
-  if (!s->X || !s->vx || !s->vy || !s->vz || !s->id) return -3;
+  s->mw = malloc(sizeof(uint32_t) * c);
+  if (!s->X || !s->vx || !s->vy || !s->vz || !s->id || !s->mw) return -3;
   if (or_alloc_node_arrays(r, s)) return -3;
   if (species_out) *species_out = r->ns;
   r->ns++;
@@ -614,22 +624,23 @@ static void or_deposit(or_run* r) {
       int j = or_locate(r, s->X[i]);
       double xi = (s->X[i] - r->x[j]) / r->dx[j];
       double v = s->vx[i];
+      double k = (double)s->mw[i]; /* weight multiplier: k base particles */
       if (r->scheme >= OR_SCHEME_EC2) {
         /* quadratic B-spline charge shares about the nearest node n0 */
         int n0 = xi < 0.5 ? j : j + 1;
         double u = xi < 0.5 ? xi : xi - 1.0;
         double a = 0.5 * (0.5 - u) * (0.5 - u), b = 0.5 * (0.5 + u) * (0.5 + u);
-        s->D[or_node2(n0 - 1, N, r->bc)] += a;
-        s->D[or_node2(n0, N, r->bc)] += 0.75 - u * u;
-        s->D[or_node2(n0 + 1, N, r->bc)] += b;
+        s->D[or_node2(n0 - 1, N, r->bc)] += k * a;
+        s->D[or_node2(n0, N, r->bc)] += k * (0.75 - u * u);
+        s->D[or_node2(n0 + 1, N, r->bc)] += k * b;
       } else {
-        s->D[j] += 1.0 - xi;
-        s->D[j + 1] += xi;
+        s->D[j] += k * (1.0 - xi);
+        s->D[j + 1] += k * xi;
       }
-      s->M1[j] += (1.0 - xi) * v;
-      s->M1[j + 1] += xi * v;
-      s->M2[j] += (1.0 - xi) * v * v;
-      s->M2[j + 1] += xi * v * v;
+      s->M1[j] += k * (1.0 - xi) * v;
+      s->M1[j + 1] += k * xi * v;
+      s->M2[j] += k * (1.0 - xi) * v * v;
+      s->M2[j + 1] += k * xi * v * v;
     }
     if (r->bc == OR_PERIODIC) {
       if (r->scheme < OR_SCHEME_EC2) s->D[0] += s->D[N];
@@ -640,7 +651,7 @@ static void or_deposit(or_run* r) {
   }
   for (int n = 0; n <= N; ++n) {
     double q = 0.0;
-    for (int si = 0; si < r->ns; ++si) q += r->sp[si].q * r->sp[si].w * r->sp[si].D[n];
+    for (int si = 0; si < r->ns; ++si) q += r->sp[si].q * r->sp[si].wb * r->sp[si].D[n];
     r->Q[n] = q;
   }
 }
@@ -682,11 +693,12 @@ static int or_bin(double v, double d, int n) {
 
 /* an ion of species s reaching x = 0 with velocity (vx, vy, vz): energy
  * (eV) and angle from the electrode normal (degrees, 0..90) */
-static void or_tally_impact(const or_run* r, or_species* s, double vx, double vy, double vz) {
+static void or_tally_impact(const or_run* r, or_species* s, double vx, double vy, double vz,
+                            double k) {
   double E = 0.5 * s->m * (vx * vx + vy * vy + vz * vz) / OR_QE;
   double th = atan2(sqrt(vy * vy + vz * vz), fabs(vx)) * (180.0 / 3.14159265358979323846);
-  s->iedf[or_bin(E, r->iedf_dE, r->iedf_n)] += 1.0;
-  s->iad[or_bin(th, 90.0 / r->iad_n, r->iad_n)] += 1.0;
+  s->iedf[or_bin(E, r->iedf_dE, r->iedf_n)] += k;
+  s->iad[or_bin(th, 90.0 / r->iad_n, r->iad_n)] += k;
 }
 
 static void or_sample(or_run* r) {
@@ -698,14 +710,14 @@ static void or_sample(or_run* r) {
       int j = or_locate(r, s->X[i]);
       if (j < r->eedf_c0 || j > r->eedf_c1) continue;
       double E = 0.5 * s->m * (s->vx[i] * s->vx[i] + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]) / OR_QE;
-      s->eedf[or_bin(E, r->eedf_dE, r->eedf_n)] += 1.0;
+      s->eedf[or_bin(E, r->eedf_dE, r->eedf_n)] += (double)s->mw[i];
     }
   }
   for (int si = 0; si < r->ns; ++si) {
     or_species* s = &r->sp[si];
     for (int n = 0; n <= N; ++n) {
       double D = s->D[n];
-      s->acc_n[n] += s->w * D / r->V[n];
+      s->acc_n[n] += s->wb * D / r->V[n];
       double T = 0.0;
       if (D > 0.0) {
         double m1 = s->M1[n] / D, m2 = s->M2[n] / D;
@@ -746,6 +758,8 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
     or_species* s = &r->sp[si];
     double sd = sqrt(OR_QE * T_eV[si] / s->m);
     s->n = n_per_species[si];
+    /* a loaded particle of weight w holds rb_m0 base particles of weight wb */
+    s->wb = s->w / (double)r->rb_m0;
     for (int64_t i = 0; i < s->n; ++i) {
       uint32_t a[4], b[4];
       or_draw(r, (uint64_t)i, 0xFFFFFFFFu, ((uint32_t)si << 8) | 0x80u, a);
@@ -762,10 +776,12 @@ int oracle_init(or_run* r, uint64_t seed, double dt,
       s->vy[i] = sd * z1;
       s->vz[i] = sd * z2;
       s->id[i] = (uint64_t)i;
+      s->mw[i] = r->rb_m0;
     }
     memset(s->absorbed, 0, sizeof(s->absorbed));
     memset(s->coll, 0, sizeof(s->coll));
     s->births = s->lost = s->clamps = s->candidates = 0;
+    s->rb_merged = s->rb_split = s->rb_skipped = 0;
     s->ke = 0.0;
   }
   for (int si = 0; si < r->ns; ++si) or_null_rate(r, &r->sp[si]);
@@ -821,6 +837,7 @@ int oracle_set_particles(or_run* r, int species, const double* X,
     s->vy[i] = vy[i];
     s->vz[i] = vz[i];
     s->id[i] = id[i];
+    s->mw[i] = r->rb_m0;
   }
   s->n = n;
   return or_refresh(r);
@@ -861,6 +878,7 @@ int oracle_set_particles_cell(or_run* r, int species, const int32_t* cell,
     s->vy[i] = (double)vy[i];
     s->vz[i] = (double)vz[i];
     s->id[i] = id[i];
+    s->mw[i] = r->rb_m0;
   }
   s->n = n;
   return or_refresh(r);
@@ -881,13 +899,14 @@ int oracle_get_particles_cell(or_run* r, int species, int32_t* cell,
 }
 
 static int or_append(or_species* s, double X, double vx, double vy, double vz,
-                     uint64_t id) {
+                     uint64_t id, uint32_t k) {
   if (s->n >= s->cap) {
     s->lost++;
     return -4;
   }
   s->X[s->n] = X; s->vx[s->n] = vx; s->vy[s->n] = vy; s->vz[s->n] = vz;
   s->id[s->n] = id;
+  s->mw[s->n] = k;
   s->n++;
   return 0;
 }
@@ -979,11 +998,13 @@ static int or_collide(or_run* r, int si, int64_t i, int64_t k) {
       double sd = sqrt(OR_KB * r->Tg / r->mg);
       double X = s->X[i];
       s->births++;
+      /* both products carry the parent's weight (charge conserved) */
+      uint32_t kw = s->mw[i];
       if (or_append(s, X, sp2 * d2[0], sp2 * d2[1], sp2 * d2[2],
-                    oracle_child_id(id, k, 1)))
+                    oracle_child_id(id, k, 1), kw))
         rc = -4;
       if (or_append(&r->sp[pr->product], X, sd * z0, sd * z1, sd * z2,
-                    oracle_child_id(id, k, 2)))
+                    oracle_child_id(id, k, 2), kw))
         rc = -4;
       break;
     }
@@ -1039,6 +1060,268 @@ static double or_gather2_mc(const or_run* r, int j, double xi) {
   return e;
 }
 
+/* ------------------------------------------------------------------ */
+/* Particle rebalancing on non-uniform grids (Sec. 3d: keep the number of
+ * particles per cell near a target so that the cost follows the cell count;
+ * the paper proposes this and gives no algorithm -- the rule below is this
+ * project's design).  Every particle carries an integer weight multiplier k
+ * (it stands for k base particles of weight wb), and the deposit, moments,
+ * energies and tallies count k.  At a rebalancing level, per species and
+ * cell j with n particles:
+ *   - n > rb_hi (merge; cells above OR_RB_MAX_CELL are left alone and
+ *     counted): order the particles by (vx, id), cut the order into
+ *     floor(n/4) consecutive groups of four (the n mod 4 fastest stay
+ *     apart), and merge the G = min(floor(n/4), ceil((n - rb_target)/2))
+ *     groups nearest the middle of that order (ties: the slower group),
+ *     skipping groups whose weight exceeds OR_RB_MAX_WEIGHT.  A group of
+ *     weight W = sum k, mean velocity u = sum k v / W and per-component
+ *     standard deviations s_x, s_y, s_z becomes two particles at the
+ *     weighted centroid X_c = sum k X / W, of weights a = ceil(W/2) and
+ *     b = W - a, with velocities u + sqrt(b/a) d and u - sqrt(a/b) d,
+ *     d = (s_x, +-s_y, +-s_z), the signs from Philox; they take the group's
+ *     two smallest ids.  CIC node charges (linear in the offset within the
+ *     cell), momentum and each velocity component's second moment -- hence
+ *     the energy and the x temperature -- are those of the group.
+ *   - 0 < n < rb_lo (split): the S = min(rb_target - n, #{k >= 2})
+ *     particles of largest k (ties: smallest id) each become two at the same
+ *     position and velocity, of weights ceil(k/2) (keeping the id) and
+ *     floor(k/2) (id child_id(id, level, 3)): every node charge, the
+ *     momentum and the energy are unchanged exactly.
+ * Random numbers: Philox with counter (id_min lo, id_min hi, level,
+ * (s << 8) | 0x10), word 0 bit 0 (y sign) and bit 1 (z sign). */
+#define OR_RB_MAX_CELL 4096
+#define OR_RB_MAX_WEIGHT 65536u
+
+typedef struct {
+  double vx;
+  uint64_t id;
+  int64_t i;
+} or_rb_key;
+
+static int or_rb_cmp_v(const void* a, const void* b) {
+  const or_rb_key* p = (const or_rb_key*)a;
+  const or_rb_key* q = (const or_rb_key*)b;
+  if (p->vx < q->vx) return -1;
+  if (p->vx > q->vx) return 1;
+  return (p->id < q->id) ? -1 : (p->id > q->id);
+}
+
+typedef struct {
+  uint32_t k;
+  uint64_t id;
+  int64_t i;
+} or_rb_wkey;
+
+static int or_rb_cmp_w(const void* a, const void* b) {
+  const or_rb_wkey* p = (const or_rb_wkey*)a;
+  const or_rb_wkey* q = (const or_rb_wkey*)b;
+  if (p->k != q->k) return (p->k > q->k) ? -1 : 1; /* heaviest first */
+  return (p->id < q->id) ? -1 : (p->id > q->id);
+}
+
+typedef struct {
+  int dist; /* |2g - (ng - 1)| */
+  int g;
+} or_rb_group;
+
+static int or_rb_cmp_g(const void* a, const void* b) {
+  const or_rb_group* p = (const or_rb_group*)a;
+  const or_rb_group* q = (const or_rb_group*)b;
+  if (p->dist != q->dist) return p->dist < q->dist ? -1 : 1;
+  return p->g < q->g ? -1 : (p->g > q->g);
+}
+
+/* rebalance species si in cell j holding the particles idx[0..n): the new
+ * particles are written to the output arrays of the species at *out */
+typedef struct {
+  double *X, *vx, *vy, *vz;
+  uint64_t* id;
+  uint32_t* mw;
+  int64_t n, cap;
+} or_rb_out;
+
+static int or_rb_put(or_rb_out* o, double X, double vx, double vy, double vz, uint64_t id,
+                     uint32_t k) {
+  if (o->n >= o->cap) return -4;
+  o->X[o->n] = X; o->vx[o->n] = vx; o->vy[o->n] = vy; o->vz[o->n] = vz;
+  o->id[o->n] = id; o->mw[o->n] = k;
+  o->n++;
+  return 0;
+}
+
+static int or_rb_cell(or_run* r, int si, const int64_t* idx, int64_t n, or_rb_out* o) {
+  or_species* s = &r->sp[si];
+  int rc = 0;
+  int64_t merge_groups = 0, splits = 0;
+  if (n > r->rb_hi) {
+    if (n > OR_RB_MAX_CELL) {
+      s->rb_skipped++;
+    } else {
+      int64_t ng = n / 4;
+      int64_t want = (n - r->rb_target + 1) / 2;
+      merge_groups = ng < want ? ng : want;
+    }
+  } else if (n > 0 && n < r->rb_lo) {
+    int64_t heavy = 0;
+    for (int64_t t = 0; t < n; ++t) heavy += s->mw[idx[t]] >= 2u;
+    splits = r->rb_target - n < heavy ? r->rb_target - n : heavy;
+  }
+  if (merge_groups > 0) {
+    or_rb_key* key = malloc(sizeof(or_rb_key) * (size_t)n);
+    int64_t ng = n / 4;
+    or_rb_group* grp = malloc(sizeof(or_rb_group) * (size_t)ng);
+    char* merged = calloc((size_t)ng, 1);
+    if (!key || !grp || !merged) { free(key); free(grp); free(merged); return -3; }
+    for (int64_t t = 0; t < n; ++t) {
+      key[t].vx = s->vx[idx[t]];
+      key[t].id = s->id[idx[t]];
+      key[t].i = idx[t];
+    }
+    qsort(key, (size_t)n, sizeof(or_rb_key), or_rb_cmp_v);
+    for (int64_t g = 0; g < ng; ++g) {
+      int64_t d = 2 * g - (ng - 1);
+      grp[g].dist = (int)(d < 0 ? -d : d);
+      grp[g].g = (int)g;
+    }
+    qsort(grp, (size_t)ng, sizeof(or_rb_group), or_rb_cmp_g);
+    int64_t taken = 0;
+    for (int64_t t = 0; t < ng && taken < merge_groups; ++t) {
+      int g = grp[t].g;
+      uint64_t W = 0;
+      for (int q = 0; q < 4; ++q) W += s->mw[key[4 * g + q].i];
+      if (W > OR_RB_MAX_WEIGHT) continue;
+      merged[g] = 1;
+      taken++;
+    }
+    for (int64_t g = 0; g < ng; ++g) {
+      if (!merged[g]) continue;
+      double W = 0.0, Xc = 0.0, u[3] = {0.0, 0.0, 0.0}, m2[3] = {0.0, 0.0, 0.0};
+      uint64_t id0 = UINT64_MAX, id1 = UINT64_MAX;
+      uint32_t Wi = 0;
+      for (int q = 0; q < 4; ++q) {
+        int64_t i = key[4 * g + q].i;
+        double k = (double)s->mw[i];
+        Wi += s->mw[i];
+        W += k;
+        Xc += k * s->X[i];
+        u[0] += k * s->vx[i];
+        u[1] += k * s->vy[i];
+        u[2] += k * s->vz[i];
+        uint64_t id = s->id[i];
+        if (id < id0) { id1 = id0; id0 = id; } else if (id < id1) { id1 = id; }
+      }
+      Xc /= W;
+      for (int c = 0; c < 3; ++c) u[c] /= W;
+      for (int q = 0; q < 4; ++q) {
+        int64_t i = key[4 * g + q].i;
+        double k = (double)s->mw[i];
+        double v[3] = {s->vx[i] - u[0], s->vy[i] - u[1], s->vz[i] - u[2]};
+        for (int c = 0; c < 3; ++c) m2[c] += k * v[c] * v[c];
+      }
+      uint32_t A[4];
+      or_draw(r, id0, (uint32_t)r->step, ((uint32_t)si << 8) | 0x10u, A);
+      double d[3] = {sqrt(m2[0] / W), sqrt(m2[1] / W), sqrt(m2[2] / W)};
+      if (A[0] & 1u) d[1] = -d[1];
+      if (A[0] & 2u) d[2] = -d[2];
+      uint32_t ka = (Wi + 1u) / 2u, kb = Wi - ka;
+      double fa = sqrt((double)kb / (double)ka), fb = sqrt((double)ka / (double)kb);
+      /* the centroid of positions in one cell stays in that cell */
+      if (or_rb_put(o, Xc, u[0] + fa * d[0], u[1] + fa * d[1], u[2] + fa * d[2], id0, ka)) rc = -4;
+      if (or_rb_put(o, Xc, u[0] - fb * d[0], u[1] - fb * d[1], u[2] - fb * d[2], id1, kb)) rc = -4;
+      s->rb_merged++;
+    }
+    /* the particles that stay as they are */
+    for (int64_t t = 0; t < n; ++t) {
+      int64_t g = t / 4;
+      if (g < ng && merged[g]) continue;
+      int64_t i = key[t].i;
+      if (or_rb_put(o, s->X[i], s->vx[i], s->vy[i], s->vz[i], s->id[i], s->mw[i])) rc = -4;
+    }
+    free(key); free(grp); free(merged);
+    return rc;
+  }
+  if (splits > 0) {
+    or_rb_wkey* key = malloc(sizeof(or_rb_wkey) * (size_t)n);
+    if (!key) return -3;
+    for (int64_t t = 0; t < n; ++t) {
+      key[t].k = s->mw[idx[t]];
+      key[t].id = s->id[idx[t]];
+      key[t].i = idx[t];
+    }
+    qsort(key, (size_t)n, sizeof(or_rb_wkey), or_rb_cmp_w);
+    for (int64_t t = 0; t < n; ++t) {
+      int64_t i = key[t].i;
+      uint32_t k = s->mw[i];
+      if (t < splits) {
+        uint32_t ka = (k + 1u) / 2u, kb = k - ka;
+        if (or_rb_put(o, s->X[i], s->vx[i], s->vy[i], s->vz[i], s->id[i], ka)) rc = -4;
+        if (or_rb_put(o, s->X[i], s->vx[i], s->vy[i], s->vz[i],
+                      oracle_child_id(s->id[i], r->step, 3), kb)) rc = -4;
+        s->rb_split++;
+      } else {
+        if (or_rb_put(o, s->X[i], s->vx[i], s->vy[i], s->vz[i], s->id[i], k)) rc = -4;
+      }
+    }
+    free(key);
+    return rc;
+  }
+  for (int64_t t = 0; t < n; ++t) {
+    int64_t i = idx[t];
+    if (or_rb_put(o, s->X[i], s->vx[i], s->vy[i], s->vz[i], s->id[i], s->mw[i])) rc = -4;
+  }
+  return rc;
+}
+
+/* one rebalancing of every species at the current level (particles gathered
+ * by cell; the output replaces the species' arrays, cell by cell) */
+static int or_rebalance(or_run* r) {
+  int rc = 0;
+  int N = r->N;
+  for (int si = 0; si < r->ns; ++si) {
+    or_species* s = &r->sp[si];
+    int64_t n = s->n;
+    int64_t* cnt = calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t* order = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int* cellof = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    or_rb_out o;
+    o.cap = s->cap;
+    o.n = 0;
+    o.X = malloc(sizeof(double) * (size_t)s->cap);
+    o.vx = malloc(sizeof(double) * (size_t)s->cap);
+    o.vy = malloc(sizeof(double) * (size_t)s->cap);
+    o.vz = malloc(sizeof(double) * (size_t)s->cap);
+    o.id = malloc(sizeof(uint64_t) * (size_t)s->cap);
+    o.mw = malloc(sizeof(uint32_t) * (size_t)s->cap);
+    if (!cnt || !order || !cellof || !o.X || !o.vx || !o.vy || !o.vz || !o.id || !o.mw) {
+      free(cnt); free(order); free(cellof);
+      free(o.X); free(o.vx); free(o.vy); free(o.vz); free(o.id); free(o.mw);
+      return -3;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      cellof[i] = or_locate(r, s->X[i]);
+      cnt[cellof[i] + 1]++;
+    }
+    for (int j = 0; j < N; ++j) cnt[j + 1] += cnt[j];
+    {
+      int64_t* pos = malloc(sizeof(int64_t) * (size_t)N);
+      if (!pos) return -3;
+      for (int j = 0; j < N; ++j) pos[j] = cnt[j];
+      for (int64_t i = 0; i < n; ++i) order[pos[cellof[i]]++] = i;
+      free(pos);
+    }
+    for (int j = 0; j < N; ++j) {
+      int e = or_rb_cell(r, si, order + cnt[j], cnt[j + 1] - cnt[j], &o);
+      if (e == -4) { rc = -4; s->lost++; }
+      else if (e) return e;
+    }
+    free(s->X); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->mw);
+    s->X = o.X; s->vx = o.vx; s->vy = o.vy; s->vz = o.vz; s->id = o.id; s->mw = o.mw;
+    s->n = o.n;
+    free(cnt); free(order); free(cellof);
+  }
+  return rc;
+}
+
 static int or_step_once(or_run* r) {
   int64_t k = r->step;
   int N = r->N;
@@ -1067,14 +1350,15 @@ static int or_step_once(or_run* r) {
                                                : (1.0 - xi) * r->E[j] + xi * r->E[j + 1];
       double vold = s->vx[i];
       double vnew = vold + qm * Ei * r->dt;
-      ke += 0.5 * s->m * s->w * (vold * vnew + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+      double wi = s->wb * (double)s->mw[i];
+      ke += 0.5 * s->m * wi * (vold * vnew + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
       /* J.E of the push: q w E_i (v^{k-1/2} + v^{k+1/2})/2 per unit volume of cell j */
-      if (sampled) s->acc_P[j] += s->q * s->w * Ei * 0.5 * (vold + vnew) / r->dx[j];
+      if (sampled) s->acc_P[j] += s->q * wi * Ei * 0.5 * (vold + vnew) / r->dx[j];
       double Xn = X + vnew * r->dt;
       if (r->bc == OR_DIRICHLET) {
         if (Xn <= 0.0) {
           s->absorbed[0]++;
-          if (s->q > 0.0) or_tally_impact(r, s, vnew, s->vy[i], s->vz[i]);
+          if (s->q > 0.0) or_tally_impact(r, s, vnew, s->vy[i], s->vz[i], (double)s->mw[i]);
           continue;
         }
         if (Xn >= r->L) { s->absorbed[1]++; continue; }
@@ -1087,6 +1371,7 @@ static int or_step_once(or_run* r) {
       s->vy[keep] = s->vy[i];
       s->vz[keep] = s->vz[i];
       s->id[keep] = s->id[i];
+      s->mw[keep] = s->mw[i];
       keep++;
     }
     s->n = keep;
@@ -1103,6 +1388,13 @@ static int or_step_once(or_run* r) {
   int e = or_refresh(r);
   if (e) return e;
   if (r->sample_every > 0 && r->step % r->sample_every == 0) or_sample(r);
+  /* particle rebalancing at level k+1, after the field and the sample: it
+   * keeps every node's charge (see or_rebalance), so the field stands */
+  if (r->rb_every > 0 && r->step % r->rb_every == 0) {
+    e = or_rebalance(r);
+    if (e == -4) rc = -4;
+    else if (e) return e;
+  }
   return rc;
 }
 
@@ -1246,4 +1538,66 @@ int64_t oracle_get_averages(const or_run* r, double* density, double* phi,
   if (phi)
     for (int n = 0; n <= N; ++n) phi[n] = r->acc_phi[n] * inv;
   return ns;
+}
+
+/* ------------------------------------------------------------------ */
+int oracle_set_rebalance(or_run* r, int every, int target, int lo, int hi, uint32_t m0) {
+  if (!r || every < 0 || (every > 0 && (target < 1 || lo < 0 || hi < target || lo > target)) ||
+      m0 < 1 || m0 > OR_RB_MAX_WEIGHT)
+    return -1;
+  if (r->initialized) return -2;
+  r->rb_every = every; r->rb_target = target; r->rb_lo = lo; r->rb_hi = hi; r->rb_m0 = m0;
+  return 0;
+}
+
+int oracle_rebalance_now(or_run* r) {
+  if (!r) return -1;
+  if (!r->initialized) return -2;
+  return or_rebalance(r);
+}
+
+int oracle_get_weights(const or_run* r, int species, uint32_t* k, int64_t cap, int64_t* n) {
+  if (!r || species < 0 || species >= r->ns || !n) return -1;
+  const or_species* s = &r->sp[species];
+  *n = s->n;
+  if (cap < s->n) return -1;
+  if (k) memcpy(k, s->mw, sizeof(uint32_t) * (size_t)s->n);
+  return 0;
+}
+
+int oracle_set_weights(or_run* r, int species, const uint32_t* k, int64_t n) {
+  if (!r || species < 0 || species >= r->ns || !k) return -1;
+  if (!r->initialized) return -2;
+  or_species* s = &r->sp[species];
+  if (n != s->n) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (k[i] < 1u || k[i] > OR_RB_MAX_WEIGHT) return -1;
+  memcpy(s->mw, k, sizeof(uint32_t) * (size_t)n);
+  return or_refresh(r);
+}
+
+int oracle_get_rebalance_counters(const or_run* r, int64_t* out3) {
+  if (!r || !out3) return -1;
+  for (int si = 0; si < OR_MAX_SPECIES; ++si) {
+    const or_species* s = &r->sp[si];
+    int on = si < r->ns;
+    out3[3 * si] = on ? s->rb_merged : 0;
+    out3[3 * si + 1] = on ? s->rb_split : 0;
+    out3[3 * si + 2] = on ? s->rb_skipped : 0;
+  }
+  return 0;
+}
+
+int oracle_deposit_fixed_w(int N, int64_t n, const int32_t* cell, const float* xi,
+                           const uint32_t* k, uint64_t* S) {
+  if (N < 1 || n < 0 || (n > 0 && (!cell || !xi || !k)) || !S) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int j = cell[i];
+    float f = xi[i];
+    if (j < 0 || j >= N || !(f >= 0.0f) || !(f < 1.0f)) return -1;
+    uint64_t rgt = (uint64_t)(uint32_t)((double)f * 4294967296.0); /* floor, f < 1 */
+    S[j] += (uint64_t)k[i] * (4294967296ull - rgt);
+    S[j + 1] += (uint64_t)k[i] * rgt;
+  }
+  return 0;
 }

@@ -181,6 +181,30 @@ int64_t oracle_get_averages(const or_run* r, double* density, double* phi,
 int oracle_nu_max(const or_run* r, int species, double* nu_max,
                   uint32_t* threshold24);
 
+/* ---- particle rebalancing (Sec. 3d proposes it; the rule is this
+ * project's design, described at or_rebalance in the source) ----------- */
+/* Every particle carries an integer weight multiplier k (it stands for k
+ * base particles); deposit, moments, energies and tallies count k.  Before
+ * init: rebalance every `every` steps (0 = never), at level k+1 after the
+ * field and the sample; merge in cells holding more than `hi` particles of a
+ * species, split in cells holding fewer than `lo` (0 < n), aiming at
+ * `target` (lo <= target <= hi); loaded particles (and set_particles) get
+ * multiplier m0 (1..65536) and base weight w / m0. */
+int oracle_set_rebalance(or_run* r, int every, int target, int lo, int hi, uint32_t m0);
+/* one rebalancing of every species now, at the current level */
+int oracle_rebalance_now(or_run* r);
+/* weight multipliers of a species' particles (order of get_particles) */
+int oracle_get_weights(const or_run* r, int species, uint32_t* k, int64_t cap, int64_t* n);
+/* replace them (n = the species' count; 1..65536 each); recomputes the field */
+int oracle_set_weights(or_run* r, int species, const uint32_t* k, int64_t n);
+/* per species s: out3[3s] groups merged, out3[3s+1] particles split,
+ * out3[3s+2] cells skipped (above 4096 particles) */
+int oracle_get_rebalance_counters(const or_run* r, int64_t* out3);
+/* weighted fixed-point CIC rule: S[cell] += k (2^32 - r), S[cell+1] += k r,
+ * r = floor(xi32 * 2^32) */
+int oracle_deposit_fixed_w(int N, int64_t n, const int32_t* cell, const float* xi,
+                           const uint32_t* k, uint64_t* S);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,12 @@ def _load(path):
         "oracle_get_energy": (i32, [vp, vp, vp]),
         "oracle_get_averages": (i64, [vp, vp, vp, vp, vp]),
         "oracle_nu_max": (i32, [vp, i32, P(d), P(u32)]),
+        "oracle_set_rebalance": (i32, [vp, i32, i32, i32, i32, u32]),
+        "oracle_rebalance_now": (i32, [vp]),
+        "oracle_get_weights": (i32, [vp, i32, vp, i64, P(i64)]),
+        "oracle_set_weights": (i32, [vp, i32, vp, i64]),
+        "oracle_get_rebalance_counters": (i32, [vp, vp]),
+        "oracle_deposit_fixed_w": (i32, [i32, i64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -123,6 +129,18 @@ def deposit_fixed(N, cell, xi, S=None):
         S = np.zeros(N + 1, dtype=np.uint64)
     _chk(lib().oracle_deposit_fixed(N, cell.size, _ptr(cell), _ptr(xi), _ptr(S)),
          "oracle_deposit_fixed")
+    return S
+
+
+def deposit_fixed_w(N, cell, xi, k, S=None):
+    """Weighted fixed-point CIC rule: S[cell] += k (2^32 - r), S[cell+1] += k r."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    xi = np.ascontiguousarray(xi, dtype=np.float32)
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    if S is None:
+        S = np.zeros(N + 1, dtype=np.uint64)
+    _chk(lib().oracle_deposit_fixed_w(N, cell.size, _ptr(cell), _ptr(xi), _ptr(k), _ptr(S)),
+         "oracle_deposit_fixed_w")
     return S
 
 
@@ -285,6 +303,34 @@ class OracleRun:
                                                C.byref(n)), "oracle_get_particles_cell")
         k = n.value
         return cell[:k], xi[:k]
+
+    def set_rebalance(self, every, target, lo, hi, m0=1):
+        """Particle rebalancing (before init): see oracle_set_rebalance."""
+        _chk(self._L.oracle_set_rebalance(self.h, int(every), int(target), int(lo), int(hi),
+                                          int(m0)), "oracle_set_rebalance")
+
+    def rebalance_now(self):
+        rc = self._L.oracle_rebalance_now(self.h)
+        _chk(rc, "oracle_rebalance_now")
+
+    def get_weights(self, species):
+        cap = self.caps[species]
+        k = np.zeros(cap, dtype=np.uint32)
+        n = C.c_int64()
+        _chk(self._L.oracle_get_weights(self.h, species, _ptr(k), cap, C.byref(n)),
+             "oracle_get_weights")
+        return k[: n.value].copy()
+
+    def set_weights(self, species, k):
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        _chk(self._L.oracle_set_weights(self.h, species, _ptr(k), k.size), "oracle_set_weights")
+
+    def rebalance_counters(self):
+        out = np.zeros(3 * MAX_SPECIES, dtype=np.int64)
+        _chk(self._L.oracle_get_rebalance_counters(self.h, _ptr(out)),
+             "oracle_get_rebalance_counters")
+        return [dict(merged=int(out[3 * s]), split=int(out[3 * s + 1]), skipped=int(out[3 * s + 2]))
+                for s in range(self.ns)]
 
     def step(self, n=1, allow_capacity=False):
         rc = self._L.oracle_step(self.h, int(n))
