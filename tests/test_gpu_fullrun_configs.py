@@ -1,0 +1,147 @@
+"""Full-run statistical parity with the oracle on the resolved and
+under-resolved discharges (Sec. 3a Table 1 geometry; Sec. 3b-c, Table 2):
+
+* resolved: 1024 uniform cells at dx = lambda_De, 524,288 particles at start,
+  w_pe dt = 0.2 (750 steps per RF period), EC and the momentum-conserving MC
+  switch;
+* under-resolved uniform: the same plasma on 128 cells (dx = 8 lambda_De),
+  256 particles per cell and species;
+* non-uniform: the same plasma on the 114-cell tanh grid refined at both
+  sheaths and on the 114-cell doubling grid (Sec. 3c rules, 4..32 dx_ref),
+  with the particle count of a 9x reduced grid.
+
+Time-averaged profiles of n_e, n_i, phi, T_e and T_i (sampled every 15
+steps from the start) and the event rates are compared as ensembles
+(tests/ensemble.py): 64 GPU seeds and 4 oracle seeds in a permutation test
+of the ensemble means, and the GPU on the oracle's 4 seeds paired with them.
+The seed-to-seed spread is heavy-tailed in the under-resolved cases (the
+ionisation counts of the dx = 8 lambda_De discharge span 111..3961 births
+over 64 seeds), which a normal-theory bound on a few runs cannot hold.  The
+oracle's cost (about 37 ms per step of the resolved discharge on one host
+core) sets the run lengths: 1500 steps (2 RF periods) for the resolved
+runs, 3000 for the others; the oracle runs go to host threads (one per run)
+while the GPU ensemble runs."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_13092_gb300 import inputs as I
+from ensemble import compare
+from helpers import oracle_from_config, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+GPU_SEEDS = tuple(range(300, 364))
+ORACLE_SEEDS = (400, 401, 402, 403)
+PROFILES = ("ne", "ni", "phi", "Te", "Ti")
+SAMPLE_EVERY = 15
+
+
+def _doubling114(seed, scheme=I.EC):
+    edges = oracle.doubling_grid(1024, I.L_GAP, 0.05, 4, 32)
+    assert edges.size - 1 == 114
+    return I.config_nonuniform(edges, seed=seed, scheme=scheme)
+
+
+CASES = {
+    # name: (config factory, steps)
+    "resolved-EC": (lambda s: I.config_resolved(seed=s, scheme=I.EC), 1500),
+    "resolved-MC": (lambda s: I.config_resolved(seed=s, scheme=I.MC), 1500),
+    "dx8-EC": (lambda s: I.config_sweep(8, seed=s, scheme=I.EC), 3000),
+    "tanh114-EC": (lambda s: I.config_tanh(seed=s, scheme=I.EC), 3000),
+    "doubling114-EC": (lambda s: _doubling114(s), 3000),
+}
+
+
+def _cfg(case, seed):
+    make, steps = CASES[case]
+    c = make(seed)
+    c.sample_every = SAMPLE_EVERY
+    c.n_steps = steps
+    I.with_headroom(c, 3.0)
+    return c
+
+
+def _summary(avg, species, steps):
+    out = dict(ne=np.asarray(avg["density"][0], float), ni=np.asarray(avg["density"][1], float),
+               phi=np.asarray(avg["phi"], float), Te=np.asarray(avg["Tx"][0], float),
+               Ti=np.asarray(avg["Tx"][1], float))
+    e, i = species[0], species[1]
+    out["rates"] = np.array([e["collisions"][0], e["collisions"][1], e["collisions"][2],
+                             i["collisions"][0], i["collisions"][1], e["births"],
+                             e["absorbed_left"] + e["absorbed_right"],
+                             i["absorbed_left"] + i["absorbed_right"]], float) / steps
+    return out
+
+
+def _oracle_run(case, seed):
+    c = _cfg(case, seed)
+    o = oracle_from_config(c)
+    o.step(c.n_steps, allow_capacity=True)
+    res = _summary(o.averages(), o.counters()["species"], c.n_steps)
+    o.close()
+    return res
+
+
+@pytest.fixture(scope="module")
+def ensembles():
+    require_gpu()
+    from paper_2308_13092_gb300 import ecpic
+    jobs = [(case, s) for case in CASES for s in ORACLE_SEEDS]
+    threads = min(len(jobs), max(1, os.cpu_count() or 1))
+    with ThreadPoolExecutor(threads) as ex:
+        # the oracle runs on host threads while the GPU ensembles run
+        futs = {job: ex.submit(_oracle_run, *job) for job in jobs}
+        seeds = GPU_SEEDS + ORACLE_SEEDS
+        eng = ecpic.Engine(max_slots=len(CASES) * len(seeds), max_cells=1024)
+        tickets = {(case, s): eng.submit(_cfg(case, s)) for case in CASES for s in seeds}
+        for _ in range(1000):
+            r, q = eng.pump(500)
+            if r == 0 and q == 0:
+                break
+        gpu = {case: {} for case in CASES}
+        for (case, s), t in tickets.items():
+            res = eng.poll(t, diagnostics=True, profiles=True)
+            assert res["state"] == 2, (case, s, res["state"])
+            d = res["diag"]
+            assert d["step"] == CASES[case][1]
+            gpu[case][s] = _summary(d, d["species"], CASES[case][1])
+        eng.close()
+        ora = {case: [futs[(case, s)].result() for s in ORACLE_SEEDS] for case in CASES}
+    return gpu, ora
+
+
+def _split(gpu, case, key, j=None):
+    get = (lambda r: r[key]) if j is None else (lambda r: r[key][j: j + 1])
+    G = [get(gpu[case][s]) for s in GPU_SEEDS]
+    Gp = [get(gpu[case][s]) for s in ORACLE_SEEDS]
+    return G, Gp
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_profiles_match_oracle_ensemble(ensembles, case):
+    gpu, ora = ensembles
+    lines = []
+    for key in PROFILES:
+        G, Gp = _split(gpu, case, key)
+        O = [o[key] for o in ora[case]]
+        lines.append(compare(G, Gp, O, f"{case} {key}"))
+    print("\n" + "\n".join(lines))
+
+
+RATES = ["e elastic", "excitation", "ionisation", "ion elastic", "charge exchange",
+         "births", "electron wall loss", "ion wall loss"]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_event_rates_match_oracle_ensemble(ensembles, case):
+    gpu, ora = ensembles
+    lines = []
+    for j, name in enumerate(RATES):
+        G, Gp = _split(gpu, case, "rates", j)
+        O = [o["rates"][j: j + 1] for o in ora[case]]
+        lines.append(compare(G, Gp, O, f"{case} rate {name}"))
+    print("\n" + "\n".join(lines))
