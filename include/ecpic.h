@@ -115,6 +115,11 @@ typedef struct {
   double* iedf;                               /* [s][iedf_bins] or NULL */
   double* iad;                                /* [s][iad_bins] or NULL */
   double* power;                              /* [s][N] or NULL */
+  /* particle rebalancing (ecpic_set_rebalance): groups of four merged,
+   * particles split, cells left alone (above 4096 particles), since init */
+  int64_t rb_merged[ECPIC_MAX_SPECIES];
+  int64_t rb_split[ECPIC_MAX_SPECIES];
+  int64_t rb_skipped[ECPIC_MAX_SPECIES];
 } ecpic_diag;
 
 /* ------------------------------------------------------------------ */
@@ -149,6 +154,46 @@ int ecpic_add_process(ecpic_run* run, int species, int kind, double threshold_eV
  * The paper is silent on the loading; a quiet start keeps the initial charge
  * noise, and the field energy it holds, near zero (App. B heating tests). */
 int ecpic_set_quiet_start(ecpic_run* run, int quiet);
+/* Particle rebalancing (Sec. 3d: on a non-uniform grid, keep the particles
+ * per cell near a target so that the cost follows the number of cells; the
+ * paper proposes this and gives no algorithm -- the rule is this library's).
+ * Before ecpic_init; EC and MC schemes.  Every particle then carries an
+ * integer weight multiplier k (it stands for k particles of the base weight
+ * w / m0, w the species weight given to ecpic_add_species); the deposit
+ * (Eq. 2-3, in units of 2^-32 base particle), moments, energies and tallies
+ * count k, and ionisation products inherit the parent's k.  Loaded particles
+ * (and ecpic_set_particles) get k = m0 (1..65536).  Every `every` steps
+ * (0: only ecpic_rebalance_now), after the field and the diagnostics sample
+ * of that level, per species and cell with n particles:
+ *  - n > hi (n <= 4096, else the cell is left alone and counted): order the
+ *    particles by (vx, id), cut the order into floor(n/4) groups of four and
+ *    merge the min(floor(n/4), ceil((n - target)/2)) groups nearest the
+ *    middle of that order (ties: the slower group), skipping groups of total
+ *    weight W > 65536; a group becomes two particles at its weighted centroid
+ *    of weights a = ceil(W/2), b = W - a and velocities u + sqrt(b/a) d and
+ *    u - sqrt(a/b) d (u the mean velocity, d = (s_x, +-s_y, +-s_z) the
+ *    per-component standard deviations, signs from Philox with counter
+ *    (id lo, id hi, level, (species << 8) | 0x10)), taking the group's two
+ *    smallest ids: CIC node charges, momentum and each component's second
+ *    moment (so the energy and the x temperature) are kept;
+ *  - 0 < n < lo: the min(target - n, #{k >= 2}) heaviest particles (ties:
+ *    smallest id) split in place into ceil(k/2) (same id) and floor(k/2)
+ *    (id = child of the id at this level, tag 3): nothing changes but the
+ *    count.
+ * 0 <= lo <= target <= hi, target <= 4096.  Counted in ecpic_diag rb_merged/rb_split/
+ * rb_skipped.  A plan that exceeds a species' capacity leaves the particles
+ * as they were and fails the run with ECPIC_ERR_CAPACITY. */
+int ecpic_set_rebalance(ecpic_run* run, int every, int target, int lo, int hi, uint32_t m0);
+/* Rebalance the run now, at its current level (synchronises). */
+int ecpic_rebalance_now(ecpic_run* run);
+/* Weight multipliers of a species' live particles, in the order of
+ * ecpic_get_particles (synchronises); ECPIC_ERR_ARG with *n set if cap is
+ * too small.  Runs with ecpic_set_rebalance only. */
+int ecpic_get_weights(ecpic_run* run, int species, uint32_t* k, int64_t cap, int64_t* n);
+/* Replace the multipliers of the particles set by the last
+ * ecpic_set_particles (n equal to its count; 1..65536 each); recomputes the
+ * current field. */
+int ecpic_set_weights(ecpic_run* run, int species, const uint32_t* k, int64_t n);
 /* Diagnostic tallies (Sec. 3a, Fig. 1; before ecpic_init):
  *  - EEDF: on sample steps, kinetic energies (eV) of the particles of every
  *    species with q < 0 in the cells whose centres lie within
@@ -297,6 +342,9 @@ typedef struct {
   int eedf_bins;
   double iedf_dE;
   int iedf_bins, iad_bins;
+  /* particle rebalancing as ecpic_set_rebalance; rb_m0 = 0 leaves it off */
+  int rb_every, rb_target, rb_lo, rb_hi;
+  uint32_t rb_m0;
 } ecpic_run_config;
 
 /* max_cells bounds N of every admitted run; species_per_run bounds their

@@ -1542,8 +1542,8 @@ int64_t oracle_get_averages(const or_run* r, double* density, double* phi,
 
 /* ------------------------------------------------------------------ */
 int oracle_set_rebalance(or_run* r, int every, int target, int lo, int hi, uint32_t m0) {
-  if (!r || every < 0 || (every > 0 && (target < 1 || lo < 0 || hi < target || lo > target)) ||
-      m0 < 1 || m0 > OR_RB_MAX_WEIGHT)
+  if (!r || every < 0 || target < 1 || target > OR_RB_MAX_CELL || lo < 0 || hi < target ||
+      lo > target || m0 < 1 || m0 > OR_RB_MAX_WEIGHT)
     return -1;
   if (r->initialized) return -2;
   r->rb_every = every; r->rb_target = target; r->rb_lo = lo; r->rb_hi = hi; r->rb_m0 = m0;

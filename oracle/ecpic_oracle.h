@@ -188,7 +188,7 @@ int oracle_nu_max(const or_run* r, int species, double* nu_max,
  * init: rebalance every `every` steps (0 = never), at level k+1 after the
  * field and the sample; merge in cells holding more than `hi` particles of a
  * species, split in cells holding fewer than `lo` (0 < n), aiming at
- * `target` (lo <= target <= hi); loaded particles (and set_particles) get
+ * `target` (lo <= target <= hi, target <= 4096); loaded particles (and set_particles) get
  * multiplier m0 (1..65536) and base weight w / m0. */
 int oracle_set_rebalance(or_run* r, int every, int target, int lo, int hi, uint32_t m0);
 /* one rebalancing of every species now, at the current level */

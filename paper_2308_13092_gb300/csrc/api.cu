@@ -226,6 +226,54 @@ int ecpic_set_tallies(ecpic_run* r, double center, double halfwidth, double eedf
   return v.empty() ? ECPIC_OK : fail(r, ECPIC_ERR_ARG, v);
 }
 
+int ecpic_set_rebalance(ecpic_run* r, int every, int target, int lo, int hi, uint32_t m0) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (r->batch) return fail(r, ECPIC_ERR_STATE, "before init");
+  if (every < 0 || target < 1 || target > ecpic::kRbMaxCell || lo < 0 || lo > target || hi < target ||
+      m0 < 1u || m0 > (uint32_t)ecpic::kRbMaxWeight)
+    return fail(r, ECPIC_ERR_ARG,
+                "bad rebalancing parameters (0 <= lo <= target <= hi, target <= 4096, 1 <= m0 <= 65536)");
+  r->spec.rb = true;
+  r->spec.rb_every = every;
+  r->spec.rb_target = target;
+  r->spec.rb_lo = lo;
+  r->spec.rb_hi = hi;
+  r->spec.rb_m0 = m0;
+  return ECPIC_OK;
+}
+
+int ecpic_rebalance_now(ecpic_run* r) {
+  if (!r) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  return guarded(r, [&]() -> int {
+    std::string err;
+    const int rc = r->batch->rebalance_now(0, &err);
+    return rc ? fail(r, rc, err) : ECPIC_OK;
+  });
+}
+
+int ecpic_get_weights(ecpic_run* r, int species, uint32_t* k, int64_t cap, int64_t* n) {
+  if (!r || !n) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  return guarded(r, [&]() -> int {
+    std::string err;
+    long long m = 0;
+    const int rc = r->batch->get_weights(0, species, k, cap, &m, &err);
+    *n = m;
+    return rc ? fail(r, rc, err) : ECPIC_OK;
+  });
+}
+
+int ecpic_set_weights(ecpic_run* r, int species, const uint32_t* k, int64_t n) {
+  if (!r || n < 0) return ECPIC_ERR_ARG;
+  if (!r->batch) return fail(r, ECPIC_ERR_STATE, "init first");
+  return guarded(r, [&]() -> int {
+    std::string err;
+    const int rc = r->batch->set_weights(0, species, k, n, &err);
+    return rc ? fail(r, rc, err) : ECPIC_OK;
+  });
+}
+
 int ecpic_set_quiet_start(ecpic_run* r, int quiet) {
   if (!r || (quiet != 0 && quiet != 1)) return ECPIC_ERR_ARG;
   if (r->batch) return fail(r, ECPIC_ERR_STATE, "before init");

@@ -23,13 +23,20 @@ constexpr int kMaxSpecies = ECPIC_MAX_SPECIES;
 constexpr int kMaxProc = ECPIC_MAX_PROC;
 constexpr int kMaxCells = ECPIC_MAX_CELLS;
 constexpr int kMaxSeg = 1024;  // slots * species per batch
-constexpr int kNumCtr = 16;    // counters per species, see Ctr
+constexpr int kNumCtr = 20;    // counters per species, see Ctr
 
 // per-species counters in RunState::ctr
 enum Ctr {
   C_ABS_L = 0, C_ABS_R = 1, C_BIRTHS = 2, C_LOST = 3, C_CLAMPS = 4, C_CAND = 5,
-  C_NAN = 6, C_IMP_LOST = 7, C_COLL0 = 8  // C_COLL0 + p, p < kMaxProc
+  C_NAN = 6, C_IMP_LOST = 7, C_COLL0 = 8,  // C_COLL0 + p, p < kMaxProc
+  C_RB_MERGED = 16, C_RB_SPLIT = 17, C_RB_SKIPPED = 18  // particle rebalancing
 };
+
+// particle rebalancing limits: cells above kRbMaxCell particles of a species
+// are left alone, groups heavier than kRbMaxWeight base particles are not
+// merged (the weighted deposit's 64-bit sums stay far from overflow)
+constexpr int kRbMaxCell = 4096;
+constexpr unsigned kRbMaxWeight = 65536u;
 
 struct ProcDev {
   int kind;
@@ -67,6 +74,10 @@ struct RunDev {
   int N, bc, scheme, uniform, ns;
   int seg0;             // first segment of this run (segments seg0..seg0+ns-1)
   int sample_every;
+  // particle rebalancing: weight multipliers on (the segments' wt arrays),
+  // every rb_every steps (0: only on demand), merge above rb_hi particles of
+  // a species in a cell, split below rb_lo, aiming at rb_target
+  int rb, rb_every, rb_target, rb_lo, rb_hi, rb_pad;
   double L, dt;
   float dtdx_u;         // dt/dx on a uniform grid
   float ng;             // gas density
@@ -118,6 +129,9 @@ struct RunState {
   double fe;                    // at the level of the last sampled push
   double phi0;                  // electrode potential of the current field
   long long phi_level;          // time level of the potential held in phi
+  long long rb_level;           // level of the last rebalancing (-1: none)
+  int rb_force;                 // rebalance at the current level whatever the cadence
+  int rb_pad;
   unsigned long long psteps;    // particle-steps advanced (live at the start of each step)
   unsigned long long ctr[kMaxSpecies][kNumCtr];
 };
@@ -133,7 +147,7 @@ struct __align__(16) RealRec {
   float vx, vy, vz;
   int c;
   float f;
-  int pad;
+  unsigned k;       // weight multiplier (1 without rebalancing)
 };
 static_assert(sizeof(RealRec) == 48, "RealRec layout");
 
@@ -144,6 +158,7 @@ struct SegDev {
   float* vy[2];
   float* vz[2];
   uint64_t* id[2];
+  uint32_t* wt[2];      // weight multipliers (rebalancing runs only, else null)
   long long cap;
   int run;              // slot index
   int species;
@@ -167,11 +182,12 @@ struct SegState {
   long long n_real;     // records in SegDev::real this step (reset by the field kernel)
   long long n_imp;      // entries in SegDev::imp this step (reset by the field kernel)
   int cur;              // current buffer set
-  int pad;
+  int rb_over;          // rebalancing: the planned particles exceed the capacity
+  long long n_rb;       // rebalancing: particles after the merges and splits
 };
 
 // kernel modes for the segment-walking kernels
-enum PassMode { MODE_STEP = 0, MODE_REFRESH = 1, MODE_SORT = 2 };
+enum PassMode { MODE_STEP = 0, MODE_REFRESH = 1, MODE_SORT = 2, MODE_REBAL = 3 };
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.

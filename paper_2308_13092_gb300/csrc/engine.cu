@@ -104,6 +104,14 @@ int spec_from_config(const ecpic_run_config* c, int64_t n_steps, RunSpec* s, std
     return ECPIC_ERR_ARG;
   }
   s->quiet = c->quiet_start;
+  if (c->rb_m0 > 0) {  // particle rebalancing (rb_m0 = 0: off)
+    s->rb = true;
+    s->rb_every = c->rb_every;
+    s->rb_target = c->rb_target;
+    s->rb_lo = c->rb_lo;
+    s->rb_hi = c->rb_hi;
+    s->rb_m0 = c->rb_m0;
+  }
   if (c->eedf_bins > 0) {
     s->eedf_center = c->eedf_center;
     s->eedf_halfwidth = c->eedf_halfwidth;

@@ -113,6 +113,9 @@ __device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int
   if (mode == MODE_REFRESH) return slot == only;
   if (S.status != 0) return false;
   if (mode == MODE_STEP) return S.step < S.step_end;
+  if (mode == MODE_REBAL)  // a rebalancing run at a rebalancing level (once per level)
+    return R.rb && (S.rb_force || (R.rb_every > 0 && S.step > 0 && S.step % R.rb_every == 0 &&
+                                   S.rb_level != S.step));
   return true;
 }
 
@@ -234,6 +237,35 @@ __device__ void dep_flush(uint32_t* dcnt, uint32_t* dlo, uint32_t* dhi, int a, i
   }
 }
 
+// ---- weighted CIC deposit (rebalancing runs) -----------------------------
+// A particle of weight multiplier k adds k (2^32 - r) to node c and k r to
+// node c+1 (64-bit shared sums, one per node).  With k <= kRbMaxWeight = 2^16
+// a particle adds at most 2^48 to a node, so flushing every kFlushParticles/2
+// = 2^15 particles keeps every sum below 2^63.
+__device__ __forceinline__ void depw_add4(unsigned long long* d64, const int c[4], const float f[4],
+                                          const unsigned k[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (c[j] >= 0) {
+      const unsigned long long r = __float2uint_rz(f[j] * 4294967296.0f);
+      atomicAdd(d64 + c[j], (unsigned long long)k[j] * (4294967296ull - r));
+      atomicAdd(d64 + c[j] + 1, (unsigned long long)k[j] * r);
+    }
+  }
+}
+
+// Adds the sums of nodes [a, e] to S and clears them; every thread of the
+// block calls it, between barriers.
+__device__ void depw_flush(unsigned long long* d64, int a, int e, unsigned long long* S) {
+  for (int n = a + (int)threadIdx.x; n <= e; n += (int)blockDim.x) {
+    const unsigned long long v = d64[n];
+    if (v) {
+      atomicAdd(S + n, v);
+      d64[n] = 0ull;
+    }
+  }
+}
+
 // ---- quadratic-spline deposit of the EC2 scheme (uniform grids) ----------
 // A particle at cell + xi with r = floor(xi 2^32) has its nearest node
 // n0 = cell + (r >= 2^31) and offset U = r or r - 2^32 (2^-32 cell units);
@@ -322,10 +354,10 @@ __device__ __forceinline__ void deposit2_one(unsigned long long* S, int c, float
   atomicAdd(S + node2(n0 + 1, N, periodic), (unsigned long long)b);
 }
 
-__device__ __forceinline__ void deposit_one(unsigned long long* S, int c, float f) {
+__device__ __forceinline__ void deposit_one(unsigned long long* S, int c, float f, unsigned k = 1u) {
   const unsigned r = __float2uint_rz(f * 4294967296.0f);
-  atomicAdd(S + c, 4294967296ull - (unsigned long long)r);
-  atomicAdd(S + c + 1, (unsigned long long)r);
+  atomicAdd(S + c, (unsigned long long)k * (4294967296ull - (unsigned long long)r));
+  atomicAdd(S + c + 1, (unsigned long long)k * (unsigned long long)r);
 }
 
 // ----------------------------------------------------------------- MCC helpers
@@ -389,7 +421,8 @@ __device__ __forceinline__ void set_status(RunState* st, int code) {
 
 // append a particle to a segment (births); false if the capacity is full
 __device__ __forceinline__ bool append_particle(const SegDev& G, SegState* ss, int c, float f,
-                                                float vx, float vy, float vz, uint64_t id) {
+                                                float vx, float vy, float vz, uint64_t id,
+                                                unsigned k = 1u) {
   const long long idx = (long long)atomicAdd((unsigned long long*)&ss->n_alloc, 1ull);
   if (idx >= G.cap) return false;
   const int cur = ss->cur;
@@ -399,6 +432,7 @@ __device__ __forceinline__ bool append_particle(const SegDev& G, SegState* ss, i
   G.vy[cur][idx] = vy;
   G.vz[cur][idx] = vz;
   G.id[cur][idx] = id;
+  if (G.wt[cur]) G.wt[cur][idx] = k;
   return true;
 }
 
@@ -446,7 +480,7 @@ struct PassShared {
 // velocity.
 __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int c, float f, uint64_t id,
                                       long long k, float Erem, bool sample, float d0, float d1,
-                                      float d2) {
+                                      float d2, unsigned kw) {
   const SegDev& G = b.segs[s];
   const int slot = G.run, sp = G.species;
   const RunDev* R = b.runs + slot;
@@ -467,23 +501,25 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   box_muller(u24_open(Cw.z), u24(Cw.w), z2, z3);
   const float sd = R->vth_gas;
   atomicAdd(&st->ctr[sp][C_BIRTHS], 1ull);
-  // secondary electron: same segment and species
+  // secondary electron: same segment and species; both products carry the
+  // parent's weight multiplier kw (charge conserved)
   const float vb = v2 * e0;
-  if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1))) {
+  const float fk = (float)kw;
+  if (append_particle(G, ss, c, f, vb, v2 * e1, v2 * e2, child_id(id, k, 1), kw)) {
     if (R->scheme >= ECPIC_SCHEME_EC2)
       deposit2_one(R->S + (size_t)sp * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
     else
-      deposit_one(R->S + (size_t)sp * (N + 1), c, f);
+      deposit_one(R->S + (size_t)sp * (N + 1), c, f, kw);
     if (sample && SP->q < 0.0 && c >= R->eedf_c0 && c <= R->eedf_c1)
       atomicAdd(R->tal + (size_t)sp * R->tal_stride +
                     tally_bin(kin_eV(SP->half_m_over_e, vb, yz2(v2 * e1, v2 * e2)), R->eedf_dEinv, R->eedf_n),
-                1ull);
+                (unsigned long long)kw);
     if (sample) {
       double* md = R->momd + (size_t)sp * 2 * (N + 1);
-      atomicAdd(md + c, (double)((1.0f - f) * vb));
-      atomicAdd(md + c + 1, (double)(f * vb));
-      atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * vb * vb));
-      atomicAdd(md + (N + 1) + c + 1, (double)(f * vb * vb));
+      atomicAdd(md + c, (double)(fk * ((1.0f - f) * vb)));
+      atomicAdd(md + c + 1, (double)(fk * (f * vb)));
+      atomicAdd(md + (N + 1) + c, (double)(fk * ((1.0f - f) * vb * vb)));
+      atomicAdd(md + (N + 1) + c + 1, (double)(fk * (f * vb * vb)));
     }
   } else {
     atomicAdd(&st->ctr[sp][C_LOST], 1ull);
@@ -494,17 +530,17 @@ __device__ __noinline__ float3 ionize(const BatchView& b, int s, int chosen, int
   if (chk(ps >= 0 && ps < b.nseg, 18, ps, b.nseg)) {
     const int pspec = SP->proc[chosen].product_species;
     const float ivx = sd * z0;
-    if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2))) {
+    if (append_particle(b.segs[ps], b.sst + ps, c, f, ivx, sd * z1, sd * z2, child_id(id, k, 2), kw)) {
       if (R->scheme >= ECPIC_SCHEME_EC2)
         deposit2_one(R->S + (size_t)pspec * (N + 1), c, f, N, R->bc == ECPIC_PERIODIC);
       else
-        deposit_one(R->S + (size_t)pspec * (N + 1), c, f);
+        deposit_one(R->S + (size_t)pspec * (N + 1), c, f, kw);
       if (sample) {
         double* md = R->momd + (size_t)pspec * 2 * (N + 1);
-        atomicAdd(md + c, (double)((1.0f - f) * ivx));
-        atomicAdd(md + c + 1, (double)(f * ivx));
-        atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * ivx * ivx));
-        atomicAdd(md + (N + 1) + c + 1, (double)(f * ivx * ivx));
+        atomicAdd(md + c, (double)(fk * ((1.0f - f) * ivx)));
+        atomicAdd(md + c + 1, (double)(fk * (f * ivx)));
+        atomicAdd(md + (N + 1) + c, (double)(fk * ((1.0f - f) * ivx * ivx)));
+        atomicAdd(md + (N + 1) + c + 1, (double)(fk * (f * ivx * ivx)));
       }
     } else {
       atomicAdd(&st->ctr[pspec][C_LOST], 1ull);
@@ -525,9 +561,10 @@ __device__ __noinline__ void tally_impact(const BatchView& b, int s, int slot, i
   const float vx = G.vx[cur][i], yz = yz2(G.vy[cur][i], G.vz[cur][i]);
   const float E = kin_eV(R->sp[sp].half_m_over_e, vx, yz);
   const float th = atan2f(sqrtf(yz), fabsf(vx)) * 57.295779513082323f;
+  const unsigned long long kw = G.wt[cur] ? (unsigned long long)G.wt[cur][i] : 1ull;
   unsigned long long* tal = R->tal + (size_t)sp * R->tal_stride + R->eedf_n;
-  atomicAdd(tal + tally_bin(E, R->iedf_dEinv, R->iedf_n), 1ull);
-  atomicAdd(tal + R->iedf_n + tally_bin(th, R->iad_binv, R->iad_n), 1ull);
+  atomicAdd(tal + tally_bin(E, R->iedf_dEinv, R->iedf_n), kw);
+  atomicAdd(tal + R->iedf_n + tally_bin(th, R->iad_binv, R->iad_n), kw);
 }
 
 // A real (non-null) collision as recorded by the pass (Sec. 2a step 6):
@@ -584,7 +621,7 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
     const float v1 = sqrtf(SP->two_e_over_m * (En - thr));
     vx = v1 * d0; vy = v1 * d1; vz = v1 * d2;
   } else if (kind == ECPIC_IONIZATION) {
-    const float3 v1 = ionize(b, s, chosen, c, f, id, k, En - thr, sample, d0, d1, d2);
+    const float3 v1 = ionize(b, s, chosen, c, f, id, k, En - thr, sample, d0, d1, d2, rec.k);
     vx = v1.x; vy = v1.y; vz = v1.z;
   } else if (kind == ECPIC_ION_ELASTIC) {
     const float h = SP->m_frac * gm;
@@ -603,17 +640,18 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
     const int b1 = tally_bin(kin_eV(SP->half_m_over_e, vx, yz2(vy, vz)), R->eedf_dEinv, R->eedf_n);
     if (b0 != b1) {
       unsigned long long* tal = R->tal + (size_t)sp * R->tal_stride;
-      atomicAdd(tal + b0, ~0ull);  // minus one, modulo 2^64
-      atomicAdd(tal + b1, 1ull);
+      atomicAdd(tal + b0, 0ull - (unsigned long long)rec.k);  // minus k, modulo 2^64
+      atomicAdd(tal + b1, (unsigned long long)rec.k);
     }
   }
   if (sample) {
     double* md = R->momd + (size_t)sp * 2 * (N + 1);
+    const float fk = (float)rec.k;
     const float d1v = vx - vx_old, d2v = vx * vx - vx_old * vx_old;
-    atomicAdd(md + c, (double)((1.0f - f) * d1v));
-    atomicAdd(md + c + 1, (double)(f * d1v));
-    atomicAdd(md + (N + 1) + c, (double)((1.0f - f) * d2v));
-    atomicAdd(md + (N + 1) + c + 1, (double)(f * d2v));
+    atomicAdd(md + c, (double)(fk * ((1.0f - f) * d1v)));
+    atomicAdd(md + c + 1, (double)(fk * (f * d1v)));
+    atomicAdd(md + (N + 1) + c, (double)(fk * ((1.0f - f) * d2v)));
+    atomicAdd(md + (N + 1) + c + 1, (double)(fk * (f * d2v)));
   }
 }
 
@@ -629,11 +667,12 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
 // 32-byte sectors anyway) and on energy-sample steps; otherwise the test
 // reads them per candidate.
 //
-// Compiled three times (KIND): 0 = ordinary steps of the linear schemes (the
+// Compiled four times (KIND): 0 = ordinary steps of the linear schemes (the
 // common case), 1 = their energy-sample steps (moments, energy, EEDF, J.E),
-// 2 = the EC2 scheme with the sample decision taken at run time.  Keeping the
-// rare code out of the common instance keeps its loop small in the
-// instruction cache.
+// 2 = the EC2 scheme with the sample decision taken at run time, 3 = the
+// linear schemes with per-particle weight multipliers (rebalancing runs),
+// sample decision at run time.  Keeping the rare code out of the common
+// instance keeps its loop small in the instruction cache.
 // L2 prefetch of a byte range (one bulk instruction; 16-byte aligned start,
 // size a multiple of 16)
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -660,8 +699,11 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const uint64_t* pid = G.id[cur];
   const long long k = st->step;
   const bool stepping = (mode == MODE_STEP);
+  constexpr bool weighted = KIND == 3;
+  const uint32_t* pwt = weighted ? G.wt[cur] : nullptr;
   const bool sample = KIND == 1 ||
-                      (KIND == 2 && stepping && R->sample_every > 0 && ((k + 1) % R->sample_every) == 0);
+                      ((KIND == 2 || KIND == 3) && stepping && R->sample_every > 0 &&
+                       ((k + 1) % R->sample_every) == 0);
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
   // the run's field staged in shared memory for the gather (after the rings)
@@ -705,6 +747,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   uint32_t* dcnt = dep;
   uint32_t* dlo = dep + (b.nmax + 1);
   uint32_t* dhi = dep + 2 * (b.nmax + 1);
+  // weighted runs: one 64-bit sum per node over the first two arrays
+  unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dep);
   unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   int since_flush = 0;
 
@@ -731,6 +775,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
                 l2_prefetch(pvz + p0, b4);
               }
               if (mcc) l2_prefetch(pid + p0, (unsigned)(((p1 - p0) * 8) & ~15ll));
+              if (weighted) l2_prefetch(pwt + p0, b4);
             }
           }
         }
@@ -755,6 +800,16 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           c[j] = in ? pc[i0 + j] : -1;
           f[j] = in ? pxi[i0 + j] : 0.0f;
           v[j] = in ? pvx[i0 + j] : 0.0f;
+        }
+      }
+      unsigned kq[4] = {1u, 1u, 1u, 1u};  // weight multipliers
+      if (weighted) {
+        if (full) {
+          const uint4 k4 = *reinterpret_cast<const uint4*>(pwt + i0);
+          kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) kq[j] = (inq && i0 + j < n) ? pwt[i0 + j] : 1u;
         }
       }
       bool cand[4] = {false, false, false, false};
@@ -833,9 +888,15 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
         for (int j = 0; j < 4; ++j) {
           const float vnew = v[j] + qm_dt * Ei[j];
           if (sample && c[j] >= 0) {
-            keq += v[j] * vnew + yz[j];
-            // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
-            atomicAdd(Psm + c[j], (v[j] + vnew) * Ei[j]);
+            if (weighted) {
+              const float fk = (float)kq[j];
+              keq += fk * (v[j] * vnew + yz[j]);
+              atomicAdd(Psm + c[j], fk * ((v[j] + vnew) * Ei[j]));
+            } else {
+              keq += v[j] * vnew + yz[j];
+              // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
+              atomicAdd(Psm + c[j], (v[j] + vnew) * Ei[j]);
+            }
           }
           v[j] = vnew;
         }
@@ -940,7 +1001,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (c[j] >= ec0 && c[j] <= ec1)
-              atomicAdd(tal + tally_bin(kin_eV(SP->half_m_over_e, v[j], yz[j]), R->eedf_dEinv, R->eedf_n), 1ull);
+              atomicAdd(tal + tally_bin(kin_eV(SP->half_m_over_e, v[j], yz[j]), R->eedf_dEinv, R->eedf_n),
+                        (unsigned long long)kq[j]);
         }
         if (mcc) {
           // a candidate with Rr >= nu_bnd |g| is a null collision whatever its
@@ -974,6 +1036,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       // (pre-collision: the collision adds the change)
       if (order2)
         dep2_add4(dlo, dhi, N, !walls, c, f);
+      else if (weighted)
+        depw_add4(d64, c, f, kq);
       else
         dep_add4(dcnt, dlo, dhi, c, f);
 #pragma unroll
@@ -983,10 +1047,11 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           my_hi = max(my_hi, c[j] + 1);
           if (sample && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
             const int Nm = b.nmax + 1;
-            atomicAdd(Msm + c[j], (1.0f - f[j]) * v[j]);
-            atomicAdd(Msm + c[j] + 1, f[j] * v[j]);
-            atomicAdd(Msm + Nm + c[j], (1.0f - f[j]) * v[j] * v[j]);
-            atomicAdd(Msm + Nm + c[j] + 1, f[j] * v[j] * v[j]);
+            const float fk = weighted ? (float)kq[j] : 1.0f;
+            atomicAdd(Msm + c[j], fk * ((1.0f - f[j]) * v[j]));
+            atomicAdd(Msm + c[j] + 1, fk * (f[j] * v[j]));
+            atomicAdd(Msm + Nm + c[j], fk * ((1.0f - f[j]) * v[j] * v[j]));
+            atomicAdd(Msm + Nm + c[j] + 1, fk * (f[j] * v[j] * v[j]));
           }
         }
       }
@@ -1049,7 +1114,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
               dst[0] = make_int4((int)(uint32_t)id, (int)(uint32_t)(id >> 32), i, chosen);
               dst[1] = make_int4(__float_as_int(En), __float_as_int(gm), __float_as_int(pvx[i]),
                                  __float_as_int(pvy[i]));
-              dst[2] = make_int4(__float_as_int(pvz[i]), pc[i], __float_as_int(pxi[i]), 0);
+              dst[2] = make_int4(__float_as_int(pvz[i]), pc[i], __float_as_int(pxi[i]),
+                                 weighted ? (int)pwt[i] : 1);
             } else {
               set_status(st, ECPIC_ERR_CAPACITY);
             }
@@ -1062,10 +1128,12 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       }
     }
     if (!more) break;
-    if (++since_flush == (order2 ? kFlushIters / 4 : kFlushIters)) {
+    if (++since_flush == (order2 ? kFlushIters / 4 : weighted ? kFlushIters / 2 : kFlushIters)) {
       __syncthreads();
       if (order2)
         dep2_flush(dlo, dhi, 0, N, Sg);
+      else if (weighted)
+        depw_flush(d64, 0, N, Sg);
       else
         dep_flush(dcnt, dlo, dhi, 0, N, Sg);
       __syncthreads();
@@ -1113,6 +1181,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   if (flo < fhi) {
     if (order2)  // shares reach one node beyond the range, or wrap
       dep2_flush(dlo, dhi, walls ? max(flo - 1, 0) : 0, walls ? min(fhi + 1, N) : N, Sg);
+    else if (weighted)  // nodes flo..fhi (a cell's two nodes)
+      depw_flush(d64, flo, fhi, Sg);
     else
       dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
   }
@@ -1194,6 +1264,8 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
     if (R.scheme >= ECPIC_SCHEME_EC2)  // EC2, MC2
       pass_piece<2, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    else if (R.rb)  // weight multipliers
+      pass_piece<3, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else if (smp)
       pass_piece<1, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else
@@ -1241,6 +1313,7 @@ __global__ void __launch_bounds__(kCollideBlock) k_collide(BatchView b) {
         rec.vz = __int_as_float(w2.x);
         rec.c = w2.y;
         rec.f = __int_as_float(w2.z);
+        rec.k = (unsigned)w2.w;
       }
     }
     const bool ok = valid && rec.chosen >= 0 && rec.chosen < kMaxProc;
@@ -1556,7 +1629,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_phi(BatchView b, int slot) {
 }
 
 // ----------------------------------------------------------------- sort
-__global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
+__global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   int* H = reinterpret_cast<int*>(pre + b.nseg + 1);
@@ -1568,7 +1641,7 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
     lohi[1] = -1;
   }
   // quads of four particles per thread, as in the pass
-  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm, 4);
+  const long long T = seg_prefix(b, mode, -1, pre, wsm, 4);
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -1633,12 +1706,12 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b) {
 }
 
 // per segment: counts -> exclusive cursors; live total
-__global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b) {
+__global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b, int mode) {
   const int s = blockIdx.x;
   if (s >= b.nseg) return;
   const SegDev& G = b.segs[s];
   const int slot = G.run;
-  if (!run_live(b.runs[slot], b.rst[slot], MODE_SORT, -1, slot)) return;
+  if (!run_live(b.runs[slot], b.rst[slot], mode, -1, slot)) return;
   __shared__ long long wsm[32];
   const int N = b.runs[slot].N;
   int* h = b.hist + G.hoff;
@@ -1656,13 +1729,13 @@ __global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b) {
   if (threadIdx.x == 0) b.sst[s].n_live = total;
 }
 
-__global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
+__global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
   __shared__ long long wsm[32];
   // quads of four particles per thread; every field is loaded before the
   // cursor atomics so the loads overlap
-  const long long T = seg_prefix(b, MODE_SORT, -1, pre, wsm, 4);
+  const long long T = seg_prefix(b, mode, -1, pre, wsm, 4);
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -1684,11 +1757,13 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
     const float* sv = G.vy[src];
     const float* sw = G.vz[src];
     const uint64_t* si = G.id[src];
+    const uint32_t* sk = G.wt[src];  // weight multipliers (rebalancing runs)
     for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
       const long long i0 = 4 * (base + lane);
       int c[4];
       float x[4], u[4], v[4], w[4];
       uint64_t id[4];
+      unsigned kq[4] = {1u, 1u, 1u, 1u};
       if (base + lane < end && i0 + 3 < n && chk(i0 + 3 < G.cap, 27, i0, G.cap)) {
         const int4 c4 = *reinterpret_cast<const int4*>(sc + i0);
         const float4 x4 = *reinterpret_cast<const float4*>(sx + i0);
@@ -1703,6 +1778,10 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
         v[0] = v4.x; v[1] = v4.y; v[2] = v4.z; v[3] = v4.w;
         w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
         id[0] = a.x; id[1] = a.y; id[2] = a2.x; id[3] = a2.y;
+        if (sk) {
+          const uint4 k4 = *reinterpret_cast<const uint4*>(sk + i0);
+          kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -1713,6 +1792,7 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
           v[j] = in ? sv[i0 + j] : 0.f;
           w[j] = in ? sw[i0 + j] : 0.f;
           id[j] = in ? si[i0 + j] : 0ull;
+          if (sk && in) kq[j] = sk[i0 + j];
         }
       }
 #pragma unroll
@@ -1732,6 +1812,7 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
           G.vy[dst][d] = v[j];
           G.vz[dst][d] = w[j];
           G.id[dst][d] = id[j];
+          if (sk) G.wt[dst][d] = kq[j];
         }
       }
     }
@@ -1739,6 +1820,7 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b) {
 }
 
 __global__ void __launch_bounds__(kPassBlock) k_finalize(BatchView b) {
+  // (the counting sort's last phase; rebalancing ends with k_rb_finalize)
   const int s = blockIdx.x;
   if (s >= b.nseg) return;
   const SegDev& G = b.segs[s];
@@ -1752,6 +1834,400 @@ __global__ void __launch_bounds__(kPassBlock) k_finalize(BatchView b) {
     ss->n_proc = ss->n_live;
     ss->n_alloc = ss->n_live;
     ss->n_dead = 0;
+  }
+}
+
+// ----------------------------------------------------------------- rebalancing
+// Particle rebalancing (Sec. 3d proposes keeping the particles per cell near a
+// target on non-uniform grids; the rule is this library's design, the same as
+// the oracle's).  It runs for the runs due at their current level (after the
+// field kernel of that level): a counting sort by cell into the other buffer
+// set (k_hist, k_scan, k_scatter in MODE_REBAL), then per (segment, cell):
+//   - more than rb_hi particles (at most kRbMaxCell): order them by (vx, id),
+//     cut the order into floor(n/4) groups of four, merge the
+//     G = min(floor(n/4), ceil((n - target)/2)) groups nearest the middle of
+//     the order (ties: the slower), skipping groups heavier than
+//     kRbMaxWeight; a group becomes two particles at its weighted centroid
+//     with velocities u + sqrt(b/a) d, u - sqrt(a/b) d (u the mean velocity,
+//     d the per-component standard deviations with Philox signs for y and z,
+//     a = ceil(W/2), b = W - a), taking the group's two smallest ids;
+//   - fewer than rb_lo (and some): split the min(target - n, #{k >= 2})
+//     heaviest (ties: smallest id) in place into ceil(k/2) (same id) and
+//     floor(k/2) (id child_id(id, level, 3));
+//   - otherwise copied.
+// k_rb_plan counts each cell's output, k_rb_scan places the cells,
+// k_rb_apply writes them back into the current buffer set, k_rb_finalize and
+// k_rb_mark set the sizes and the run's rebalancing level.
+constexpr int kRbBlock = 256;
+constexpr int kRbGroups = kRbMaxCell / 4;
+
+struct RbSmem {
+  unsigned long long k2[kRbMaxCell];  // second key: id
+  uint32_t k1[kRbMaxCell];            // first key: monotone vx bits, or ~k
+  uint16_t ix[kRbMaxCell];            // index within the cell
+  uint16_t pref[kRbGroups];           // eligible groups before each order position
+  uint8_t el[kRbGroups];              // group at an order position may merge
+};
+
+// FP32 bits ordered like the values (+0 and -0 as one value)
+__device__ __forceinline__ uint32_t rb_fkey(float v) {
+  const uint32_t u = __float_as_uint(v == 0.0f ? 0.0f : v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// ascending bitonic sort of P (a power of two) entries by (k1, k2)
+__device__ void rb_bitonic(RbSmem& sm, int P) {
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+        const int i = 2 * stride * (t / stride) + (t % stride);
+        const int j = i + stride;
+        const bool up = (i & size) == 0;
+        const bool gt = sm.k1[i] > sm.k1[j] || (sm.k1[i] == sm.k1[j] && sm.k2[i] > sm.k2[j]);
+        if (gt == up) {
+          const uint32_t a = sm.k1[i]; sm.k1[i] = sm.k1[j]; sm.k1[j] = a;
+          const unsigned long long c = sm.k2[i]; sm.k2[i] = sm.k2[j]; sm.k2[j] = c;
+          const uint16_t x = sm.ix[i]; sm.ix[i] = sm.ix[j]; sm.ix[j] = x;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// order position of merge group g among ng groups: by distance from the
+// middle of the velocity order, the slower group first on a tie
+__device__ __forceinline__ int rb_pos(int g, int ng) {
+  const int d = 2 * g - (ng - 1);
+  return (d < 0 ? -d : d) - (d < 0 ? 1 : 0);
+}
+
+__device__ __forceinline__ void rb_copy(const SegDev& G, int in, int out, long long i, long long o) {
+  G.cell[out][o] = G.cell[in][i];
+  G.xi[out][o] = G.xi[in][i];
+  G.vx[out][o] = G.vx[in][i];
+  G.vy[out][o] = G.vy[in][i];
+  G.vz[out][o] = G.vz[in][i];
+  G.id[out][o] = G.id[in][i];
+  G.wt[out][o] = G.wt[in][i];
+}
+
+// One cell: the particles [start, start + n) of buffer set `in` (sorted by
+// cell).  Returns the cell's output count; when write, the output goes to
+// buffer set `out` from position obase and the counters are updated.  Every
+// thread of the block calls it (block-uniform arguments).
+__device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n, bool write,
+                       long long obase, RbSmem& sm, long long* wsm) {
+  const SegDev& G = b.segs[s];
+  const int slot = G.run, sp = G.species;
+  const RunDev* R = b.runs + slot;
+  RunState* st = b.rst + slot;
+  const int out = b.sst[s].cur, in = out ^ 1;
+  const int T = R->rb_target;
+  int mode = 0;  // 0 copy, 1 merge, 2 split, 3 skip (copy, counted)
+  if (n > R->rb_hi) mode = n > kRbMaxCell ? 3 : 1;
+  else if (n > 0 && n < R->rb_lo) mode = 2;
+  const int tid = threadIdx.x;
+  if (mode == 2) {
+    long long heavy = 0;
+    for (int t = tid; t < n; t += blockDim.x) heavy += G.wt[in][start + t] >= 2u ? 1 : 0;
+    heavy = block_sum(heavy, wsm);
+    const int S = (int)min((long long)(T - n), heavy);
+    if (S <= 0) {
+      mode = 0;
+    } else {
+      if (!write) return n + S;
+      int P = 1;
+      while (P < n) P <<= 1;
+      for (int t = tid; t < P; t += blockDim.x) {
+        if (t < n) {
+          sm.k1[t] = ~G.wt[in][start + t];  // heaviest first
+          sm.k2[t] = G.id[in][start + t];
+          sm.ix[t] = (uint16_t)t;
+        } else {
+          sm.k1[t] = 0xFFFFFFFFu;
+          sm.k2[t] = ~0ull;
+          sm.ix[t] = 0;
+        }
+      }
+      __syncthreads();
+      rb_bitonic(sm, P);
+      const long long k_lvl = st->step;
+      for (int t = tid; t < n; t += blockDim.x) {
+        const long long i = start + sm.ix[t];
+        if (t < S) {
+          const long long o = obase + 2 * t;
+          rb_copy(G, in, out, i, o);
+          rb_copy(G, in, out, i, o + 1);
+          const unsigned k = G.wt[in][i];
+          G.wt[out][o] = (k + 1u) / 2u;
+          G.wt[out][o + 1] = k / 2u;
+          G.id[out][o + 1] = child_id(G.id[in][i], k_lvl, 3);
+        } else {
+          rb_copy(G, in, out, i, obase + S + t);
+        }
+      }
+      if (tid == 0) atomicAdd(&st->ctr[sp][C_RB_SPLIT], (unsigned long long)S);
+      __syncthreads();
+      return n + S;
+    }
+  }
+  if (mode == 0 || mode == 3) {
+    if (write) {
+      for (int t = tid; t < n; t += blockDim.x) rb_copy(G, in, out, start + t, obase + t);
+      if (mode == 3 && tid == 0) atomicAdd(&st->ctr[sp][C_RB_SKIPPED], 1ull);
+    }
+    return n;
+  }
+  // merge: order by (vx, id), groups of four, the ones nearest the middle
+  const int ng = n / 4;
+  const int Gw = min(ng, (n - T + 1) / 2);
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int t = tid; t < P; t += blockDim.x) {
+    if (t < n) {
+      sm.k1[t] = rb_fkey(G.vx[in][start + t]);
+      sm.k2[t] = G.id[in][start + t];
+      sm.ix[t] = (uint16_t)t;
+    } else {
+      sm.k1[t] = 0xFFFFFFFFu;
+      sm.k2[t] = ~0ull;
+      sm.ix[t] = 0;
+    }
+  }
+  __syncthreads();
+  rb_bitonic(sm, P);
+  for (int g = tid; g < ng; g += blockDim.x) {
+    unsigned W = 0u;
+    for (int q = 0; q < 4; ++q) W += G.wt[in][start + sm.ix[4 * g + q]];
+    sm.el[rb_pos(g, ng)] = W <= kRbMaxWeight ? 1 : 0;
+  }
+  __syncthreads();
+  // eligible groups before each order position (block scan; ng <= 1024)
+  {
+    const int per = (ng + blockDim.x - 1) / blockDim.x;
+    const int a = min(ng, tid * per), e = min(ng, a + per);
+    long long loc = 0;
+    for (int q = a; q < e; ++q) loc += sm.el[q];
+    long long tot;
+    long long run = block_excl_scan(loc, wsm, &tot);
+    for (int q = a; q < e; ++q) {
+      sm.pref[q] = (uint16_t)run;
+      run += sm.el[q];
+    }
+    __syncthreads();
+    const int chosen = (int)min((long long)Gw, tot);
+    if (!write) return n - 2 * chosen;
+  }
+  // output offsets: a chosen group's first particle emits two, its others
+  // none, every other particle one
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int a = min(n, tid * per), e = min(n, a + per);
+  auto emits = [&](int t) -> int {
+    const int g = t / 4;
+    if (g >= ng) return 1;
+    const int ps = rb_pos(g, ng);
+    const bool ch = sm.el[ps] && (int)sm.pref[ps] < Gw;
+    return ch ? ((t & 3) == 0 ? 2 : 0) : 1;
+  };
+  long long loc = 0;
+  for (int t = a; t < e; ++t) loc += emits(t);
+  long long tot;
+  long long pos = block_excl_scan(loc, wsm, &tot);
+  const long long k_lvl = st->step;
+  unsigned long long merged = 0;
+  for (int t = a; t < e; ++t) {
+    const int m = emits(t);
+    if (m == 1) {
+      rb_copy(G, in, out, start + sm.ix[t], obase + pos);
+    } else if (m == 2) {
+      // the group's weighted centroid, mean velocity and spreads (FP64)
+      double W = 0.0, X = 0.0, u[3] = {0.0, 0.0, 0.0}, m2[3] = {0.0, 0.0, 0.0};
+      unsigned Wi = 0u;
+      unsigned long long id0 = ~0ull, id1 = ~0ull;
+      long long ii[4];
+      for (int q = 0; q < 4; ++q) {
+        const long long i = start + sm.ix[t + q];
+        ii[q] = i;
+        const unsigned k = G.wt[in][i];
+        const double kd = (double)k;
+        Wi += k;
+        W += kd;
+        X += kd * (double)G.xi[in][i];
+        u[0] += kd * (double)G.vx[in][i];
+        u[1] += kd * (double)G.vy[in][i];
+        u[2] += kd * (double)G.vz[in][i];
+        const unsigned long long id = G.id[in][i];
+        if (id < id0) { id1 = id0; id0 = id; } else if (id < id1) { id1 = id; }
+      }
+      X /= W;
+      for (int q = 0; q < 3; ++q) u[q] /= W;
+      for (int q = 0; q < 4; ++q) {
+        const long long i = ii[q];
+        const double kd = (double)G.wt[in][i];
+        const double dv[3] = {(double)G.vx[in][i] - u[0], (double)G.vy[in][i] - u[1],
+                              (double)G.vz[in][i] - u[2]};
+        for (int r = 0; r < 3; ++r) m2[r] += kd * dv[r] * dv[r];
+      }
+      const uint4 A = draw(R->seed, id0, (uint32_t)k_lvl, ((uint32_t)sp << 8) | 0x10u);
+      double d[3] = {sqrt(m2[0] / W), sqrt(m2[1] / W), sqrt(m2[2] / W)};
+      if (A.x & 1u) d[1] = -d[1];
+      if (A.x & 2u) d[2] = -d[2];
+      const unsigned ka = (Wi + 1u) / 2u, kb = Wi - ka;
+      const double fa = sqrt((double)kb / (double)ka), fb = sqrt((double)ka / (double)kb);
+      float xc = (float)X;
+      if (xc >= 1.0f) xc = 0.99999994f;  // the centroid lies in the cell
+      const long long o = obase + pos;
+      const int cc = G.cell[in][ii[0]];
+      G.cell[out][o] = cc;
+      G.cell[out][o + 1] = cc;
+      G.xi[out][o] = xc;
+      G.xi[out][o + 1] = xc;
+      G.vx[out][o] = (float)(u[0] + fa * d[0]);
+      G.vy[out][o] = (float)(u[1] + fa * d[1]);
+      G.vz[out][o] = (float)(u[2] + fa * d[2]);
+      G.vx[out][o + 1] = (float)(u[0] - fb * d[0]);
+      G.vy[out][o + 1] = (float)(u[1] - fb * d[1]);
+      G.vz[out][o + 1] = (float)(u[2] - fb * d[2]);
+      G.id[out][o] = id0;
+      G.id[out][o + 1] = id1;
+      G.wt[out][o] = ka;
+      G.wt[out][o + 1] = kb;
+      ++merged;
+    }
+    pos += m;
+  }
+  merged = warp_sum(merged);
+  if ((tid & 31) == 0 && merged) atomicAdd(&st->ctr[sp][C_RB_MERGED], merged);
+  __syncthreads();
+  return (int)tot;
+}
+
+// per-CTA prefix of the rebalancing work: the cells of every segment of a due
+// run (pre[0..nseg])
+__device__ long long rb_prefix(const BatchView& b, long long* pre, long long* wsm) {
+  const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per;
+  long long loc = 0;
+  for (int k = 0; k < per; ++k) {
+    const int s = s0 + k;
+    if (s < b.nseg) {
+      const int slot = b.segs[s].run;
+      const bool due = run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot);
+      const long long cnt = due ? b.runs[slot].N : 0;
+      pre[s] = cnt;
+      loc += cnt;
+    }
+  }
+  long long total;
+  long long run = block_excl_scan(loc, wsm, &total);
+  for (int k = 0; k < per; ++k) {
+    const int s = s0 + k;
+    if (s < b.nseg) {
+      const long long cnt = pre[s];
+      pre[s] = run;
+      run += cnt;
+    }
+  }
+  if (threadIdx.x == 0) pre[b.nseg] = total;
+  __syncthreads();
+  return total;
+}
+
+// write = 0: each cell's output count into rbcnt; write = 1: the cells'
+// particles into the current buffer set at the scanned offsets
+__global__ void __launch_bounds__(kRbBlock) k_rb_cells(BatchView b, int write) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RbSmem& sm = *reinterpret_cast<RbSmem*>(smem_raw);
+  long long* pre = reinterpret_cast<long long*>(smem_raw + sizeof(RbSmem));
+  __shared__ long long wsm[32];
+  const long long T = rb_prefix(b, pre, wsm);
+  for (long long item = blockIdx.x; item < T; item += gridDim.x) {
+    const int s = seg_find(pre, b.nseg, item);
+    const int c = (int)(item - pre[s]);
+    const SegDev& G = b.segs[s];
+    if (write && b.sst[s].rb_over) continue;
+    const int* h = b.hist + G.hoff;  // after the scatter: the end of each cell
+    const long long end = h[c];
+    const long long start = c > 0 ? h[c - 1] : 0;
+    // (an unconditional guard: the writes below index by this range)
+    if (!(start >= 0 && end >= start && end <= G.cap)) continue;
+    int* oc = b.rbcnt + G.hoff;
+    const int cnt = rb_cell(b, s, c, start, (int)(end - start), write != 0, write ? oc[c] : 0, sm, wsm);
+    if (!write && threadIdx.x == 0) oc[c] = cnt;
+  }
+}
+
+// per segment: output counts -> exclusive offsets; the total (capacity check)
+__global__ void __launch_bounds__(kPassBlock) k_rb_scan(BatchView b) {
+  const int s = blockIdx.x;
+  if (s >= b.nseg) return;
+  const SegDev& G = b.segs[s];
+  const int slot = G.run;
+  if (!run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot)) return;
+  __shared__ long long wsm[32];
+  const int N = b.runs[slot].N;
+  int* h = b.rbcnt + G.hoff;
+  const int per = (N + kPassBlock - 1) / kPassBlock;
+  const int beg = min(N, (int)threadIdx.x * per), end = min(N, beg + per);
+  long long loc = 0;
+  for (int i = beg; i < end; ++i) loc += h[i];
+  long long total;
+  long long run = block_excl_scan(loc, wsm, &total);
+  for (int i = beg; i < end; ++i) {
+    const int c = h[i];
+    h[i] = (int)run;
+    run += c;
+  }
+  if (threadIdx.x == 0) {
+    b.sst[s].n_rb = total;
+    b.sst[s].rb_over = total > G.cap ? 1 : 0;
+  }
+}
+
+// per segment: sizes after the rebalancing (or, if the plan overflowed the
+// capacity, the sorted particles unchanged); cell arrays cleared
+__global__ void __launch_bounds__(kPassBlock) k_rb_finalize(BatchView b) {
+  const int s = blockIdx.x;
+  if (s >= b.nseg) return;
+  const SegDev& G = b.segs[s];
+  const int slot = G.run;
+  if (!run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot)) return;
+  const int N = b.runs[slot].N;
+  for (int i = threadIdx.x; i < N; i += kPassBlock) {
+    b.hist[G.hoff + i] = 0;
+    b.rbcnt[G.hoff + i] = 0;
+  }
+  if (threadIdx.x == 0) {
+    SegState* ss = b.sst + s;
+    if (ss->rb_over) {
+      ss->cur ^= 1;  // the sorted buffer set
+      ss->n_proc = ss->n_live;
+      ss->n_alloc = ss->n_live;
+    } else {
+      ss->n_proc = ss->n_rb;
+      ss->n_alloc = ss->n_rb;
+    }
+    ss->n_dead = 0;
+  }
+}
+
+// per run: the level rebalanced; a capacity overflow fails the run
+__global__ void k_rb_mark(BatchView b) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= b.max_slots) return;
+  RunState* st = b.rst + slot;
+  const RunDev& R = b.runs[slot];
+  if (!run_live(R, *st, MODE_REBAL, -1, slot)) return;
+  bool over = false;
+  for (int q = 0; q < R.ns; ++q) {
+    SegState* ss = b.sst + R.seg0 + q;
+    over = over || ss->rb_over;
+    ss->rb_over = 0;
+  }
+  st->rb_level = st->step;
+  st->rb_force = 0;
+  if (over) {
+    set_status(st, ECPIC_ERR_CAPACITY);
   }
 }
 
@@ -1810,6 +2286,7 @@ __global__ void k_init(BatchView b, int slot, InitParams p) {
     G.vy[cur][i] = __double2float_rn(__dmul_rn(sd, z1));
     G.vz[cur][i] = __double2float_rn(__dmul_rn(sd, z2));
     G.id[cur][i] = (uint64_t)i;
+    if (G.wt[cur]) G.wt[cur][i] = p.rb_m0;
   }
 }
 
@@ -1948,12 +2425,12 @@ void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s) 
   if (phase == 0) {
     const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
     set_smem_attr((const void*)k_hist, smh);
-    k_hist<<<grid, kPassBlock, smh, s>>>(b);
+    k_hist<<<grid, kPassBlock, smh, s>>>(b, MODE_SORT);
   } else if (phase == 1) {
-    k_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
+    k_scan<<<b.nseg, kPassBlock, 0, s>>>(b, MODE_SORT);
   } else if (phase == 2) {
     const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
-    k_scatter<<<grid, kPassBlock, sms, s>>>(b);
+    k_scatter<<<grid, kPassBlock, sms, s>>>(b, MODE_SORT);
   } else {
     k_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
   }
@@ -1961,6 +2438,22 @@ void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s) 
 
 void launch_sort(const BatchView& b, int grid, cudaStream_t s) {
   for (int ph = 0; ph < 4; ++ph) launch_sort_phase(b, grid, ph, s);
+}
+
+void launch_rebalance(const BatchView& b, int grid, cudaStream_t s) {
+  const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
+  set_smem_attr((const void*)k_hist, smh);
+  k_hist<<<grid, kPassBlock, smh, s>>>(b, MODE_REBAL);
+  k_scan<<<b.nseg, kPassBlock, 0, s>>>(b, MODE_REBAL);
+  const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
+  k_scatter<<<grid, kPassBlock, sms, s>>>(b, MODE_REBAL);
+  const size_t smr = sizeof(RbSmem) + sizeof(long long) * (size_t)(b.nseg + 1);
+  set_smem_attr((const void*)k_rb_cells, smr);
+  k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 0);
+  k_rb_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
+  k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 1);
+  k_rb_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
+  k_rb_mark<<<(b.max_slots + 127) / 128, 128, 0, s>>>(b);
 }
 
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s) {

@@ -16,6 +16,7 @@ struct BatchView {
   const SegDev* segs;   // device, nseg
   SegState* sst;        // device, nseg
   int* hist;            // device, sum of N over segments
+  int* rbcnt;           // device, nseg * nmax: rebalancing output counts / cursors
   int max_slots;
   int nseg;
   int nmax;             // largest N in the batch
@@ -25,6 +26,7 @@ struct InitParams {
   long long n[kMaxSpecies];
   double sd[kMaxSpecies];  // sqrt(e T / m)
   int quiet;               // positions X_i = (i + 1/2) L / n instead of Philox
+  unsigned rb_m0;          // weight multiplier of loaded particles (rebalancing runs)
 };
 
 size_t pass_smem_bytes(const BatchView& b);
@@ -41,6 +43,10 @@ void launch_phi(const BatchView& b, int slot, cudaStream_t s);
 void launch_sort(const BatchView& b, int grid, cudaStream_t s);
 void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s);
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s);
+// particle rebalancing of the runs due at their current level (or forced):
+// counting sort by cell into the other buffer set, then per cell the merge /
+// split plan, its scan, the merged/split particles written back, sizes set
+void launch_rebalance(const BatchView& b, int grid, cudaStream_t s);
 
 void launch_deposit_device(int N, long long n, const int* cell, const float* xi,
                            unsigned long long* S, cudaStream_t s);

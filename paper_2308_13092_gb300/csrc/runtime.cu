@@ -95,6 +95,7 @@ size_t layout_bytes(const RunSpec& s) {
     for (int buf = 0; buf < 2; ++buf) {
       const size_t c = (size_t)sp.cap;
       add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(4 * c); add(8 * c);
+      if (s.rb) add(4 * c);  // weight multipliers
     }
   for (const auto& sp : s.species) add(sizeof(RealRec) * (size_t)real_capacity(sp, s));
   for (const auto& sp : s.species) add(sizeof(int) * (size_t)impact_capacity(sp));
@@ -153,6 +154,7 @@ size_t carve_layout(const RunSpec& spec, char* base, RunDev* R, SegDev* segs, in
         G.vy[buf] = cv.take<float>(c);
         G.vz[buf] = cv.take<float>(c);
         G.id[buf] = cv.take<uint64_t>(c);
+        G.wt[buf] = spec.rb ? cv.take<uint32_t>(c) : nullptr;
       }
       G.cap = (long long)c;
     } else {
@@ -162,6 +164,7 @@ size_t carve_layout(const RunSpec& spec, char* base, RunDev* R, SegDev* segs, in
       std::memset(G.vy, 0, sizeof(G.vy));
       std::memset(G.vz, 0, sizeof(G.vz));
       std::memset(G.id, 0, sizeof(G.id));
+      std::memset(G.wt, 0, sizeof(G.wt));
       G.cap = 0;
     }
     G.real = nullptr;
@@ -216,6 +219,13 @@ std::string validate_spec(const RunSpec& s) {
         return "the EC2 and MC2 schemes need a uniform grid";
   }
   if (s.species.empty() || s.species.size() > (size_t)kMaxSpecies) return "1..4 species required";
+  if (s.rb) {
+    if (s.scheme != ECPIC_SCHEME_EC && s.scheme != ECPIC_SCHEME_MC)
+      return "particle rebalancing needs the EC or MC scheme";
+    if (s.rb_every < 0 || s.rb_target < 1 || s.rb_target > kRbMaxCell || s.rb_lo < 0 ||
+        s.rb_lo > s.rb_target || s.rb_hi < s.rb_target || s.rb_m0 < 1 || s.rb_m0 > kRbMaxWeight)
+      return "bad rebalancing parameters (0 <= lo <= target <= hi, target <= 4096, 1 <= m0 <= 65536)";
+  }
   if (!(s.dt > 0) || !std::isfinite(s.dt)) return "dt must be positive";
   if (s.n_init.size() != s.species.size() || s.T_eV.size() != s.species.size())
     return "n_per_species/T_eV size mismatch";
@@ -289,6 +299,9 @@ void fill_diag(const Diag& d, const RunSpec& spec, ecpic_diag* out) {
     out->candidates[s] = (int64_t)c[C_CAND];
     out->clamps[s] = (int64_t)c[C_CLAMPS];
     for (int p = 0; p < kMaxProc; ++p) out->collisions[s][p] = (int64_t)c[C_COLL0 + p];
+    out->rb_merged[s] = (int64_t)c[C_RB_MERGED];
+    out->rb_split[s] = (int64_t)c[C_RB_SPLIT];
+    out->rb_skipped[s] = (int64_t)c[C_RB_SKIPPED];
   }
   out->fe = d.st.fe;
   out->n_samples = d.st.n_samples;
@@ -332,7 +345,7 @@ void fill_diag(const Diag& d, const RunSpec& spec, ecpic_diag* out) {
     for (int b = 0; b < spec.iad_bins; ++b)
       if (out->iad) out->iad[(size_t)s * spec.iad_bins + b] = (double)t[spec.eedf_bins + spec.iedf_bins + b];
     // J.E = q w (v^- + v^+)/2 E_i / dx_j, summed per sample, mean over samples
-    const double qw = spec.species[s].q * spec.species[s].w;
+    const double qw = spec.species[s].q * base_weight(spec, s);
     for (int j = 0; j < N && out->power; ++j)
       out->power[(size_t)s * N + j] =
           0.5 * qw * d.pw[(size_t)s * N + j] / (spec.edges[j + 1] - spec.edges[j]) * inv;
@@ -364,6 +377,8 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
   cudaMalloc(&d_segs_, sizeof(SegDev) * nseg_);
   cudaMalloc(&d_sst_, sizeof(SegState) * nseg_);
   cudaMalloc(&d_hist_, sizeof(int) * (size_t)nseg_ * nmax_);
+  cudaMalloc(&d_rbcnt_, sizeof(int) * (size_t)nseg_ * nmax_);
+  level_.assign(max_slots_, 0);
   h_runs_.assign(max_slots_, RunDev{});
   h_segs_.assign(nseg_, SegDev{});
   for (int s = 0; s < nseg_; ++s) {
@@ -375,6 +390,7 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
   cudaMemsetAsync(d_rst_, 0, sizeof(RunState) * max_slots_, stream_);
   cudaMemsetAsync(d_sst_, 0, sizeof(SegState) * nseg_, stream_);
   cudaMemsetAsync(d_hist_, 0, sizeof(int) * (size_t)nseg_ * nmax_, stream_);
+  cudaMemsetAsync(d_rbcnt_, 0, sizeof(int) * (size_t)nseg_ * nmax_, stream_);
   cudaMemcpyAsync(d_segs_, h_segs_.data(), sizeof(SegDev) * nseg_, cudaMemcpyHostToDevice, stream_);
   slot_mem_.assign(max_slots_, nullptr);
   slot_bytes_.assign(max_slots_, 0);
@@ -398,6 +414,7 @@ Batch::~Batch() {
   cudaFree(d_segs_);
   cudaFree(d_sst_);
   cudaFree(d_hist_);
+  cudaFree(d_rbcnt_);
   if (own_stream_) cudaStreamDestroy(stream_);
 }
 
@@ -439,6 +456,7 @@ BatchView Batch::view() const {
   v.segs = d_segs_;
   v.sst = d_sst_;
   v.hist = d_hist_;
+  v.rbcnt = d_rbcnt_;
   v.max_slots = max_slots_;
   v.nseg = nseg_;
   v.nmax = nmax_;
@@ -494,6 +512,11 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   R.ns = ns;
   R.seg0 = slot * spc_;
   R.sample_every = spec.sample_every;
+  R.rb = spec.rb ? 1 : 0;
+  R.rb_every = spec.rb ? spec.rb_every : 0;
+  R.rb_target = spec.rb_target;
+  R.rb_lo = spec.rb_lo;
+  R.rb_hi = spec.rb_hi;
   R.L = spec.edges[N];
   R.dt = spec.dt;
   R.v0 = spec.v0;
@@ -565,7 +588,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     SpeciesDev& D = R.sp[s];
     D.q = hs.q;
     D.m = hs.m;
-    D.w = hs.w;
+    D.w = base_weight(spec, s);
     D.qm_dt = (float)(hs.q / hs.m * spec.dt);
     D.half_m_over_e = (float)(0.5 * hs.m / kQe);
     D.two_e_over_m = (float)(2.0 * kQe / hs.m);
@@ -628,6 +651,11 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   RunState st{};
   st.step = 0;
   st.step_end = spec.step_end;
+  st.rb_level = -1;
+  level_[slot] = 0;
+  // the slot's cell arrays start from zero whatever its last run left
+  cudaMemsetAsync(d_hist_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_, stream_);
+  cudaMemsetAsync(d_rbcnt_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_, stream_);
   cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
   h_runs_[slot] = R;
   upload_run(slot);
@@ -639,6 +667,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   // particles and the field of step 0
   InitParams ip{};
   ip.quiet = spec.quiet;
+  ip.rb_m0 = spec.rb ? spec.rb_m0 : 1u;
   for (int s = 0; s < ns; ++s) {
     ip.n[s] = spec.n_init[s];
     ip.sd[s] = std::sqrt(kQe * spec.T_eV[s] / spec.species[s].m);
@@ -717,6 +746,7 @@ int Batch::reserve(int slot, const long long* cap, std::string* err) {
     cudaMemcpyAsync(B.vy[c], A.vy[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
     cudaMemcpyAsync(B.vz[c], A.vz[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
     cudaMemcpyAsync(B.id[c], A.id[c], 8 * n, cudaMemcpyDeviceToDevice, stream_);
+    if (A.wt[c] && B.wt[c]) cudaMemcpyAsync(B.wt[c], A.wt[c], 4 * n, cudaMemcpyDeviceToDevice, stream_);
   }
   // the real-collision and impact lists are empty between steps
   for (int s = 0; s < spc_; ++s) h_segs_[seg0 + s] = segs[s];
@@ -964,6 +994,106 @@ int Batch::ensure_graphs(std::string* err) {
   return rc;
 }
 
+bool Batch::rb_due_within(int steps) const {
+  for (int s = 0; s < max_slots_; ++s) {
+    if (!active_[s] || !specs_[s].rb || specs_[s].rb_every <= 0) continue;
+    const long long e = specs_[s].rb_every;
+    const long long L = level_[s];
+    const long long top = std::min(L + steps, specs_[s].step_end);
+    if (top > L && (top / e) > (L / e)) return true;  // a multiple of e in (L, top]
+  }
+  return false;
+}
+
+void Batch::advance_levels(int steps) {
+  for (int s = 0; s < max_slots_; ++s)
+    if (active_[s]) level_[s] = std::min(level_[s] + steps, specs_[s].step_end);
+}
+
+void Batch::rebalance_launch() {
+  launch_rebalance(view(), std::max(1, 2 * sm_count_), stream_);
+}
+
+int Batch::rebalance_now(int slot, std::string* err) {
+  if (!slot_active(slot) || !specs_[slot].rb) {
+    if (err) *err = "no rebalancing run in this slot (ecpic_set_rebalance before init)";
+    return ECPIC_ERR_STATE;
+  }
+  cudaSetDevice(device_);
+  const int one = 1;
+  int rc = check(cudaMemcpyAsync(&d_rst_[slot].rb_force, &one, sizeof(int), cudaMemcpyHostToDevice,
+                                 stream_), "rebalance flag", err);
+  if (rc) return rc;
+  rebalance_launch();
+  rc = check(cudaStreamSynchronize(stream_), "rebalance", err);  // `one` lives until here
+  if (rc) return rc;
+  return check(cudaGetLastError(), "rebalance", err);
+}
+
+int Batch::get_weights(int slot, int species, uint32_t* k, long long cap, long long* n,
+                       std::string* err) {
+  if (!slot_active(slot) || species < 0 || species >= (int)specs_[slot].species.size() || !n ||
+      !specs_[slot].rb) {
+    if (err) *err = "bad slot or species, or a run without weight multipliers";
+    return ECPIC_ERR_ARG;
+  }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  const int seg = slot * spc_ + species;
+  SegState ss;
+  cudaMemcpy(&ss, d_sst_ + seg, sizeof(SegState), cudaMemcpyDeviceToHost);
+  const SegDev& G = h_segs_[seg];
+  const size_t m = (size_t)ss.n_proc;
+  std::vector<int32_t> c(m);
+  std::vector<uint32_t> w(m);
+  cudaMemcpy(c.data(), G.cell[ss.cur], 4 * m, cudaMemcpyDeviceToHost);
+  rc = check(cudaMemcpy(w.data(), G.wt[ss.cur], 4 * m, cudaMemcpyDeviceToHost), "weight read", err);
+  if (rc) return rc;
+  long long live = 0;
+  for (size_t i = 0; i < m; ++i) live += c[i] >= 0;
+  *n = live;
+  if (live > cap) {
+    if (err) *err = "output capacity too small";
+    return ECPIC_ERR_ARG;
+  }
+  long long q = 0;
+  for (size_t i = 0; i < m; ++i)
+    if (c[i] >= 0) {
+      if (k) k[q] = w[i];
+      ++q;
+    }
+  return ECPIC_OK;
+}
+
+int Batch::set_weights(int slot, int species, const uint32_t* k, long long n, std::string* err) {
+  if (!slot_active(slot) || species < 0 || species >= (int)specs_[slot].species.size() ||
+      !specs_[slot].rb || (n > 0 && !k)) {
+    if (err) *err = "bad slot or species, or a run without weight multipliers";
+    return ECPIC_ERR_ARG;
+  }
+  for (long long i = 0; i < n; ++i)
+    if (k[i] < 1u || k[i] > kRbMaxWeight) {
+      if (err) *err = "weight multipliers must lie in 1..65536";
+      return ECPIC_ERR_ARG;
+    }
+  cudaSetDevice(device_);
+  int rc = check(cudaStreamSynchronize(stream_), "synchronize", err);
+  if (rc) return rc;
+  const int seg = slot * spc_ + species;
+  SegState ss;
+  cudaMemcpy(&ss, d_sst_ + seg, sizeof(SegState), cudaMemcpyDeviceToHost);
+  if (ss.n_proc != n || ss.n_dead != 0) {
+    if (err) *err = "set_weights needs the particle count of the last set_particles";
+    return ECPIC_ERR_ARG;
+  }
+  const SegDev& G = h_segs_[seg];
+  rc = check(cudaMemcpy(G.wt[ss.cur], k, 4 * (size_t)n, cudaMemcpyHostToDevice), "weight write", err);
+  if (rc) return rc;
+  refresh(slot);
+  return check(cudaGetLastError(), "set_weights", err);
+}
+
 int Batch::step(long long n, std::string* err) {
   if (n < 0) {
     if (err) *err = "negative step count";
@@ -990,11 +1120,13 @@ int Batch::step_chunk(long long n, std::string* err) {
   const BatchView b = view();
   if (!use_graphs_) pass_grid_ = choose_grid();
   while (n > 0) {
-    if (use_graphs_ && since_sort_ == 0 && n >= sort_every_) {
+    // a sort cycle in which no run is due to rebalance: its graph
+    if (use_graphs_ && since_sort_ == 0 && n >= sort_every_ && !rb_due_within(sort_every_)) {
       rc = timing_ ? launch_timed(tk_, &tk_next_, err)
                    : check(cudaGraphLaunch(graph_k_, stream_), "graph launch", err);
       if (rc) return rc;
       n -= sort_every_;
+      advance_levels(sort_every_);
       continue;
     }
     if (use_graphs_) {
@@ -1007,6 +1139,10 @@ int Batch::step_chunk(long long n, std::string* err) {
       launch_field(b, 1, -1, stream_);
     }
     --n;
+    // the runs due at the new level rebalance (after its field)
+    const bool due = rb_due_within(1);
+    advance_levels(1);
+    if (due) rebalance_launch();
     if (++since_sort_ >= sort_every_) {
       if (use_graphs_ && timing_) {
         rc = launch_timed(ts_, &ts_next_, err);
@@ -1043,6 +1179,11 @@ int Batch::profile_step(long long n, double* ms, long long* launches, std::strin
     launch_field(b, 1, -1, stream_);
     cudaEventRecord(ev[2], stream_);
     if (each && (rc = check(cudaEventSynchronize(ev[2]), "field kernel", err))) break;
+    {
+      const bool due = rb_due_within(1);
+      advance_levels(1);
+      if (due) rebalance_launch();  // (timed with the sort)
+    }
     const bool sort = ++since_sort_ >= sort_every_;
     if (sort) {
       if (each) {
@@ -1282,6 +1423,10 @@ int Batch::set_particles(int slot, int species, const int32_t* cell, const float
   cudaMemcpy(G.vy[u], vy, 4 * m, cudaMemcpyHostToDevice);
   cudaMemcpy(G.vz[u], vz, 4 * m, cudaMemcpyHostToDevice);
   cudaMemcpy(G.id[u], id, 8 * m, cudaMemcpyHostToDevice);
+  if (G.wt[u]) {
+    const std::vector<uint32_t> w(m, specs_[slot].rb_m0);
+    cudaMemcpy(G.wt[u], w.data(), 4 * m, cudaMemcpyHostToDevice);
+  }
   ss.n_proc = ss.n_alloc = n;
   ss.n_dead = 0;
   cudaMemcpy(d_sst_ + seg, &ss, sizeof(SegState), cudaMemcpyHostToDevice);
@@ -1413,6 +1558,8 @@ int Batch::set_step_end(int slot, long long step_end, std::string* err) {
   RunState st;
   cudaMemcpy(&st, d_rst_ + slot, sizeof(RunState), cudaMemcpyDeviceToHost);
   st.step_end = step_end;
+  specs_[slot].step_end = step_end;
+  level_[slot] = std::min<long long>(st.step, step_end);
   return check(cudaMemcpy(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice),
                "set_step_end", err);
 }

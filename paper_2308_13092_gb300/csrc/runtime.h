@@ -42,7 +42,18 @@ struct RunSpec {
   double eedf_center = -1.0, eedf_halfwidth = 0.5e-3, eedf_dE = 0.5, iedf_dE = 2.0;
   int eedf_bins = 100, iedf_bins = 256, iad_bins = 90;
   long long step_end = LLONG_MAX;
+  // particle rebalancing (weight multipliers on): every rb_every steps (0:
+  // on demand only), merge above rb_hi, split below rb_lo, aim rb_target;
+  // loaded particles get multiplier rb_m0 and the species base weight w / rb_m0
+  bool rb = false;
+  int rb_every = 0, rb_target = 0, rb_lo = 0, rb_hi = 0;
+  unsigned rb_m0 = 1;
 };
+
+// base weight of a species (a particle of multiplier k weighs k times it)
+inline double base_weight(const RunSpec& s, int species) {
+  return s.species[species].w / (s.rb ? (double)s.rb_m0 : 1.0);
+}
 
 // argument checks of a complete run description; "" when valid
 std::string validate_grid(const std::vector<double>& edges, int bc);
@@ -101,6 +112,11 @@ class Batch {
                   std::string* err);
   int since_sort() const { return since_sort_; }
   int sort_now(std::string* err);
+  // particle rebalancing of one run now, whatever its cadence (between steps)
+  int rebalance_now(int slot, std::string* err);
+  // weight multipliers of a species' live particles (order of get_particles)
+  int get_weights(int slot, int species, uint32_t* k, long long cap, long long* n, std::string* err);
+  int set_weights(int slot, int species, const uint32_t* k, long long n, std::string* err);
   int sync(std::string* err);
   int slot_status(int slot);  // synchronises
 
@@ -150,6 +166,12 @@ class Batch {
   char* stage_slot(size_t bytes, int* slot);
   void stage_done(int slot);  // after the copy from the slot is enqueued
   int grow_full_runs(std::string* err);
+  // host-side prediction of the runs' levels (they advance one level per step
+  // up to their end), to launch the rebalancing only where a run is due; the
+  // kernels check the device state themselves
+  bool rb_due_within(int steps) const;
+  void advance_levels(int steps);
+  void rebalance_launch();
   int check(cudaError_t e, const char* what, std::string* err);
   // a step graph instance with phase events: ev[i] -> ev[i+1] is phase ph[i]
   struct TimedGraph {
@@ -173,6 +195,8 @@ class Batch {
   SegDev* d_segs_ = nullptr;
   SegState* d_sst_ = nullptr;
   int* d_hist_ = nullptr;
+  int* d_rbcnt_ = nullptr;
+  std::vector<long long> level_;  // predicted level of each slot
   std::vector<RunDev> h_runs_;
   std::vector<SegDev> h_segs_;
   std::vector<void*> slot_mem_;

@@ -47,6 +47,7 @@ class ecpic_diag(C.Structure):
         ("eedf_cell0", C.c_int), ("eedf_cell1", C.c_int), ("eedf_dE", C.c_double),
         ("iedf_dE", C.c_double), ("impacts_dropped", C.c_int64 * 4), ("eedf", C.c_void_p),
         ("iedf", C.c_void_p), ("iad", C.c_void_p), ("power", C.c_void_p),
+        ("rb_merged", C.c_int64 * 4), ("rb_split", C.c_int64 * 4), ("rb_skipped", C.c_int64 * 4),
     ]
 
 
@@ -73,6 +74,8 @@ class ecpic_run_config(C.Structure):
         ("eedf_center", C.c_double), ("eedf_halfwidth", C.c_double), ("eedf_dE", C.c_double),
         ("eedf_bins", C.c_int), ("iedf_dE", C.c_double), ("iedf_bins", C.c_int),
         ("iad_bins", C.c_int),
+        ("rb_every", C.c_int), ("rb_target", C.c_int), ("rb_lo", C.c_int), ("rb_hi", C.c_int),
+        ("rb_m0", C.c_uint32),
     ]
 
 
@@ -101,6 +104,10 @@ SIGNATURES = {
     "ecpic_sort_state": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
     "ecpic_autotune": (i32, [vp, i64, vp, vp, vp]),
     "ecpic_set_quiet_start": (i32, [vp, i32]),
+    "ecpic_set_rebalance": (i32, [vp, i32, i32, i32, i32, u32]),
+    "ecpic_rebalance_now": (i32, [vp]),
+    "ecpic_get_weights": (i32, [vp, i32, vp, i64, C.POINTER(i64)]),
+    "ecpic_set_weights": (i32, [vp, i32, vp, i64]),
     "ecpic_set_tallies": (i32, [vp, d, d, d, i32, d, i32, i32]),
     "ecpic_create": (i32, [C.POINTER(vp), i32, vp]),
     "ecpic_destroy": (None, [vp]),
@@ -249,6 +256,8 @@ class Run:
             r.set_quiet_start(True)
         if getattr(cfg, "tallies", None):
             r.set_tallies(**cfg.tallies)
+        if getattr(cfg, "rebalance", None):
+            r.set_rebalance(**cfg.rebalance)
         if init:
             r.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
             if cfg.sample_every:
@@ -332,6 +341,28 @@ class Run:
 
     def set_pass_grid(self, ctas):
         _chk(self.h, self._L.ecpic_set_pass_grid(self.h, int(ctas)), "ecpic_set_pass_grid")
+
+    def set_rebalance(self, every, target, lo, hi, m0=1):
+        """Particle rebalancing (before init): see ecpic_set_rebalance."""
+        _chk(self.h, self._L.ecpic_set_rebalance(self.h, int(every), int(target), int(lo), int(hi),
+                                                 int(m0)), "ecpic_set_rebalance")
+
+    def rebalance_now(self):
+        _chk(self.h, self._L.ecpic_rebalance_now(self.h), "ecpic_rebalance_now")
+
+    def get_weights(self, species):
+        n = C.c_int64()
+        rc = self._L.ecpic_get_weights(self.h, species, None, 0, C.byref(n))
+        if rc not in (ECPIC_OK, ECPIC_ERR_ARG):
+            _chk(self.h, rc, "ecpic_get_weights")
+        k = np.zeros(max(1, n.value), dtype=np.uint32)
+        _chk(self.h, self._L.ecpic_get_weights(self.h, species, _p(k), k.size, C.byref(n)),
+             "ecpic_get_weights")
+        return k[: n.value]
+
+    def set_weights(self, species, k):
+        k = np.ascontiguousarray(k, dtype=np.uint32)
+        _chk(self.h, self._L.ecpic_set_weights(self.h, species, _p(k), k.size), "ecpic_set_weights")
 
     def set_phase_timing(self, on=True):
         _chk(self.h, self._L.ecpic_set_phase_timing(self.h, 1 if on else 0), "ecpic_set_phase_timing")
@@ -433,6 +464,9 @@ def _diag_dict(dg, ns, N, arrs=None):
             clamps=dg.clamps[s], collisions=list(dg.collisions[s])))
     for s in range(ns):
         out["species"][s]["impacts_dropped"] = dg.impacts_dropped[s]
+        out["species"][s]["rb_merged"] = dg.rb_merged[s]
+        out["species"][s]["rb_split"] = dg.rb_split[s]
+        out["species"][s]["rb_skipped"] = dg.rb_skipped[s]
     if arrs:
         M = N + 1
         out["density"] = arrs["density"].reshape(ns, M)
@@ -504,6 +538,11 @@ class Engine:
         rc.procs = C.cast(procs, C.c_void_p)
         rc.seed, rc.dt, rc.sample_every = int(cfg.seed), cfg.dt, int(cfg.sample_every)
         rc.quiet_start = 1 if getattr(cfg, "quiet", False) else 0
+        rb = getattr(cfg, "rebalance", None)
+        if rb:
+            rc.rb_every, rc.rb_target, rc.rb_lo, rc.rb_hi = (int(rb["every"]), int(rb["target"]),
+                                                             int(rb["lo"]), int(rb["hi"]))
+            rc.rb_m0 = int(rb.get("m0", 1))
         tally = dict(TALLY_DEFAULT)
         tally.update(getattr(cfg, "tallies", None) or {})
         for k, v in tally.items():

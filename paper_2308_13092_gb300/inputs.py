@@ -85,6 +85,8 @@ class RunConfig:
     sample_every: int = 0
     quiet: bool = False  # loader: evenly spaced positions (quiet start)
     tallies: Optional[dict] = None  # diagnostic tally set-up (None: defaults)
+    # particle rebalancing: dict(every, target, lo, hi, m0) or None (off)
+    rebalance: Optional[dict] = None
 
     @property
     def N(self) -> int:

@@ -22,6 +22,8 @@ def oracle_from_config(cfg: I.RunConfig, init: bool = True):
         o.set_quiet_start(True)
     if getattr(cfg, "tallies", None):
         o.set_tallies(**cfg.tallies)
+    if getattr(cfg, "rebalance", None):
+        o.set_rebalance(**cfg.rebalance)
     if init:
         o.init(cfg.seed, cfg.dt, [s.n0 for s in cfg.species], [s.T_eV for s in cfg.species])
     return o
