@@ -63,8 +63,8 @@ AUTOTUNE_STEPS = 64  # steps per autotuner trial (20 trials) before the warm-up
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "b373cca53d44b32af2fb32008aba0fde29fac74de218251660dd60107f71cd0f",
-           "dram_bytes_per_particle_step": 569.518e6 / 14.326e6}
+TRAFFIC = {"sources_sha256": "a2121a0f3f2769d150dfd1f81ce6a0a0d78a72672a6ce9464de0406ca9b62adb",
+           "dram_bytes_per_particle_step": 570.676e6 / 14.3047e6}
 
 
 def kernel_sources_sha256():
