@@ -206,3 +206,69 @@ def test_rebalancing_counters_follow_the_oracle_and_even_out_the_cells():
     dev0 = np.mean(np.abs(counts0 - 256))
     dev1 = np.mean(np.abs(counts1 - 256))
     assert dev1 < 0.5 * dev0, (dev0, dev1)
+
+
+def _key(d):
+    return [(s["n"], s["births"], s["candidates"], tuple(s["collisions"]), s["rb_merged"],
+             s["rb_split"]) for s in d["species"]]
+
+
+def _small_rb(seed, every, capacity_extra=None):
+    c = I.config_small(seed=seed)
+    c.sample_every = 10
+    c.n_steps = 240
+    c.rebalance = dict(every=every, target=64, lo=55, hi=70, m0=16)
+    if capacity_extra is not None:
+        for sp in c.species:
+            sp.capacity = sp.n0 + capacity_extra
+    return c
+
+
+def test_rebalancing_run_alone_equals_run_in_mix():
+    """Two rebalancing runs (cadences 20 and 30) and a plain one in one engine
+    batch: each rebalancing run's counters, rebalancing counts, particles,
+    weights and density equal the same run stepped alone (the rebalancing is
+    per run and per cell; the deposit is an integer sum)."""
+    from paper_2308_13092_gb300 import ecpic
+    cfgs = [_small_rb(21, 20), I.config_small(seed=22), _small_rb(23, 30)]
+    cfgs[1].n_steps = 240
+    cfgs[1].sample_every = 10
+    eng = ecpic.Engine(max_slots=3, max_cells=256)
+    tks = [eng.submit(c) for c in cfgs]
+    while True:
+        r, q = eng.pump(100)
+        if r == 0 and q == 0:
+            break
+    for c, t in zip(cfgs, tks):
+        if not c.rebalance:
+            continue
+        dm = eng.poll(t, diagnostics=True, profiles=True)["diag"]
+        g = gpu_from_config(c)
+        g.step(c.n_steps)
+        g.sync()
+        da = g.diagnostics(profiles=True)
+        assert _key(dm) == _key(da)
+        assert dm["species"][0]["rb_merged"] > 0 and dm["species"][0]["rb_split"] > 0
+        assert np.array_equal(dm["density"], da["density"])
+    eng.close()
+
+
+def test_rebalancing_run_grows_like_an_ample_one():
+    """A rebalancing run given its initial load plus 300 particles of capacity,
+    growing automatically, follows the run given ample capacity particle for
+    particle (weights carried through the reallocation)."""
+    a = gpu_from_config(_small_rb(24, 20, capacity_extra=40_000))
+    b = gpu_from_config(_small_rb(24, 20, capacity_extra=300))
+    b.set_auto_grow(True)
+    a.step(240)
+    b.step(240)
+    a.sync()
+    b.sync()
+    assert _key(a.diagnostics()) == _key(b.diagnostics())
+    for s in range(2):
+        pa, pb = a.get_particles(s), b.get_particles(s)
+        ka, kb = a.get_weights(s), b.get_weights(s)
+        ia, ib = np.argsort(pa["id"]), np.argsort(pb["id"])
+        for key in ("cell", "xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+        assert np.array_equal(ka[ia], kb[ib])
