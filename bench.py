@@ -294,6 +294,9 @@ def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
         flush.sum()
 
     with torch.cuda.stream(stream):
+        # sort cadence (divisors of the timed steps) and pass grid from the
+        # library's autotuner, as for the batched line
+        tuned = run.autotune(16, ks=sort_cadences(steps))
         run.set_phase_timing(True)  # per-phase events inside the replayed steps
         for _ in range(warmup):
             l2_flush()
@@ -324,7 +327,8 @@ def single_run_block(torch, ecpic, stream, device, steps=100, warmup=10):
             "field_ms_avg": prof["field_ms"] / max(1, prof["launches"][1]),
             "collide_ms_avg": prof["collide_ms"] / max(1, prof["launches"][3]),
             "sort_ms_per_step": prof["sort_ms"] / max(1, prof["steps"]),
-            "steps_timed": prof["steps"]}
+            "steps_timed": prof["steps"], "sort_every": tuned["sort_every"],
+            "pass_ctas": tuned["pass_ctas"] or "auto"}
 
 
 def one_by_one_block(ecpic, cfgs, stream, device, n_runs=12, steps=200):
