@@ -79,3 +79,38 @@ def test_max_species_one_step(weights, scheme):
     cfg.species.append(I.Species(-I.QE, m40, w * f3, 6000, 2000, 0.05))
     assert len(cfg.species) == MAX_SPECIES
     _one_step(cfg, True)
+
+
+@pytest.mark.parametrize("grid", ["tanh", "doubling"])
+def test_potential_error_on_stretched_grids_at_max_cells(grid):
+    """The GPU solves Eq. 4 through Gauss's law (integer prefix sums, then one
+    FP64 scan for phi); on a stretched grid of up to ECPIC_MAX_CELLS cells the
+    scan is longest.  Both sides get the same FP32 offsets, so the deposits
+    differ by at most 2^-32 of a share per particle and the potential
+    difference measures the solver's accumulation: within 1e-9 of the
+    potential's scale (FP64), the stored FP32 face field within 2^-22 of its
+    scale."""
+    import oracle
+    L = 0.05
+    if grid == "tanh":
+        edges = I.tanh_edges(MAX_CELLS, L, L / MAX_CELLS / 16)
+    else:
+        edges = oracle.doubling_grid(8192, L, 0.004, 1, 16)
+    assert edges.size - 1 <= MAX_CELLS
+    dx = np.diff(edges)
+    assert dx.max() / dx.min() >= 16
+    cfg = I.ccp("stretched", N=edges.size - 1, n0=5e13, dt=1.0 / (400 * I.F_RF), ppc=0,
+                v0=300.0, p_mtorr=60.0, n_steps=1, seed=9, edges=edges, L=L, collisions=False,
+                n_per_species=24 * MAX_CELLS)
+    g, o = gpu_from_config(cfg), oracle_from_config(cfg)
+    _set_same_state(cfg, g, o)
+    fg, fo = g.fields(), o.fields()
+    ps = np.max(np.abs(fo["phi"]))
+    es = np.max(np.abs(fo["E"]))
+    dphi = np.max(np.abs(fg["phi"] - fo["phi"])) / ps
+    dE = np.max(np.abs(fg["E"] - fo["E"])) / es
+    print(f"\n{grid} {edges.size - 1} cells: max |dphi|/scale {dphi:.3e}, max |dE|/scale {dE:.3e}")
+    assert dphi <= 1e-9, dphi
+    assert dE <= 2.0 ** -22, dE
+    g.close()
+    o.close()
