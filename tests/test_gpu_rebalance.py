@@ -74,10 +74,12 @@ def _node_charges(edges, cell, xi, k):
     return D
 
 
-@pytest.mark.parametrize("scheme,grid", [(I.EC, "uniform"), (I.MC, "uniform"), (I.EC, "doubling")])
-def test_one_rebalancing_matches_oracle(scheme, grid):
+@pytest.mark.parametrize("scheme,grid,bc", [(I.EC, "uniform", I.DIRICHLET), (I.MC, "uniform", I.DIRICHLET),
+                                            (I.EC, "doubling", I.DIRICHLET), (I.MC, "doubling", I.PERIODIC)])
+def test_one_rebalancing_matches_oracle(scheme, grid, bc):
     edges = None if grid == "uniform" else oracle.doubling_grid(64, 0.04, 0.008, 1, 4)
     cfg = _cfg(edges=edges, scheme=scheme)
+    cfg.bc = bc
     rng = np.random.default_rng(7)
     N = cfg.N
     counts = rng.integers(0, 90, N)  # target 24: over-full (> 36) and under-full (< 12) cells
