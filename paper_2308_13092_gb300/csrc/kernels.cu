@@ -239,29 +239,67 @@ __device__ void dep_flush(uint32_t* dcnt, uint32_t* dlo, uint32_t* dhi, int a, i
 
 // ---- weighted CIC deposit (rebalancing runs) -----------------------------
 // A particle of weight multiplier k adds k (2^32 - r) to node c and k r to
-// node c+1 (64-bit shared sums, one per node).  With k <= kRbMaxWeight = 2^16
-// a particle adds at most 2^48 to a node, so flushing every kFlushParticles/2
-// = 2^15 particles keeps every sum below 2^63.
-__device__ __forceinline__ void depw_add4(unsigned long long* d64, const int c[4], const float f[4],
-                                          const unsigned k[4]) {
+// node c+1.  Shared 64-bit atomics are compare-and-swap loops on this part
+// and the lanes of a warp share a few cells on sorted data, so the sums stay
+// in native 32-bit atomics: with r = rh 2^16 + rl, k rl = a1 2^16 + a0 and
+// k rh = b1 2^16 + b0 (k <= 2^16, so every piece is below 2^16), each cell
+// keeps K = sum k, A = sum a0, M = sum (a1 + b0), B = sum b1, and
+// R = sum k r = 2^32 B + 2^16 M + A.  Flushed at least every
+// kFlushParticles / 2 = 2^15 particles, K stays <= 2^31 and M < 2^32.
+// Four arrays keep the pass at four CTAs per SM on 1024-cell batches.
+struct DepW {
+  uint32_t *k, *a, *m, *b;  // (nmax + 1) each
+};
+
+__device__ __forceinline__ void depw_add4(const DepW& d, const int c[4], const float f[4],
+                                          const unsigned kq[4]) {
+  unsigned K[4], A[4], M[4], B[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    if (c[j] >= 0) {
-      const unsigned long long r = __float2uint_rz(f[j] * 4294967296.0f);
-      atomicAdd(d64 + c[j], (unsigned long long)k[j] * (4294967296ull - r));
-      atomicAdd(d64 + c[j] + 1, (unsigned long long)k[j] * r);
+    const bool v = c[j] >= 0;
+    const unsigned r = v ? __float2uint_rz(f[j] * 4294967296.0f) : 0u;
+    const unsigned k = v ? kq[j] : 0u;
+    const unsigned p = k * (r & 0xFFFFu), q = k * (r >> 16);
+    K[j] = k;
+    A[j] = p & 0xFFFFu;
+    M[j] = (p >> 16) + (q & 0xFFFFu);
+    B[j] = q >> 16;
+  }
+#pragma unroll
+  for (int j = 3; j >= 1; --j) {
+    if (c[j] >= 0 && c[j] == c[j - 1]) {
+      K[j - 1] += K[j];
+      A[j - 1] += A[j];
+      M[j - 1] += M[j];
+      B[j - 1] += B[j];
+      K[j] = 0u;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (K[j]) {
+      atomicAdd(d.k + c[j], K[j]);
+      atomicAdd(d.a + c[j], A[j]);
+      atomicAdd(d.m + c[j], M[j]);
+      atomicAdd(d.b + c[j], B[j]);
     }
   }
 }
 
-// Adds the sums of nodes [a, e] to S and clears them; every thread of the
-// block calls it, between barriers.
-__device__ void depw_flush(unsigned long long* d64, int a, int e, unsigned long long* S) {
-  for (int n = a + (int)threadIdx.x; n <= e; n += (int)blockDim.x) {
-    const unsigned long long v = d64[n];
-    if (v) {
-      atomicAdd(S + n, v);
-      d64[n] = 0ull;
+// Adds the sums of cells [a, e) to the node array S (cell c to nodes c and
+// c+1) and clears them; every thread of the block calls it, between barriers.
+__device__ void depw_flush(const DepW& d, int a, int e, unsigned long long* S) {
+  for (int c = a + (int)threadIdx.x; c < e; c += (int)blockDim.x) {
+    const uint32_t K = d.k[c];
+    if (K) {
+      const unsigned long long R = ((unsigned long long)d.b[c] << 32) +
+                                   ((unsigned long long)d.m[c] << 16) + d.a[c];
+      atomicAdd(S + c, ((unsigned long long)K << 32) - R);
+      if (R) atomicAdd(S + c + 1, R);
+      d.k[c] = 0u;
+      d.a[c] = 0u;
+      d.m[c] = 0u;
+      d.b[c] = 0u;
     }
   }
 }
@@ -667,12 +705,13 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
 // 32-byte sectors anyway) and on energy-sample steps; otherwise the test
 // reads them per candidate.
 //
-// Compiled four times (KIND): 0 = ordinary steps of the linear schemes (the
+// Compiled five times (KIND): 0 = ordinary steps of the linear schemes (the
 // common case), 1 = their energy-sample steps (moments, energy, EEDF, J.E),
-// 2 = the EC2 scheme with the sample decision taken at run time, 3 = the
-// linear schemes with per-particle weight multipliers (rebalancing runs),
-// sample decision at run time.  Keeping the rare code out of the common
-// instance keeps its loop small in the instruction cache.
+// 2 = the EC2 scheme with the sample decision taken at run time, 3 and 4 =
+// the linear schemes with per-particle weight multipliers (rebalancing
+// runs), ordinary and sample steps.  Keeping the rare code out of the
+// common instances keeps their loops small in the instruction cache and
+// their registers free of the sample-step state.
 // L2 prefetch of a byte range (one bulk instruction; 16-byte aligned start,
 // size a multiple of 16)
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -699,10 +738,10 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   const uint64_t* pid = G.id[cur];
   const long long k = st->step;
   const bool stepping = (mode == MODE_STEP);
-  constexpr bool weighted = KIND == 3;
+  constexpr bool weighted = KIND == 3 || KIND == 4;
   const uint32_t* pwt = weighted ? G.wt[cur] : nullptr;
-  const bool sample = KIND == 1 ||
-                      ((KIND == 2 || KIND == 3) && stepping && R->sample_every > 0 &&
+  const bool sample = KIND == 1 || KIND == 4 ||
+                      (KIND == 2 && stepping && R->sample_every > 0 &&
                        ((k + 1) % R->sample_every) == 0);
   const SpeciesDev* SP = &R->sp[sp];
   const float qm_dt = SP->qm_dt, dtdx_u = R->dtdx_u;
@@ -747,8 +786,9 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   uint32_t* dcnt = dep;
   uint32_t* dlo = dep + (b.nmax + 1);
   uint32_t* dhi = dep + 2 * (b.nmax + 1);
-  // weighted runs: one 64-bit sum per node over the first two arrays
-  unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dep);
+  // weighted runs: four 32-bit sums per cell (dep holds four arrays when the
+  // batch has weighted runs)
+  const DepW dw{dep, dep + (b.nmax + 1), dep + 2 * (b.nmax + 1), dep + 3 * (b.nmax + 1)};
   unsigned long long* Sg = R->S + (size_t)sp * (N + 1);
   int since_flush = 0;
 
@@ -802,8 +842,10 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           v[j] = in ? pvx[i0 + j] : 0.0f;
         }
       }
-      unsigned kq[4] = {1u, 1u, 1u, 1u};  // weight multipliers
-      if (weighted) {
+      // weight multipliers: read here on sample steps (the moments use them),
+      // else just before the deposit (a shorter live range)
+      unsigned kq[4] = {1u, 1u, 1u, 1u};
+      if (weighted && sample) {
         if (full) {
           const uint4 k4 = *reinterpret_cast<const uint4*>(pwt + i0);
           kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
@@ -1036,8 +1078,18 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       // (pre-collision: the collision adds the change)
       if (order2)
         dep2_add4(dlo, dhi, N, !walls, c, f);
-      else if (weighted)
-        depw_add4(d64, c, f, kq);
+      else if (weighted) {
+        if (!sample) {
+          if (full) {
+            const uint4 k4 = *reinterpret_cast<const uint4*>(pwt + i0);
+            kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kq[j] = (inq && i0 + j < n) ? pwt[i0 + j] : 1u;
+          }
+        }
+        depw_add4(dw, c, f, kq);
+      }
       else
         dep_add4(dcnt, dlo, dhi, c, f);
 #pragma unroll
@@ -1133,7 +1185,7 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
       if (order2)
         dep2_flush(dlo, dhi, 0, N, Sg);
       else if (weighted)
-        depw_flush(d64, 0, N, Sg);
+        depw_flush(dw, 0, N, Sg);
       else
         dep_flush(dcnt, dlo, dhi, 0, N, Sg);
       __syncthreads();
@@ -1181,8 +1233,8 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   if (flo < fhi) {
     if (order2)  // shares reach one node beyond the range, or wrap
       dep2_flush(dlo, dhi, walls ? max(flo - 1, 0) : 0, walls ? min(fhi + 1, N) : N, Sg);
-    else if (weighted)  // nodes flo..fhi (a cell's two nodes)
-      depw_flush(d64, flo, fhi, Sg);
+    else if (weighted)
+      depw_flush(dw, flo, fhi, Sg);
     else
       dep_flush(dcnt, dlo, dhi, flo, fhi, Sg);
   }
@@ -1224,17 +1276,22 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
   __syncthreads();
 }
 
-template <bool STAGE>
+// WEIGHTED: the batch holds rebalancing runs (weight multipliers).  Their
+// instance of the pass is compiled into a kernel of its own so that the
+// kernel of unweighted batches keeps its register allocation.
+template <bool STAGE, bool WEIGHTED>
 __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, int only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
-  // deposit sums, 3 (nmax+1): count, lo, hi (linear); -, lo, hi per node (EC2)
+  // deposit sums, 3 (nmax+1): count, lo, hi (linear); -, lo, hi per node (EC2);
+  // four when the batch has weighted runs
   uint32_t* dep = reinterpret_cast<uint32_t*>(pre + b.nseg + 1);
-  float* Msm = reinterpret_cast<float*>(dep + 3 * (b.nmax + 1));
+  const int ndep = b.weighted ? 4 : 3;
+  float* Msm = reinterpret_cast<float*>(dep + ndep * (b.nmax + 1));
   unsigned char* ring = reinterpret_cast<unsigned char*>(Msm + 3 * (b.nmax + 1));  // Msm: M1 | M2 | J.E
   __shared__ PassShared sh;
   for (int i = threadIdx.x; i <= b.nmax; i += kPassBlock) {
-    for (int q = 0; q < 3; ++q) dep[q * (b.nmax + 1) + i] = 0u;
+    for (int q = 0; q < ndep; ++q) dep[q * (b.nmax + 1) + i] = 0u;
     Msm[i] = 0.0f;
     Msm[b.nmax + 1 + i] = 0.0f;
     Msm[2 * (b.nmax + 1) + i] = 0.0f;
@@ -1264,8 +1321,10 @@ __global__ void __launch_bounds__(kPassBlock, 4) k_pass(BatchView b, int mode, i
     const bool smp = stepping && R.sample_every > 0 && ((k + 1) % R.sample_every) == 0;
     if (R.scheme >= ECPIC_SCHEME_EC2)  // EC2, MC2
       pass_piece<2, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
-    else if (R.rb)  // weight multipliers
-      pass_piece<3, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    else if (WEIGHTED && R.rb && smp)  // weight multipliers
+      pass_piece<WEIGHTED ? 4 : 1, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
+    else if (WEIGHTED && R.rb)
+      pass_piece<WEIGHTED ? 3 : 0, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else if (smp)
       pass_piece<1, STAGE>(b, s, beg, end, mode, dep, Msm, ring, sh);
     else
@@ -2373,7 +2432,8 @@ __global__ void k_philox_device(long long n, const uint32_t* ctr, const uint32_t
 // ----------------------------------------------------------------- launchers
 size_t pass_smem_bytes(const BatchView& b) {
   return sizeof(long long) * (size_t)(b.nseg + 1) +
-         3 * sizeof(uint32_t) * (size_t)(b.nmax + 1) + sizeof(float) * 3 * (size_t)(b.nmax + 1) +
+         (b.weighted ? 4 : 3) * sizeof(uint32_t) * (size_t)(b.nmax + 1) +
+         sizeof(float) * 3 * (size_t)(b.nmax + 1) +
          sizeof(int) * (size_t)(3 * kRing) * (kPassBlock / 32) + sizeof(float) * (size_t)(b.nmax + 1);
 }
 
@@ -2383,24 +2443,38 @@ static void set_smem_attr(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <bool W>
+static int pass_occupancy(size_t sm) {
+  set_smem_attr((const void*)k_pass<true, W>, sm);
+  set_smem_attr((const void*)k_pass<false, W>, sm);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<true, W>, kPassBlock, sm);
+  return n > 0 ? n : 1;
+}
+
 int pass_max_ctas_per_sm(const BatchView& b) {
   const size_t sm = pass_smem_bytes(b);
-  set_smem_attr((const void*)k_pass<true>, sm);
-  set_smem_attr((const void*)k_pass<false>, sm);
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<true>, kPassBlock, sm);
-  return n > 0 ? n : 1;
+  return b.weighted ? pass_occupancy<true>(sm) : pass_occupancy<false>(sm);
+}
+
+template <bool W>
+static void launch_pass_w(const BatchView& b, int grid, int mode, int only, cudaStream_t s,
+                          bool stage_field, size_t sm) {
+  if (stage_field) {
+    set_smem_attr((const void*)k_pass<true, W>, sm);
+    k_pass<true, W><<<grid, kPassBlock, sm, s>>>(b, mode, only);
+  } else {
+    set_smem_attr((const void*)k_pass<false, W>, sm);
+    k_pass<false, W><<<grid, kPassBlock, sm, s>>>(b, mode, only);
+  }
 }
 
 void launch_pass(const BatchView& b, int grid, int mode, int only, cudaStream_t s, bool stage_field) {
   const size_t sm = pass_smem_bytes(b);
-  if (stage_field) {
-    set_smem_attr((const void*)k_pass<true>, sm);
-    k_pass<true><<<grid, kPassBlock, sm, s>>>(b, mode, only);
-  } else {
-    set_smem_attr((const void*)k_pass<false>, sm);
-    k_pass<false><<<grid, kPassBlock, sm, s>>>(b, mode, only);
-  }
+  if (b.weighted)
+    launch_pass_w<true>(b, grid, mode, only, s, stage_field, sm);
+  else
+    launch_pass_w<false>(b, grid, mode, only, s, stage_field, sm);
 }
 
 void launch_collide(const BatchView& b, int grid, cudaStream_t s) {

@@ -20,6 +20,7 @@ struct BatchView {
   int max_slots;
   int nseg;
   int nmax;             // largest N in the batch
+  int weighted;         // some resident run carries weight multipliers (rebalancing)
 };
 
 struct InitParams {

@@ -460,6 +460,9 @@ BatchView Batch::view() const {
   v.max_slots = max_slots_;
   v.nseg = nseg_;
   v.nmax = nmax_;
+  v.weighted = 0;
+  for (int s = 0; s < max_slots_; ++s)
+    if (active_[s] && specs_[s].rb) v.weighted = 1;
   return v;
 }
 
@@ -975,10 +978,13 @@ int Batch::ensure_graphs(std::string* err) {
   const bool built = timing_ ? (tk_[0].exec && tk_[1].exec && t1_[0].exec && t1_[1].exec &&
                                 ts_[0].exec && ts_[1].exec)
                              : (graph_k_ && graph_1_);
-  if (built && g == pass_grid_ && stage_field(g) == graph_stage_) return ECPIC_OK;
+  const int w = view().weighted;
+  if (built && g == pass_grid_ && stage_field(g) == graph_stage_ && w == graph_weighted_)
+    return ECPIC_OK;
   invalidate_graphs();
   pass_grid_ = g;
   graph_stage_ = stage_field(g);
+  graph_weighted_ = w;
   int rc = ECPIC_OK;
   if (timing_) {
     for (int i = 0; i < 2 && rc == ECPIC_OK; ++i) {

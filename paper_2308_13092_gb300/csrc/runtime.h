@@ -216,6 +216,7 @@ class Batch {
   int pass_grid_ = 0;
   int pass_grid_override_ = 0;
   bool graph_stage_ = true;
+  int graph_weighted_ = 0;  // the graphs were captured for a batch with weighted runs
   cudaGraphExec_t graph_k_ = nullptr;
   cudaGraphExec_t graph_1_ = nullptr;
   bool timing_ = false;

@@ -255,6 +255,35 @@ def test_rebalancing_run_alone_equals_run_in_mix():
     eng.close()
 
 
+def test_rebalancing_run_admitted_into_a_stepping_batch():
+    """A plain run steps alone (the step graphs are captured for a batch with
+    no weight multipliers); a rebalancing run then joins, and later leaves
+    while the plain run goes on.  The batch's pass switches to the weighted
+    kernel and back; both runs equal the same runs stepped alone."""
+    from paper_2308_13092_gb300 import ecpic
+    plain = I.config_small(seed=24)
+    plain.n_steps = 400
+    plain.sample_every = 10
+    rb = _small_rb(25, 20)
+    eng = ecpic.Engine(max_slots=2, max_cells=256)
+    t0 = eng.submit(plain)
+    eng.pump(60)
+    t1 = eng.submit(rb)
+    while True:
+        r, q = eng.pump(50)
+        if r == 0 and q == 0:
+            break
+    for c, t in ((plain, t0), (rb, t1)):
+        dm = eng.poll(t, diagnostics=True, profiles=True)["diag"]
+        g = gpu_from_config(c)
+        g.step(c.n_steps)
+        g.sync()
+        da = g.diagnostics(profiles=True)
+        assert _key(dm) == _key(da)
+        assert np.array_equal(dm["density"], da["density"])
+    eng.close()
+
+
 def test_rebalancing_run_grows_like_an_ample_one():
     """A rebalancing run given its initial load plus 300 particles of capacity,
     growing automatically, follows the run given ample capacity particle for
