@@ -63,8 +63,8 @@ AUTOTUNE_STEPS = 64  # steps per autotuner trial (20 trials) before the warm-up
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "a2121a0f3f2769d150dfd1f81ce6a0a0d78a72672a6ce9464de0406ca9b62adb",
-           "dram_bytes_per_particle_step": 570.676e6 / 14.3047e6}
+TRAFFIC = {"sources_sha256": "0712e120484b9a20c36af8e7fe4d754575c2286fcaea9758d9b1332714eeadac",
+           "dram_bytes_per_particle_step": 570.058e6 / 14.3047e6}
 
 
 def kernel_sources_sha256():
