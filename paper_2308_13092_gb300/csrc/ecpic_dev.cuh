@@ -121,7 +121,7 @@ struct RunState {
   long long step;       // current time level k
   long long step_end;   // stepping stops at this level
   int status;           // first device-side error (ecpic_status)
-  int pad;
+  int fresh;            // admitted in a wave, its particles and step-0 field not yet formed
   long long n_samples;
   double ke_acc[kMaxSpecies];   // accumulating during a sampled push
   double ke[kMaxSpecies];       // of the last sampled push

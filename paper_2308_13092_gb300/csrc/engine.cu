@@ -265,7 +265,7 @@ int ecpic_engine_pump(ecpic_engine* e, int64_t max_steps, int* n_resident, int* 
         ++it;
         continue;
       }
-      int rc = e->batch->admit(slot, it->spec, &err);
+      int rc = e->batch->admit(slot, it->spec, &err, true);
       auto& tk = e->tickets[it->ticket];
       if (rc == ECPIC_ERR_NOMEM) {
         ++it;  // device allocation failed: keep it queued
@@ -279,6 +279,10 @@ int ecpic_engine_pump(ecpic_engine* e, int64_t max_steps, int* n_resident, int* 
         e->slot_ticket[slot] = it->ticket;
       }
       it = e->queue.erase(it);
+    }
+    {
+      int rc = e->batch->admit_wave(&err);
+      if (rc) return efail(e, rc, err);
     }
     int resident = 0;
     for (int s = 0; s < e->max_slots; ++s) resident += e->slot_ticket[s] ? 1 : 0;

@@ -110,7 +110,7 @@ __device__ void block_incl_scan_array(T* a, int n, T* wsm) {
 __device__ __forceinline__ bool run_live(const RunDev& R, const RunState& S, int mode, int only,
                                          int slot) {
   if (!R.active) return false;
-  if (mode == MODE_REFRESH) return slot == only;
+  if (mode == MODE_REFRESH) return only == kOnlyFresh ? S.fresh != 0 : slot == only;
   if (S.status != 0) return false;
   if (mode == MODE_STEP) return S.step < S.step_end;
   if (mode == MODE_REBAL)  // a rebalancing run at a rebalancing level (once per level)
@@ -1418,6 +1418,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
   // the loads travel together
   const int active = R->active;
   const int status0 = st->status;
+  const int fresh = st->fresh;
   const long long step0 = st->step, step_end = st->step_end;
   const int N = R->N, ns = R->ns, seg0 = R->seg0;
   const int se = R->sample_every;
@@ -1432,8 +1433,12 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
   if (!active) return;
   if (advance) {
     if (status0 != 0 || step0 >= step_end) return;
-  } else if (only >= 0 && slot != only) {
+  } else if ((only >= 0 && slot != only) || (only == kOnlyFresh && !fresh)) {
     return;
+  }
+  if (only == kOnlyFresh) {
+    __syncthreads();  // every thread has read the flag
+    if (threadIdx.x == 0) st->fresh = 0;
   }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* C = reinterpret_cast<double*>(smem_raw);  // N+1
@@ -2294,7 +2299,7 @@ __global__ void k_rb_mark(BatchView b) {
 // Uniform positions and Maxwellian velocities (Sec. 2b) from Philox blocks
 // (id = i, step word 0xFFFFFFFF, word3 = (s<<8)|0x80 for X, |0x81 for v),
 // in FP64 so that the cell index matches the FP64 definition exactly.
-__global__ void k_init(BatchView b, int slot, InitParams p) {
+__device__ __forceinline__ void init_run(const BatchView& b, int slot, const InitParams& p) {
   const RunDev* R = b.runs + slot;
   const int sp = blockIdx.y;
   if (sp >= R->ns) return;
@@ -2347,6 +2352,16 @@ __global__ void k_init(BatchView b, int slot, InitParams p) {
     G.id[cur][i] = (uint64_t)i;
     if (G.wt[cur]) G.wt[cur][i] = p.rb_m0;
   }
+}
+
+__global__ void k_init(BatchView b, int slot, InitParams p) { init_run(b, slot, p); }
+
+// A wave of admitted runs: blockIdx.z indexes the list of slots.
+__global__ void k_init_many(BatchView b, const int* slots, const InitParams* ps, int count) {
+  if ((int)blockIdx.z >= count) return;
+  const int slot = slots[blockIdx.z];
+  if (slot < 0 || slot >= b.max_slots) return;
+  init_run(b, slot, ps[blockIdx.z]);
 }
 
 // ----------------------------------------------------------------- test kernels
@@ -2537,6 +2552,18 @@ void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t
   if (blocks < 1) blocks = 1;
   if (blocks > 4096) blocks = 4096;
   k_init<<<dim3((unsigned)blocks, kMaxSpecies), 256, 0, s>>>(b, slot, p);
+}
+
+void launch_init_many(const BatchView& b, const int* slots, const InitParams* ps, int count,
+                      long long nmax, cudaStream_t s) {
+  if (count <= 0) return;
+  long long blocks = (nmax + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  for (int off = 0; off < count; off += 65535) {
+    const int c = count - off < 65535 ? count - off : 65535;
+    k_init_many<<<dim3((unsigned)blocks, kMaxSpecies, (unsigned)c), 256, 0, s>>>(b, slots + off, ps + off, c);
+  }
 }
 
 void launch_deposit_device(int N, long long n, const int* cell, const float* xi,

@@ -23,6 +23,10 @@ struct BatchView {
   int weighted;         // some resident run carries weight multipliers (rebalancing)
 };
 
+// `only` argument of the refresh pass and field: the runs admitted in the
+// current wave (RunState::fresh set) instead of one slot
+constexpr int kOnlyFresh = -2;
+
 struct InitParams {
   long long n[kMaxSpecies];
   double sd[kMaxSpecies];  // sqrt(e T / m)
@@ -44,6 +48,10 @@ void launch_phi(const BatchView& b, int slot, cudaStream_t s);
 void launch_sort(const BatchView& b, int grid, cudaStream_t s);
 void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s);
 void launch_init(const BatchView& b, int slot, const InitParams& p, cudaStream_t s);
+// Loads the particles of `count` runs (device arrays of slots and their
+// parameters); nmax = the largest species load among them.
+void launch_init_many(const BatchView& b, const int* slots, const InitParams* ps, int count,
+                      long long nmax, cudaStream_t s);
 // particle rebalancing of the runs due at their current level (or forced):
 // counting sort by cell into the other buffer set, then per cell the merge /
 // split plan, its scan, the merged/split particles written back, sizes set

@@ -378,9 +378,13 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
   cudaMalloc(&d_sst_, sizeof(SegState) * nseg_);
   cudaMalloc(&d_hist_, sizeof(int) * (size_t)nseg_ * nmax_);
   cudaMalloc(&d_rbcnt_, sizeof(int) * (size_t)nseg_ * nmax_);
+  cudaMalloc(&d_wave_slots_, sizeof(int) * max_slots_);
+  cudaMalloc(&d_wave_params_, sizeof(InitParams) * max_slots_);
   level_.assign(max_slots_, 0);
   h_runs_.assign(max_slots_, RunDev{});
   h_segs_.assign(nseg_, SegDev{});
+  wave_sst_.assign(nseg_, SegState{});
+  wave_rst_.assign(max_slots_, RunState{});
   for (int s = 0; s < nseg_; ++s) {
     h_segs_[s].run = s / spc_;
     h_segs_[s].species = s % spc_;
@@ -415,6 +419,8 @@ Batch::~Batch() {
   cudaFree(d_sst_);
   cudaFree(d_hist_);
   cudaFree(d_rbcnt_);
+  cudaFree(d_wave_slots_);
+  cudaFree(d_wave_params_);
   if (own_stream_) cudaStreamDestroy(stream_);
 }
 
@@ -470,7 +476,7 @@ void Batch::upload_run(int slot) {
   cudaMemcpyAsync(d_runs_ + slot, &h_runs_[slot], sizeof(RunDev), cudaMemcpyHostToDevice, stream_);
 }
 
-int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
+int Batch::admit(int slot, const RunSpec& spec, std::string* err, bool defer) {
   if (slot < 0 || slot >= max_slots_ || active_[slot]) {
     if (err) *err = "slot unavailable";
     return ECPIC_ERR_STATE;
@@ -647,21 +653,30 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
   cudaMemcpyAsync(mem, img, data_end, cudaMemcpyHostToDevice, stream_);
   stage_done(ks);
   cudaMemsetAsync(static_cast<char*>(mem) + data_end, 0, prefix - data_end, stream_);
-  cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
-                  stream_);
-  cudaMemcpyAsync(d_sst_ + R.seg0, sst.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
-                  stream_);
   RunState st{};
   st.step = 0;
   st.step_end = spec.step_end;
   st.rb_level = -1;
+  st.fresh = defer ? 1 : 0;
   level_[slot] = 0;
-  // the slot's cell arrays start from zero whatever its last run left
-  cudaMemsetAsync(d_hist_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_, stream_);
-  cudaMemsetAsync(d_rbcnt_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_, stream_);
-  cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
   h_runs_[slot] = R;
-  upload_run(slot);
+  if (defer) {
+    // the slot's tables, states and cell arrays go up with its wave
+    std::copy(sst.begin(), sst.end(), wave_sst_.begin() + (size_t)slot * spc_);
+    wave_rst_[slot] = st;
+  } else {
+    cudaMemcpyAsync(d_segs_ + R.seg0, &h_segs_[R.seg0], sizeof(SegDev) * spc_, cudaMemcpyHostToDevice,
+                    stream_);
+    cudaMemcpyAsync(d_sst_ + R.seg0, sst.data(), sizeof(SegState) * spc_, cudaMemcpyHostToDevice,
+                    stream_);
+    // the slot's cell arrays start from zero whatever its last run left
+    cudaMemsetAsync(d_hist_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_,
+                    stream_);
+    cudaMemsetAsync(d_rbcnt_ + (size_t)slot * spc_ * nmax_, 0, sizeof(int) * (size_t)spc_ * nmax_,
+                    stream_);
+    cudaMemcpyAsync(d_rst_ + slot, &st, sizeof(RunState), cudaMemcpyHostToDevice, stream_);
+    upload_run(slot);
+  }
   slot_mem_[slot] = mem;
   slot_bytes_[slot] = bytes;
   bytes_in_use_ += bytes;
@@ -675,9 +690,66 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err) {
     ip.n[s] = spec.n_init[s];
     ip.sd[s] = std::sqrt(kQe * spec.T_eV[s] / spec.species[s].m);
   }
+  if (defer) {
+    wave_slots_.push_back(slot);
+    wave_params_.push_back(ip);
+    return ECPIC_OK;
+  }
   launch_init(view(), slot, ip, stream_);
   refresh(slot);
   return check(cudaGetLastError(), "admit", err);
+}
+
+int Batch::admit_wave(std::string* err) {
+  const int count = (int)wave_slots_.size();
+  if (count == 0) return ECPIC_OK;
+  cudaSetDevice(device_);
+  long long nmax = 0;
+  for (const InitParams& p : wave_params_)
+    for (int s = 0; s < kMaxSpecies; ++s) nmax = std::max(nmax, p.n[s]);
+  // the wave's run tables, segment tables and states, and zeroed cell
+  // arrays, one copy per contiguous range of slots (pageable sources: each
+  // copy has left them when the call returns)
+  std::vector<int> sl = wave_slots_;
+  std::sort(sl.begin(), sl.end());
+  int rc = ECPIC_OK;
+  for (size_t i = 0; i < sl.size() && !rc;) {
+    size_t j = i + 1;
+    while (j < sl.size() && sl[j] == sl[j - 1] + 1) ++j;
+    const size_t a = (size_t)sl[i], n = (size_t)(sl[j - 1] - sl[i] + 1), sa = a * spc_, sn = n * spc_;
+    rc = check(cudaMemcpyAsync(d_runs_ + a, &h_runs_[a], sizeof(RunDev) * n, cudaMemcpyHostToDevice,
+                               stream_), "wave upload", err);
+    if (!rc)
+      rc = check(cudaMemcpyAsync(d_rst_ + a, &wave_rst_[a], sizeof(RunState) * n,
+                                 cudaMemcpyHostToDevice, stream_), "wave upload", err);
+    if (!rc)
+      rc = check(cudaMemcpyAsync(d_segs_ + sa, &h_segs_[sa], sizeof(SegDev) * sn,
+                                 cudaMemcpyHostToDevice, stream_), "wave upload", err);
+    if (!rc)
+      rc = check(cudaMemcpyAsync(d_sst_ + sa, &wave_sst_[sa], sizeof(SegState) * sn,
+                                 cudaMemcpyHostToDevice, stream_), "wave upload", err);
+    if (!rc)
+      rc = check(cudaMemsetAsync(d_hist_ + sa * nmax_, 0, sizeof(int) * sn * nmax_, stream_),
+                 "wave upload", err);
+    if (!rc)
+      rc = check(cudaMemsetAsync(d_rbcnt_ + sa * nmax_, 0, sizeof(int) * sn * nmax_, stream_),
+                 "wave upload", err);
+    i = j;
+  }
+  if (!rc)
+    rc = check(cudaMemcpyAsync(d_wave_slots_, wave_slots_.data(), sizeof(int) * count,
+                               cudaMemcpyHostToDevice, stream_), "wave upload", err);
+  if (!rc)
+    rc = check(cudaMemcpyAsync(d_wave_params_, wave_params_.data(), sizeof(InitParams) * count,
+                               cudaMemcpyHostToDevice, stream_), "wave upload", err);
+  wave_slots_.clear();
+  wave_params_.clear();
+  if (rc) return rc;
+  const BatchView b = view();
+  launch_init_many(b, d_wave_slots_, d_wave_params_, count, nmax, stream_);
+  launch_pass(b, std::max(1, choose_grid()), MODE_REFRESH, kOnlyFresh, stream_, false);
+  launch_field(b, 0, kOnlyFresh, stream_);
+  return check(cudaGetLastError(), "admission wave", err);
 }
 
 void Batch::refresh(int slot) {

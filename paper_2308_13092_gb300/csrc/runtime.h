@@ -85,8 +85,11 @@ class Batch {
   Batch(const Batch&) = delete;
   Batch& operator=(const Batch&) = delete;
 
-  // allocate, upload, load particles (Philox), first deposit and field
-  int admit(int slot, const RunSpec& spec, std::string* err);
+  // allocate, upload, load particles (Philox), first deposit and field;
+  // with defer, the loading, deposit and field wait for admit_wave(), which
+  // forms them for every run admitted since in three launches
+  int admit(int slot, const RunSpec& spec, std::string* err, bool defer = false);
+  int admit_wave(std::string* err);
   void release(int slot);
   bool slot_active(int slot) const { return slot >= 0 && slot < max_slots_ && active_[slot]; }
 
@@ -197,6 +200,13 @@ class Batch {
   int* d_hist_ = nullptr;
   int* d_rbcnt_ = nullptr;
   std::vector<long long> level_;  // predicted level of each slot
+  // runs admitted with defer, waiting for admit_wave()
+  std::vector<int> wave_slots_;
+  std::vector<InitParams> wave_params_;
+  std::vector<SegState> wave_sst_;  // per slot x species: initial segment states
+  std::vector<RunState> wave_rst_;  // per slot: initial run states
+  int* d_wave_slots_ = nullptr;
+  InitParams* d_wave_params_ = nullptr;
   std::vector<RunDev> h_runs_;
   std::vector<SegDev> h_segs_;
   std::vector<void*> slot_mem_;
