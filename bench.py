@@ -21,7 +21,7 @@ Also reported (same JSON line):
   served      a Poisson stream of run requests admitted by device memory,
               with p50/p99 completion latency, against one-at-a-time service;
   e2e         the batched job through the public API from host configs to
-              host diagnostics.
+              host diagnostics, whole jobs of 5 RF periods (2000 steps).
 The timed window holds whole sort cycles: the autotuner picks the sort
 cadence K among the divisors of --steps (4..64), the warm-up runs on to a sort
 boundary, and the window's per-kernel device times come from CUDA events
@@ -57,6 +57,7 @@ BYTES_PER_PARTICLE_STEP = 40
 METRIC = "particle-steps/s"
 N_RUNS = 256
 AUTOTUNE_STEPS = 64  # steps per autotuner trial (20 trials) before the warm-up
+E2E_STEPS = 2000  # end-to-end job length: 5 RF periods at 400 steps per period
 
 # DRAM traffic of k_pass measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one stepping launch on the 64-run manifest, see
@@ -484,8 +485,9 @@ def e2e_block(ecpic, cfgs, stream, device, steps):
     return {"value": ps / dt, "unit": "particle-steps/s",
             "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
             "steps": steps,
-            "what": "ecpic_engine_submit of 256 host configs (particles loaded on the GPU), "
-                    "pump to completion, ecpic_engine_poll of every run's diagnostics; wall clock"}
+            "what": f"ecpic_engine_submit of {len(cfgs)} host configs (particles loaded on the GPU), "
+                    f"pump to completion ({steps} steps = {steps // 400} RF periods each), "
+                    "ecpic_engine_poll of every run's diagnostics; wall clock"}
 
 
 def sort_cadences(steps, lo=4, hi=64, want=(8, 16, 32, 64)):
@@ -609,7 +611,9 @@ def main():
         extras["served_load_0.9"] = served_block(ecpic, stream, local,
                                                  capacity=value / max(1, world), rho=0.9)
         extras["appendix_b"] = appendix_b_block(ecpic, stream, local)
-        e2e = e2e_block(ecpic, short, stream, local, steps=200)
+        # whole jobs of 5 RF periods (2000 steps), the shortest request length
+        # of the served stream
+        e2e = e2e_block(ecpic, manifest(rank, args, E2E_STEPS), stream, local, steps=E2E_STEPS)
     else:
         e2e = None
     cpu = None
