@@ -36,6 +36,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -56,8 +57,9 @@ from paper_2308_13092_gb300 import inputs as I  # noqa: E402
 BYTES_PER_PARTICLE_STEP = 40
 METRIC = "particle-steps/s"
 N_RUNS = 256
-AUTOTUNE_STEPS = 64  # steps per autotuner trial (20 trials) before the warm-up
+AUTOTUNE_STEPS = 64  # steps per autotuner trial (two per candidate) before the warm-up
 E2E_STEPS = 2000  # end-to-end job length: 5 RF periods at 400 steps per period
+SAMPLE_EVERY = 40  # energy-sample cadence of the manifest runs: 1/10 RF period
 
 # DRAM traffic of k_pass measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one stepping launch on the 64-run manifest, see
@@ -93,10 +95,20 @@ def parse():
     return ap.parse_args()
 
 
-def autotune_steps(per_trial, Ks=(8, 16, 32, 64), grids=5):
-    """Steps the autotuner advances the runs: per (K, grid) trial, K steps to
-    start the cadence and max(per_trial, 2K) rounded up to whole cycles."""
-    return grids * sum(K + -(-max(per_trial, 2 * K) // K) * K for K in Ks)
+def autotune_steps(per_trial, Ks=(8, 16, 32, 64), grids=5, sample_every=SAMPLE_EVERY):
+    """Steps the autotuner advances the runs: every (K, grid) pair is tried
+    twice; per trial, K steps to start the cadence and max(per_trial, 2K)
+    rounded up to whole cycles of both the sort and the energy sample (the
+    sort cycle alone where their common multiple exceeds 8x that)."""
+    total = 0
+    for K in Ks:
+        want = max(per_trial, 2 * K)
+        cyc = K
+        if sample_every > 0:
+            lcm = K * sample_every // math.gcd(K, sample_every)
+            cyc = lcm if lcm <= 8 * want else K
+        total += K + -(-want // cyc) * cyc
+    return 2 * grids * total
 
 
 def combine_ranks(ms, ps):
@@ -127,7 +139,7 @@ def peaks():
 def manifest(rank, args, steps):
     runs = I.batched_manifest(args.runs, seed=rank, steps=steps, scale=args.scale)
     for r in runs:
-        r.sample_every = 40  # 1/10 RF period at 400 steps per period
+        r.sample_every = SAMPLE_EVERY
     return runs
 
 
@@ -407,7 +419,7 @@ def served_block(ecpic, stream, device, capacity, n_req=256, rho=0.7, slots=64):
     for r in reqs:
         r.config.n_steps = max(40, r.config.n_steps // 10)
         I.with_headroom(r.config, I.growth_headroom(r.config.n_steps))
-        r.config.sample_every = 40
+        r.config.sample_every = SAMPLE_EVERY
     work = np.mean([r.config.n_particles * r.config.n_steps for r in reqs])
     rate = rho * capacity / work
     arr = np.cumsum(np.random.default_rng(2).exponential(1.0 / rate, n_req))
@@ -528,8 +540,7 @@ def main():
     cfgs = manifest(rank, args, total)
     eng = ecpic.Engine(device=local, stream=stream.cuda_stream, max_slots=len(cfgs),
                        max_cells=1024)
-    for c in cfgs:
-        eng.submit(c)
+    tickets = [eng.submit(c) for c in cfgs]
     eng.pump(0)  # admit and load everything
     # sort cadence and pass grid from the autotuner (its trials are steps of
     # the same runs, before the warm-up)
@@ -549,6 +560,10 @@ def main():
         eng.pump(align)  # on to a sort boundary
     assert eng.sort_state()["since_sort"] == 0
     eng.phase_times()  # clear the warm-up's sums
+    # energy-sample steps in the window (every run steps in lockstep from its
+    # admission): the pass of level k samples when (k + 1) % SAMPLE_EVERY == 0
+    k0 = eng.poll(tickets[0], diagnostics=True)["diag"]["step"]
+    samples = sum(1 for k in range(k0, k0 + args.steps) if (k + 1) % SAMPLE_EVERY == 0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ps0 = eng.stats()["particle_steps"]
     if world > 1:
@@ -635,6 +650,7 @@ def main():
                              f"of particle records live per GPU and step, 28 B each)",
                        "sort_every": K, "sort_cadences_tried": ks,
                        "sorts_in_window": sorts,
+                       "sample_steps_in_window": samples,
                        "warmup_steps_run": args.warmup + align,
                        "pass_ctas": tuned["pass_ctas"] or "auto",
                        "tuning": "defaults" if args.no_autotune else

@@ -268,8 +268,12 @@ int ecpic_set_pass_grid(ecpic_run* run, int ctas);
 /* Autotuner over the sort cadence K and the particles per CTA: times the
  * graph-replayed step for each candidate pair of counting-sort cadence K in
  * {8, 16, 32, 64} and pass grid (automatic, one wave at full or half
- * occupancy, two or four waves), steps_per_trial steps each (at least 2K), and keeps
- * the pair with the least device time per particle-step.  The trials advance
+ * occupancy, two or four waves), steps_per_trial steps each (at least 2K,
+ * rounded up to whole sort cycles and, where their common multiple is at most
+ * 8x that, whole energy-sample cycles of the resident runs), every pair
+ * twice (in order, then in reverse order, so that the discharges' evolution
+ * during the trials weighs on all pairs alike), and keeps the pair with the
+ * least mean device time per particle-step.  The trials advance
  * the run for real; results do not depend on K or the grid (integer
  * deposit, id-keyed random numbers).  Outputs may be NULL: the chosen K, the
  * chosen grid (0 = automatic) and its ns per particle-step.  Synchronises. */

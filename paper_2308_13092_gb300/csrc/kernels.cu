@@ -712,6 +712,52 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
 // runs), ordinary and sample steps.  Keeping the rare code out of the
 // common instances keeps their loops small in the instruction cache and
 // their registers free of the sample-step state.
+// Segmented sums across the lanes of a warp for the sample steps' per-node
+// float sums (vx moments, J.E).  Adding every particle's share to shared
+// memory made a sample step's pass ten times an ordinary one: float atomics
+// on shared memory retry while lanes contend, and on cell-sorted particles
+// the 32 lanes of a warp add to the same few cells.  A lane whose particles
+// all lie in one cell takes that cell as its key; consecutive lanes with
+// equal keys form a segment, their values are summed down the segment in
+// five shuffle steps, and the segment's first lane adds the sum to shared
+// memory.  A lane whose particles lie in several cells (drifting electrons
+// some steps after a sort) has key -1 and adds each of its runs of equal
+// cells straight to the run's FP64 sums in HBM.  Called by all lanes.
+__device__ __forceinline__ unsigned warp_seg_heads(int key, bool* head) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+  *head = lane == 0 || key != prev;
+  return __ballot_sync(0xFFFFFFFFu, *head);
+}
+
+// On return, a segment's first lane holds the segment's sum.
+__device__ __forceinline__ float warp_seg_sum(float x, unsigned heads) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long hb = heads;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_down_sync(0xFFFFFFFFu, x, o);
+    // lanes lane+1 .. lane+o start no segment: lane+o is in this one
+    const unsigned long long span = ((1ull << o) - 1ull) << (lane + 1);
+    if (lane + o < 32 && (hb & span) == 0ull) x += y;
+  }
+  return x;
+}
+
+// The key of a lane's valid entries c[j] >= 0: their common cell, -1 if they
+// lie in several cells or there are none.
+__device__ __forceinline__ int lane_cell_key(const int c[4]) {
+  int k = -1;
+  bool multi = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (c[j] >= 0) {
+      if (k < 0) k = c[j];
+      else if (c[j] != k) multi = true;
+    }
+  return multi ? -1 : k;
+}
+
 // L2 prefetch of a byte range (one bulk instruction; 16-byte aligned start,
 // size a multiple of 16)
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -926,23 +972,44 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
           }
         }
         float keq = 0.0f;
+        float pje[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const float vnew = v[j] + qm_dt * Ei[j];
-          if (sample && c[j] >= 0) {
-            if (weighted) {
-              const float fk = (float)kq[j];
-              keq += fk * (v[j] * vnew + yz[j]);
-              atomicAdd(Psm + c[j], fk * ((v[j] + vnew) * Ei[j]));
-            } else {
-              keq += v[j] * vnew + yz[j];
-              // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
-              atomicAdd(Psm + c[j], (v[j] + vnew) * Ei[j]);
-            }
+          if (sample) {
+            const float fk = weighted ? (float)kq[j] : 1.0f;
+            if (c[j] >= 0) keq += fk * (v[j] * vnew + yz[j]);
+            // J.E of the push, per cell at level k (scaled by q w / 2 dx later)
+            pje[j] = c[j] >= 0 ? fk * ((v[j] + vnew) * Ei[j]) : 0.0f;
           }
           v[j] = vnew;
         }
-        if (sample) ke += (double)keq;
+        if (sample) {
+          ke += (double)keq;
+          // J.E per cell of level k: per lane, then down each segment
+          const int key = lane_cell_key(c);
+          float pl = 0.0f;
+          int cc = -1;
+          double* pwg = R->pw + (size_t)sp * N;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (c[j] < 0) continue;
+            if (key < 0 && c[j] != cc) {
+              if (cc >= 0) atomicAdd(pwg + cc, (double)pl);
+              cc = c[j];
+              pl = 0.0f;
+            }
+            pl += pje[j];
+          }
+          if (key < 0 && cc >= 0) {
+            atomicAdd(pwg + cc, (double)pl);
+            pl = 0.0f;
+          }
+          bool head;
+          const unsigned heads = warp_seg_heads(key, &head);
+          pl = warp_seg_sum(pl, heads);
+          if (head && key >= 0) atomicAdd(Psm + key, pl);
+        }
         // Philox block A of all four: independent chains the scheduler
         // interleaves; A.x decides the candidate, A.y selects the process
         uint32_t r0[4] = {0u, 0u, 0u, 0u}, ry[4] = {0u, 0u, 0u, 0u};
@@ -1097,14 +1164,60 @@ __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long 
         if (c[j] >= 0) {
           my_lo = min(my_lo, c[j]);
           my_hi = max(my_hi, c[j] + 1);
-          if (sample && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) {
-            const int Nm = b.nmax + 1;
-            const float fk = weighted ? (float)kq[j] : 1.0f;
-            atomicAdd(Msm + c[j], fk * ((1.0f - f[j]) * v[j]));
-            atomicAdd(Msm + c[j] + 1, fk * (f[j] * v[j]));
-            atomicAdd(Msm + Nm + c[j], fk * ((1.0f - f[j]) * v[j] * v[j]));
-            atomicAdd(Msm + Nm + c[j] + 1, fk * (f[j] * v[j] * v[j]));
+        }
+      }
+      if (sample) {
+        // vx moments at the nodes of the new cell (CIC shares): per lane
+        // summed where its particles share a cell, then down each segment
+        const int Nm = b.nmax + 1;
+        int cm[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          cm[j] = (c[j] >= 0 && chk(c[j] + 1 <= b.nmax, 20, c[j], b.nmax)) ? c[j] : -1;
+        const int key = lane_cell_key(cm);
+        float a1 = 0.0f, b1 = 0.0f, a2 = 0.0f, b2 = 0.0f;
+        int cc = -1;  // spread lanes: the current run of equal cells
+        double* mdg = R->momd + (size_t)sp * 2 * (N + 1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (cm[j] < 0) continue;
+          const float fk = weighted ? (float)kq[j] : 1.0f;
+          const float lo = fk * ((1.0f - f[j]) * v[j]), hi = fk * (f[j] * v[j]);
+          if (key < 0 && cm[j] != cc) {
+            // spread over cells: each run of equal cells straight to the
+            // run's FP64 sums in HBM
+            if (cc >= 0) {
+              atomicAdd(mdg + cc, (double)a1);
+              atomicAdd(mdg + cc + 1, (double)b1);
+              atomicAdd(mdg + (N + 1) + cc, (double)a2);
+              atomicAdd(mdg + (N + 1) + cc + 1, (double)b2);
+            }
+            cc = cm[j];
+            a1 = b1 = a2 = b2 = 0.0f;
           }
+          a1 += lo;
+          b1 += hi;
+          a2 += lo * v[j];
+          b2 += hi * v[j];
+        }
+        if (key < 0 && cc >= 0) {
+          atomicAdd(mdg + cc, (double)a1);
+          atomicAdd(mdg + cc + 1, (double)b1);
+          atomicAdd(mdg + (N + 1) + cc, (double)a2);
+          atomicAdd(mdg + (N + 1) + cc + 1, (double)b2);
+          a1 = b1 = a2 = b2 = 0.0f;
+        }
+        bool head;
+        const unsigned heads = warp_seg_heads(key, &head);
+        a1 = warp_seg_sum(a1, heads);
+        b1 = warp_seg_sum(b1, heads);
+        a2 = warp_seg_sum(a2, heads);
+        b2 = warp_seg_sum(b2, heads);
+        if (head && key >= 0) {
+          atomicAdd(Msm + key, a1);
+          atomicAdd(Msm + key + 1, b1);
+          atomicAdd(Msm + Nm + key, a2);
+          atomicAdd(Msm + Nm + key + 1, b2);
         }
       }
     }

@@ -2,6 +2,7 @@
 #include "runtime.h"
 
 #include <algorithm>
+#include <utility>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -1350,30 +1351,67 @@ int Batch::autotune(long long steps, int* K_out, int* grid_out, double* ns_out, 
   double best = -1.0;
   int bestK = K0, bestG = G0;
   int rc = ECPIC_OK;
-  for (int K : Ks) {
-    for (int g : grids) {
-      set_pass_grid(g);
-      set_sort_every(K);
-      const long long n = ((std::max(steps, 2LL * K) + K - 1) / K) * K;
-      if ((rc = step(K, err))) break;  // builds the graphs, starts the cadence
-      unsigned long long p0 = 0, p1 = 0;
-      if ((rc = psteps(&p0))) break;
-      cudaEventRecord(a, stream_);
-      if ((rc = step(n, err))) break;
-      cudaEventRecord(b, stream_);
-      if ((rc = check(cudaEventSynchronize(b), "autotune", err))) break;
-      if ((rc = psteps(&p1))) break;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (p1 <= p0) continue;  // nothing left to step
-      const double ns = 1e6 * (double)ms / (double)(p1 - p0);
-      if (best < 0.0 || ns < best) {
-        best = ns;
-        bestK = K;
-        bestG = g;
+  // every trial holds whole sort cycles and whole energy-sample cycles of
+  // the resident runs (a sample step's pass costs a few ordinary ones, so
+  // trials holding different numbers of them would not compare); cadences
+  // whose common multiple exceeds 8x the trial fall back to the sort cycle
+  auto trial_cycle = [&](int K) -> long long {
+    long long cyc = K;
+    const long long cap = 8LL * std::max(steps, 2LL * K);
+    for (int s = 0; s < max_slots_; ++s) {
+      if (!active_[s] || specs_[s].sample_every <= 0) continue;
+      const long long se = specs_[s].sample_every;
+      long long a = cyc, bb = se;
+      while (bb) {
+        const long long t = a % bb;
+        a = bb;
+        bb = t;
       }
+      const long long l = cyc / a * se;
+      if (l > cap) return K;
+      cyc = l;
     }
-    if (rc) break;
+    return cyc;
+  };
+  // every candidate is tried twice, in order and then in reverse order, and
+  // scored by the mean of its two trials: the discharges evolve while the
+  // trials run (the cost per particle-step drifts as they grow and heat), and
+  // a drift linear in time then weighs on every candidate alike
+  std::vector<std::pair<int, int>> cand;
+  for (int K : Ks)
+    for (int g : grids) cand.emplace_back(K, g);
+  const int nc = (int)cand.size();
+  std::vector<double> sum(nc, 0.0);
+  std::vector<int> cnt(nc, 0);
+  for (int t = 0; t < 2 * nc && rc == ECPIC_OK; ++t) {
+    const int i = t < nc ? t : 2 * nc - 1 - t;
+    const int K = cand[i].first, g = cand[i].second;
+    const long long cyc = trial_cycle(K);
+    set_pass_grid(g);
+    set_sort_every(K);
+    const long long n = ((std::max(steps, 2LL * K) + cyc - 1) / cyc) * cyc;
+    if ((rc = step(K, err))) break;  // builds the graphs, starts the cadence
+    unsigned long long p0 = 0, p1 = 0;
+    if ((rc = psteps(&p0))) break;
+    cudaEventRecord(a, stream_);
+    if ((rc = step(n, err))) break;
+    cudaEventRecord(b, stream_);
+    if ((rc = check(cudaEventSynchronize(b), "autotune", err))) break;
+    if ((rc = psteps(&p1))) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (p1 <= p0) continue;  // nothing left to step
+    sum[i] += 1e6 * (double)ms / (double)(p1 - p0);
+    cnt[i] += 1;
+  }
+  for (int i = 0; i < nc; ++i) {
+    if (!cnt[i]) continue;
+    const double ns = sum[i] / cnt[i];
+    if (best < 0.0 || ns < best) {
+      best = ns;
+      bestK = cand[i].first;
+      bestG = cand[i].second;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

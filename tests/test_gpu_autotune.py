@@ -17,8 +17,9 @@ def _gpu():
 
 
 def test_run_autotune_keeps_physics_bit_identical():
-    # room for the discharge's growth over the ~1800 trial steps: a full
-    # species drops births in thread order, which no two runs share
+    # room for the discharge's growth over the ~3800 trial steps (every
+    # candidate tried twice): a full species drops births in thread order,
+    # which no two runs share
     cfg = I.with_headroom(I.config_small(seed=7), 8.0)
     a = gpu_from_config(cfg)
     b = gpu_from_config(cfg)
@@ -40,7 +41,8 @@ def test_run_autotune_keeps_physics_bit_identical():
 
 def test_engine_autotune_picks_a_candidate():
     from paper_2308_13092_gb300 import ecpic
-    cfgs = I.batched_manifest(12, seed=5, steps=2000, scale=0.05)
+    # the runs outlive the trials (every candidate twice: ~3800 steps)
+    cfgs = I.batched_manifest(12, seed=5, steps=6000, scale=0.05)
     eng = ecpic.Engine(max_slots=12, max_cells=1024)
     for c in cfgs:
         eng.submit(c)

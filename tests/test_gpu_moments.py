@@ -170,3 +170,52 @@ def test_density_of_quiet_neutral_cold_load_is_n0_on_the_gpu():
     for s in range(2):
         assert np.max(np.abs(d["density"][s] / n0 - 1.0)) < 1e-8, d["density"][s][:3]
         assert np.all(np.abs(d["Tx"][s]) < 1e-12)
+
+
+def _set_sorted_state(cfg, g, o, seed=12, weights=False):
+    """Cell-sorted particles, as the counting sort leaves them, most of them
+    slow enough to stay in their cell over the step: whole warps then share a
+    cell, so the sample step's warp-segmented sums carry most of the moments
+    and of J.E; a 5 % tail of fast particles crosses cells, and those lanes
+    add their own runs (the other path).  With weights, multipliers 1..16 on
+    both sides."""
+    rng = np.random.default_rng(seed)
+    dx = np.diff(cfg.edges)
+    for s, sp in enumerate(cfg.species):
+        vth = np.sqrt(I.QE * (1.0 if s == 0 else 0.1) / sp.m)
+        st = I.random_state(rng, cfg.N, sp.n0, vth, cells_per_step=2.5, dt=cfg.dt,
+                            dx_min=dx.min(), tail=0.05, id_base=1000000 * s)
+        order = np.argsort(st["cell"], kind="stable")
+        st = {k: v[order] for k, v in st.items()}
+        g.set_particles(s, st["cell"], st["xi"], st["vx"], st["vy"], st["vz"], st["id"])
+        o.set_particles_cell(s, st["cell"], st["xi"], st["vx"], st["vy"], st["vz"], st["id"])
+        if weights:
+            k = rng.integers(1, 17, st["cell"].size).astype(np.uint32)
+            g.set_weights(s, k)
+            o.set_weights(s, k)
+
+
+@pytest.mark.parametrize("scheme,grid,weights", [(I.EC, "uniform", False), (I.MC, "doubling", False),
+                                                 (I.EC, "uniform", True), (I.EC2, "uniform", False)])
+def test_sample_step_moments_on_cell_sorted_particles(scheme, grid, weights):
+    edges = None if grid == "uniform" else oracle.doubling_grid(128, 0.05, 0.01, 1, 8)
+    cfg = _small(scheme=scheme, edges=edges, collisions=False, n=20000, seed=8)
+    if weights:
+        cfg.rebalance = dict(every=0, target=512, lo=64, hi=1024, m0=16)
+    g, o = _pair(cfg)
+    _set_sorted_state(cfg, g, o, weights=weights)
+    g.reset_averages(1)
+    o.reset_averages(1)
+    g.step(1)
+    g.sync()
+    o.step(1)
+    rep = _check(cfg, g, o)
+    assert rep["density_0"] <= 1.0 and rep["density_1"] <= 1.0
+    # J.E of the sampled push per cell (the tally test's bound)
+    d = g.diagnostics()
+    t = o.tallies()
+    for s in range(len(cfg.species)):
+        gp, op = d["power"][s], t["power"][s]
+        scale = np.abs(op).max()
+        assert scale > 0
+        np.testing.assert_allclose(gp, op, rtol=0, atol=2e-4 * scale)

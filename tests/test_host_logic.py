@@ -28,9 +28,16 @@ def test_sort_cadences_examples():
 
 
 def test_autotune_step_count_matches_the_trials():
-    # per (K, grid) trial: K steps to start the cadence and max(per_trial, 2K)
-    # rounded up to whole cycles; five grids
-    assert bench.autotune_steps(64, Ks=(10, 20)) == 5 * ((10 + 70) + (20 + 80))
+    # two trials per (K, grid) pair; per trial: K steps to start the cadence
+    # and max(per_trial, 2K) rounded up to whole cycles of the sort and of the
+    # sample (every 40 steps); five grids
+    assert bench.autotune_steps(64, Ks=(10, 20)) == 2 * 5 * ((10 + 80) + (20 + 80))
+    # K = 50: lcm(50, 40) = 200 <= 8 x 100
+    assert bench.autotune_steps(64, Ks=(50,)) == 2 * 5 * (50 + 200)
+    # without sampling: whole sort cycles only
+    assert bench.autotune_steps(64, Ks=(10, 20), sample_every=0) == 2 * 5 * ((10 + 70) + (20 + 80))
+    # a common multiple above 8x the trial falls back to the sort cycle
+    assert bench.autotune_steps(64, Ks=(63,), sample_every=40) == 2 * 5 * (63 + 126)
 
 
 def test_threaded_oracle_timing_counts_every_runs_particle_steps():
