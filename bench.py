@@ -66,8 +66,8 @@ SAMPLE_EVERY = 40  # energy-sample cadence of the manifest runs: 1/10 RF period
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "0712e120484b9a20c36af8e7fe4d754575c2286fcaea9758d9b1332714eeadac",
-           "dram_bytes_per_particle_step": 570.058e6 / 14.3047e6}
+TRAFFIC = {"sources_sha256": "80e37fad84c247a69fd38acf9ebd8e98559cb6f5fea235a1181c843cdac8789a",
+           "dram_bytes_per_particle_step": 571.022e6 / 14.3047e6}
 
 
 def kernel_sources_sha256():
