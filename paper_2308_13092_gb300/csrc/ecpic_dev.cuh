@@ -47,6 +47,7 @@ struct ProcDev {
 
 struct SpeciesDev {
   double q, m, w;
+  double cw;            // q w 2^-32: the charge of one 2^-32 deposit share (C m^-2)
   float qm_dt;          // (q/m) dt: the push adds qm_dt * E
   float half_m_over_e;  // E[eV] = half_m_over_e * |g|^2
   float two_e_over_m;   // |v| = sqrt(two_e_over_m * E[eV])
@@ -74,6 +75,10 @@ struct RunDev {
   int N, bc, scheme, uniform, ns;
   int seg0;             // first segment of this run (segments seg0..seg0+ns-1)
   int sample_every;
+  // field solve: every species' q w is equal up to sign (field_pm), so one
+  // signed integer sum of the deposits per node serves all; bit s of
+  // field_neg: species s has the opposite sign of species 0
+  int field_pm, field_neg;
   // particle rebalancing: weight multipliers on (the segments' wt arrays),
   // every rb_every steps (0: only on demand), merge above rb_hi particles of
   // a species in a cell, split below rb_lo, aiming at rb_target

@@ -1540,9 +1540,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
   const double* dx = R->dx;
   unsigned long long* Sall = R->S;
   const double inv_L = R->inv_L;
-  double qw[kMaxSpecies];
-#pragma unroll
-  for (int s = 0; s < kMaxSpecies; ++s) qw[s] = R->sp[s].q * R->sp[s].w;
+  const int field_pm = R->field_pm, field_neg = R->field_neg;
   if (!active) return;
   if (advance) {
     if (status0 != 0 || step0 >= step_end) return;
@@ -1567,9 +1565,11 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
   constexpr double kInvEps0 = 1.0 / kEps0;
   constexpr double kInvQe = 1.0 / 1.602176634e-19;
   constexpr double k2m32 = 2.3283064365386963e-10;  // 2^-32
+  // the charge of one deposit share per species (q w 2^-32, formed on the
+  // host: FP64 is slow on this part, and every thread would repeat it)
   double cw[kMaxSpecies];
 #pragma unroll
-  for (int s = 0; s < kMaxSpecies; ++s) cw[s] = s < ns ? qw[s] * k2m32 : 0.0;
+  for (int s = 0; s < kMaxSpecies; ++s) cw[s] = s < ns ? R->sp[s].cw : 0.0;
   // this thread's segment (species tid), for the size update at the end;
   // nothing changes the sizes while this kernel runs
   SegState* my_ss = nullptr;
@@ -1657,7 +1657,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
   // C_n = cs * C'_n with cs = 2^-32 q_0 w_0 and C'_n that integer.  The sum is
   // exact while the species' totals stay below 2^63 together.
   unsigned long long tot[kMaxSpecies];
-  bool pm = true;
+  bool pm = field_pm != 0;
   unsigned long long sum_tot = 0ull;
 #pragma unroll
   for (int s = 0; s < kMaxSpecies; ++s) {
@@ -1672,7 +1672,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
       }
       run[s] += off;
       tot[s] = t + s0[s];
-      pm = pm && (qw[s] == qw[0] || qw[s] == -qw[0]) && tot[s] < (1ull << 62);
+      pm = pm && tot[s] < (1ull << 62);
       sum_tot += tot[s] >> 2;
     }
   }
@@ -1685,7 +1685,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
     unsigned long long qi = 0ull;
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s)
-      if (s < ns) qi += qw[s] == qw[0] ? tot[s] : 0ull - tot[s];
+      if (s < ns) qi += ((field_neg >> s) & 1) ? 0ull - tot[s] : tot[s];
     qtot = (double)(long long)qi;
   } else {
 #pragma unroll
@@ -1704,7 +1704,7 @@ __global__ void __launch_bounds__(kFieldBlock, 2) k_field(BatchView b, int advan
         if (n > 0) run[s] += S[n];
         S[n] = 0ull;
         if (pm)
-          qi += qw[s] == qw[0] ? run[s] : 0ull - run[s];
+          qi += ((field_neg >> s) & 1) ? 0ull - run[s] : run[s];
         else
           c += cw[s] * (double)run[s];
       }

@@ -7,7 +7,7 @@
 namespace ecpic {
 
 constexpr int kPassBlock = 256;
-constexpr int kFieldBlock = 512;
+constexpr int kFieldBlock = 256;
 constexpr int kCollideBlock = 256;
 
 struct BatchView {

@@ -599,6 +599,7 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err, bool defer) {
     D.q = hs.q;
     D.m = hs.m;
     D.w = base_weight(spec, s);
+    D.cw = hs.q * D.w * 2.3283064365386963e-10;  // 2^-32
     D.qm_dt = (float)(hs.q / hs.m * spec.dt);
     D.half_m_over_e = (float)(0.5 * hs.m / kQe);
     D.two_e_over_m = (float)(2.0 * kQe / hs.m);
@@ -644,6 +645,16 @@ int Batch::admit(int slot, const RunSpec& spec, std::string* err, bool defer) {
       P.product_seg = hp.kind == ECPIC_IONIZATION ? R.seg0 + hp.product : -1;
       if (hp.kind == ECPIC_ION_ELASTIC || hp.kind == ECPIC_CX) D.heavy = 1;
     }
+  }
+  // field solve: species whose q w are equal up to sign share one signed
+  // integer sum of their deposits per node
+  R.field_pm = 1;
+  R.field_neg = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double a = R.sp[s].q * R.sp[s].w, a0 = R.sp[0].q * R.sp[0].w;
+    if (a == a0) continue;
+    if (a == -a0) R.field_neg |= 1 << s;
+    else R.field_pm = 0;
   }
   // particle segments
   std::vector<SegState> sst(spc_);
