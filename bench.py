@@ -66,8 +66,8 @@ SAMPLE_EVERY = 40  # energy-sample cadence of the manifest runs: 1/10 RF period
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
 # the kernel sources hash to the measured version; after any change the
 # traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "80e37fad84c247a69fd38acf9ebd8e98559cb6f5fea235a1181c843cdac8789a",
-           "dram_bytes_per_particle_step": 571.022e6 / 14.3047e6}
+TRAFFIC = {"sources_sha256": "96ac73e13e7929218eab50b86a4028ba86e6e38eb24596926a4b203e0278087c",
+           "dram_bytes_per_particle_step": 570.457e6 / 14.3047e6}
 
 
 def kernel_sources_sha256():
