@@ -64,18 +64,28 @@ SAMPLE_EVERY = 40  # energy-sample cadence of the manifest runs: 1/10 RF period
 # DRAM traffic of k_pass measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one stepping launch on the 64-run manifest, see
 # profiles/k_pass_batched64.md), per particle-step.  It is reported only while
-# the kernel sources hash to the measured version; after any change the
-# traffic is unknown (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "96ac73e13e7929218eab50b86a4028ba86e6e38eb24596926a4b203e0278087c",
+# the kernel sources' code (comments and whitespace aside) hashes to the
+# measured version; after any change to the code the traffic is unknown
+# (null) until it is measured again.
+TRAFFIC = {"sources_sha256": "2e9f3743a85ff921ba7603d5575d92c61718f7c3d2d3d85ec5990a1e71dac88b",
            "dram_bytes_per_particle_step": 570.457e6 / 14.3047e6}
+
+
+def kernel_code(text):
+    """The code of a CUDA source without its comments and with whitespace
+    collapsed, so that edits to comments leave the traffic pin valid."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
 
 
 def kernel_sources_sha256():
     import hashlib
     h = hashlib.sha256()
     for f in ("kernels.cu", "ecpic_dev.cuh"):
-        with open(os.path.join(ROOT, "paper_2308_13092_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2308_13092_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(kernel_code(fh.read()).encode())
     return h.hexdigest()
 
 

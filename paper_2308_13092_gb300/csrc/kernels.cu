@@ -693,25 +693,6 @@ __device__ __forceinline__ void collide_real(const BatchView& b, int s, int slot
   }
 }
 
-// Streaming part of one piece: quads [qbeg, qend) of segment s, four
-// particles per thread with 16-byte loads.  Gather (Eq. 6-7 / CIC), leapfrog
-// (Eq. 8-9) in cell units, walls, the Philox candidate test, fixed-point
-// deposit of X^{k+1} (Eq. 2-3).  Collision candidates (Sec. 2a step 6)
-// enter a per-warp ring with their selection word and |g|^2 (or vx); the
-// warp drains it 32 at a time (all lanes busy) with the null-collision test.
-// The few real collisions are recorded for k_collide, which scatters them
-// with its own register budget.  vy, vz are streamed when a species'
-// candidate probability is 1/16 or more (its candidates then touch most
-// 32-byte sectors anyway) and on energy-sample steps; otherwise the test
-// reads them per candidate.
-//
-// Compiled five times (KIND): 0 = ordinary steps of the linear schemes (the
-// common case), 1 = their energy-sample steps (moments, energy, EEDF, J.E),
-// 2 = the EC2 scheme with the sample decision taken at run time, 3 and 4 =
-// the linear schemes with per-particle weight multipliers (rebalancing
-// runs), ordinary and sample steps.  Keeping the rare code out of the
-// common instances keeps their loops small in the instruction cache and
-// their registers free of the sample-step state.
 // Segmented sums across the lanes of a warp for the sample steps' per-node
 // float sums (vx moments, J.E).  Adding every particle's share to shared
 // memory made a sample step's pass ten times an ordinary one: float atomics
@@ -764,6 +745,25 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Streaming part of one piece: quads [qbeg, qend) of segment s, four
+// particles per thread with 16-byte loads.  Gather (Eq. 6-7 / CIC), leapfrog
+// (Eq. 8-9) in cell units, walls, the Philox candidate test, fixed-point
+// deposit of X^{k+1} (Eq. 2-3).  Collision candidates (Sec. 2a step 6)
+// enter a per-warp ring with their selection word and |g|^2 (or vx); the
+// warp drains it 32 at a time (all lanes busy) with the null-collision test.
+// The few real collisions are recorded for k_collide, which scatters them
+// with its own register budget.  vy, vz are streamed when a species'
+// candidate probability is 1/16 or more (its candidates then touch most
+// 32-byte sectors anyway) and on energy-sample steps; otherwise the test
+// reads them per candidate.
+//
+// Compiled five times (KIND): 0 = ordinary steps of the linear schemes (the
+// common case), 1 = their energy-sample steps (moments, energy, EEDF, J.E),
+// 2 = the EC2 scheme with the sample decision taken at run time, 3 and 4 =
+// the linear schemes with per-particle weight multipliers (rebalancing
+// runs), ordinary and sample steps.  Keeping the rare code out of the
+// common instances keeps their loops small in the instruction cache and
+// their registers free of the sample-step state.
 template <int KIND, bool STAGE>
 __device__ __forceinline__ void pass_piece(const BatchView& b, int s, long long qbeg, long long qend, int mode,
                            uint32_t* dep, float* Msm, unsigned char* ring, PassShared& sh) {

@@ -82,3 +82,11 @@ def test_paired_and_spread():
     assert "paired" in line
     with pytest.raises(AssertionError):
         ensemble.compare(G, Gp * 1.5, O * 1.5, "shifted")
+
+
+def test_traffic_pin_ignores_comments_but_not_code():
+    a = "int x = 1; // one\n/* a block\n comment */ int y;"
+    b = "int x = 1;\n\n   int y;   // another comment"
+    assert bench.kernel_code(a) == bench.kernel_code(b)
+    assert bench.kernel_code("int x = 1;") != bench.kernel_code("int x = 2;")
+    assert len(bench.kernel_sources_sha256()) == 64
