@@ -53,3 +53,22 @@ def test_engine_autotune_picks_a_candidate():
     r, q = eng.pump(10)
     assert r == 12 and q == 0
     eng.close()
+
+
+def test_engine_autotune_advances_the_steps_the_bench_plans_for():
+    """The bench sizes its manifest so that no run retires inside the
+    autotuner's trials, from its own count of the steps they take (two trials
+    per cadence and grid, each whole sort and sample cycles): the engine
+    advances exactly that many."""
+    import bench
+    from paper_2308_13092_gb300 import ecpic
+    cfgs = I.batched_manifest(4, seed=9, steps=8000, scale=0.02)
+    for c in cfgs:
+        c.sample_every = 40
+    eng = ecpic.Engine(max_slots=4, max_cells=1024)
+    tks = [eng.submit(c) for c in cfgs]
+    eng.pump(0)
+    eng.autotune(64, ks=[10, 20])
+    got = eng.poll(tks[0], diagnostics=True)["diag"]["step"]
+    assert got == bench.autotune_steps(64, Ks=(10, 20), sample_every=40), got
+    eng.close()
