@@ -2032,8 +2032,8 @@ __global__ void __launch_bounds__(kPassBlock) k_finalize(BatchView b) {
 //     heaviest (ties: smallest id) in place into ceil(k/2) (same id) and
 //     floor(k/2) (id child_id(id, level, 3));
 //   - otherwise copied.
-// k_rb_plan counts each cell's output, k_rb_scan places the cells,
-// k_rb_apply writes them back into the current buffer set, k_rb_finalize and
+// k_rb_cells counts each cell's output, k_rb_scan places the cells, k_rb_cells
+// again writes them back into the current buffer set, k_rb_finalize and
 // k_rb_mark set the sizes and the run's rebalancing level.
 constexpr int kRbBlock = 256;
 constexpr int kRbGroups = kRbMaxCell / 4;
