@@ -239,7 +239,7 @@ int ecpic_get_fields(ecpic_run* run, double* phi, float* E);
 /* Null-collision bound of a species: nu_max (1/s) and the 24-bit candidate
  * threshold ceil((1 - exp(-nu_max dt)) 2^24). */
 int ecpic_nu_max(ecpic_run* run, int species, double* nu_max, uint32_t* threshold24);
-/* Counting-sort cadence in steps (>= 1; default 16). */
+/* Counting-sort cadence in steps (>= 1; default 32). */
 int ecpic_set_sort_every(ecpic_run* run, int sort_every);
 /* Force a counting sort by cell now (compacts absorbed particles). */
 int ecpic_sort_now(ecpic_run* run);

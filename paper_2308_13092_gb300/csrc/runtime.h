@@ -214,7 +214,7 @@ class Batch {
   std::vector<char> active_;
   std::vector<RunSpec> specs_;
   size_t bytes_in_use_ = 0;
-  int sort_every_ = 16;
+  int sort_every_ = 32;
   int since_sort_ = 0;
   bool use_graphs_ = true;
   bool auto_grow_ = false;
