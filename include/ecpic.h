@@ -364,11 +364,14 @@ const char* ecpic_engine_last_error(const ecpic_engine* eng);
  * copies the configuration; ECPIC_ERR_NOMEM if it could never fit. */
 int ecpic_engine_submit(ecpic_engine* eng, const ecpic_run_config* cfg, int64_t n_steps,
                         uint64_t* ticket);
-/* One scheduling round: admit queued runs that fit, advance every resident
- * run by up to max_steps steps (runs stop at their own step count; every
- * about 64 steps, a species filled beyond 3/4 of its capacity has it doubled,
- * see ecpic_set_auto_grow), wait, and retire the runs that finished.  *n_resident (may be NULL) receives the
- * number of runs resident after the round, *n_queued the queue length. */
+/* One scheduling round: admit queued runs that fit (first fit in submission
+ * order; the round's admissions are loaded, deposited and given their step-0
+ * field together, in one launch of each kernel), advance every resident run
+ * by up to max_steps steps (runs stop at their own step count; every about 64
+ * steps, a species filled beyond 3/4 of its capacity has it doubled, see
+ * ecpic_set_auto_grow), wait, and retire the runs that finished.
+ * *n_resident (may be NULL) receives the number of runs resident after the
+ * round, *n_queued the queue length. */
 int ecpic_engine_pump(ecpic_engine* eng, int64_t max_steps, int* n_resident, int* n_queued);
 /* State of a ticket: 0 queued, 1 resident, 2 finished, < 0 an ecpic_status
  * error of that run.  When finished, or resident (then read from the device:
