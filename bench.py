@@ -121,6 +121,14 @@ def autotune_steps(per_trial, Ks=(8, 16, 32, 64), grids=5, sample_every=SAMPLE_E
     return 2 * grids * total
 
 
+def sample_steps(k0, steps, every=SAMPLE_EVERY):
+    """Energy-sample steps among the `steps` steps from level k0: the push of
+    level k samples when (k + 1) % every == 0."""
+    if every <= 0:
+        return 0
+    return sum(1 for k in range(k0, k0 + steps) if (k + 1) % every == 0)
+
+
 def combine_ranks(ms, ps):
     """Whole-job figures of a weak-scaling replica run: the slowest rank's
     time and the particle-steps of all ranks (host-side gloo reductions; the
@@ -573,7 +581,7 @@ def main():
     # energy-sample steps in the window (every run steps in lockstep from its
     # admission): the pass of level k samples when (k + 1) % SAMPLE_EVERY == 0
     k0 = eng.poll(tickets[0], diagnostics=True)["diag"]["step"]
-    samples = sum(1 for k in range(k0, k0 + args.steps) if (k + 1) % SAMPLE_EVERY == 0)
+    samples = sample_steps(k0, args.steps)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ps0 = eng.stats()["particle_steps"]
     if world > 1:

@@ -90,3 +90,15 @@ def test_traffic_pin_ignores_comments_but_not_code():
     assert bench.kernel_code(a) == bench.kernel_code(b)
     assert bench.kernel_code("int x = 1;") != bench.kernel_code("int x = 2;")
     assert len(bench.kernel_sources_sha256()) == 64
+
+
+def test_sample_steps_in_a_window():
+    # the push of level k samples when (k + 1) % 40 == 0: levels 39, 79, ...
+    assert bench.sample_steps(0, 39) == 0
+    assert bench.sample_steps(0, 40) == 1
+    assert bench.sample_steps(39, 1) == 1
+    assert bench.sample_steps(40, 39) == 0
+    assert bench.sample_steps(1000, 4000) == 100
+    assert bench.sample_steps(7, 20, every=0) == 0
+    # a 20-step window holds one sample step for half of its start levels
+    assert sum(bench.sample_steps(k, 20) for k in range(40)) == 20
