@@ -2032,10 +2032,13 @@ __global__ void __launch_bounds__(kPassBlock) k_finalize(BatchView b) {
 //     heaviest (ties: smallest id) in place into ceil(k/2) (same id) and
 //     floor(k/2) (id child_id(id, level, 3));
 //   - otherwise copied.
-// k_rb_cells counts each cell's output, k_rb_scan places the cells, k_rb_cells
-// again writes them back into the current buffer set, k_rb_finalize and
+// k_rb_classify lists the cells that merge or split and counts the others,
+// k_rb_cells counts each listed cell's output, k_rb_scan places the cells,
+// k_rb_copy streams the unchanged cells' particles back into the current
+// buffer set and k_rb_cells writes the listed cells there, k_rb_finalize and
 // k_rb_mark set the sizes and the run's rebalancing level.
 constexpr int kRbBlock = 256;
+constexpr int kRbListCells = 4096;  // list entry = segment * kRbListCells + cell
 constexpr int kRbGroups = kRbMaxCell / 4;
 
 struct RbSmem {
@@ -2044,6 +2047,7 @@ struct RbSmem {
   uint16_t ix[kRbMaxCell];            // index within the cell
   uint16_t pref[kRbGroups];           // eligible groups before each order position
   uint8_t el[kRbGroups];              // group at an order position may merge
+  unsigned kmax;                      // the cell's largest weight multiplier
 };
 
 // FP32 bits ordered like the values (+0 and -0 as one value)
@@ -2149,15 +2153,28 @@ __device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n,
     }
   }
   if (mode == 0 || mode == 3) {
-    if (write) {
+    // (listed cells only: a split cell with nothing to split)
+    if (write)
       for (int t = tid; t < n; t += blockDim.x) rb_copy(G, in, out, start + t, obase + t);
-      if (mode == 3 && tid == 0) atomicAdd(&st->ctr[sp][C_RB_SKIPPED], 1ull);
-    }
     return n;
   }
   // merge: order by (vx, id), groups of four, the ones nearest the middle
   const int ng = n / 4;
   const int Gw = min(ng, (n - T + 1) / 2);
+  if (!write) {
+    // with no multiplier above kRbMaxWeight / 4 every group is eligible
+    // (W <= kRbMaxWeight), so the count needs no ordering
+    if (tid == 0) sm.kmax = 0u;
+    __syncthreads();
+    unsigned km = 0u;
+    for (int t = tid; t < n; t += blockDim.x) km = max(km, G.wt[in][start + t]);
+    km = __reduce_max_sync(0xFFFFFFFFu, km);
+    if ((tid & 31) == 0) atomicMax(&sm.kmax, km);
+    __syncthreads();
+    const unsigned kmax = sm.kmax;
+    __syncthreads();  // every thread has read it before the next cell resets it
+    if (kmax <= kRbMaxWeight / 4u) return n - 2 * Gw;
+  }
   int P = 1;
   while (P < n) P <<= 1;
   for (int t = tid; t < P; t += blockDim.x) {
@@ -2196,9 +2213,9 @@ __device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n,
     if (!write) return n - 2 * chosen;
   }
   // output offsets: a chosen group's first particle emits two, its others
-  // none, every other particle one
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int a = min(n, tid * per), e = min(n, a + per);
+  // none, every other particle one.  They are scanned in shared memory (the
+  // sort keys are no longer needed), so that consecutive threads take
+  // consecutive order positions and their stores coalesce.
   auto emits = [&](int t) -> int {
     const int g = t / 4;
     if (g >= ng) return 1;
@@ -2206,17 +2223,23 @@ __device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n,
     const bool ch = sm.el[ps] && (int)sm.pref[ps] < Gw;
     return ch ? ((t & 3) == 0 ? 2 : 0) : 1;
   };
-  long long loc = 0;
-  for (int t = a; t < e; ++t) loc += emits(t);
-  long long tot;
-  long long pos = block_excl_scan(loc, wsm, &tot);
+  long long* opos = reinterpret_cast<long long*>(sm.k2);
+  for (int t = tid; t < n; t += blockDim.x) opos[t] = emits(t);
+  __syncthreads();
+  block_incl_scan_array(opos, n, wsm);
+  const long long tot = opos[n - 1];
   const long long k_lvl = st->step;
   unsigned long long merged = 0;
-  for (int t = a; t < e; ++t) {
-    const int m = emits(t);
-    if (m == 1) {
-      rb_copy(G, in, out, start + sm.ix[t], obase + pos);
-    } else if (m == 2) {
+  // single particles: consecutive threads, consecutive positions
+  for (int t = tid; t < n; t += blockDim.x)
+    if (emits(t) == 1) rb_copy(G, in, out, start + sm.ix[t], obase + opos[t] - 1);
+  // chosen groups, one per thread (the FP64 merge arithmetic is a long
+  // dependent chain on this part's slow FP64 pipe: spread it over the block)
+  for (int g = tid; g < ng; g += blockDim.x) {
+    const int t = 4 * g;
+    if (emits(t) != 2) continue;
+    const long long pos = opos[t] - 2;
+    {
       // the group's weighted centroid, mean velocity and spreads (FP64)
       double W = 0.0, X = 0.0, u[3] = {0.0, 0.0, 0.0}, m2[3] = {0.0, 0.0, 0.0};
       unsigned Wi = 0u;
@@ -2271,7 +2294,6 @@ __device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n,
       G.wt[out][o + 1] = kb;
       ++merged;
     }
-    pos += m;
   }
   merged = warp_sum(merged);
   if ((tid & 31) == 0 && merged) atomicAdd(&st->ctr[sp][C_RB_MERGED], merged);
@@ -2279,51 +2301,48 @@ __device__ int rb_cell(const BatchView& b, int s, int c, long long start, int n,
   return (int)tot;
 }
 
-// per-CTA prefix of the rebalancing work: the cells of every segment of a due
-// run (pre[0..nseg])
-__device__ long long rb_prefix(const BatchView& b, long long* pre, long long* wsm) {
-  const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
-  const int s0 = threadIdx.x * per;
-  long long loc = 0;
-  for (int k = 0; k < per; ++k) {
-    const int s = s0 + k;
-    if (s < b.nseg) {
-      const int slot = b.segs[s].run;
-      const bool due = run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot);
-      const long long cnt = due ? b.runs[slot].N : 0;
-      pre[s] = cnt;
-      loc += cnt;
-    }
+// Per (segment, cell) of a due run, one thread: a cell that merges or splits
+// (more than rb_hi particles, at most kRbMaxCell; fewer than rb_lo) goes on
+// the list for k_rb_cells; the others keep their particles, so their output
+// count is their count and k_rb_copy moves them (mode 0; 2: above kRbMaxCell,
+// counted as skipped).
+__global__ void __launch_bounds__(kPassBlock) k_rb_classify(BatchView b) {
+  const int s = blockIdx.y;
+  const int c = blockIdx.x * kPassBlock + threadIdx.x;
+  if (s >= b.nseg) return;
+  const SegDev& G = b.segs[s];
+  const int slot = G.run;
+  const RunDev& R = b.runs[slot];
+  if (!run_live(R, b.rst[slot], MODE_REBAL, -1, slot) || c >= R.N || c >= kRbListCells) return;
+  const int* h = b.hist + G.hoff;  // after the scatter: the end of each cell
+  const int n = h[c] - (c > 0 ? h[c - 1] : 0);
+  const bool listed = (n > R.rb_hi && n <= kRbMaxCell) || (n > 0 && n < R.rb_lo);
+  b.rbmode[G.hoff + c] = listed ? 1 : (n > R.rb_hi ? 2 : 0);
+  if (listed) {
+    // at most one entry per (segment, cell): within nseg * nmax by construction
+    const int k = atomicAdd(b.rbnum, 1);
+    const bool fits = k < b.nseg * b.nmax;
+    chk(fits, 30, k, (long long)b.nseg * b.nmax);
+    if (fits) b.rblist[k] = s * kRbListCells + c;
+  } else {
+    b.rbcnt[G.hoff + c] = n;
   }
-  long long total;
-  long long run = block_excl_scan(loc, wsm, &total);
-  for (int k = 0; k < per; ++k) {
-    const int s = s0 + k;
-    if (s < b.nseg) {
-      const long long cnt = pre[s];
-      pre[s] = run;
-      run += cnt;
-    }
-  }
-  if (threadIdx.x == 0) pre[b.nseg] = total;
-  __syncthreads();
-  return total;
 }
 
-// write = 0: each cell's output count into rbcnt; write = 1: the cells'
-// particles into the current buffer set at the scanned offsets
+// write = 0: each listed cell's output count into rbcnt; write = 1: the
+// listed cells' particles into the current buffer set at the scanned offsets
 __global__ void __launch_bounds__(kRbBlock) k_rb_cells(BatchView b, int write) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RbSmem& sm = *reinterpret_cast<RbSmem*>(smem_raw);
-  long long* pre = reinterpret_cast<long long*>(smem_raw + sizeof(RbSmem));
   __shared__ long long wsm[32];
-  const long long T = rb_prefix(b, pre, wsm);
-  for (long long item = blockIdx.x; item < T; item += gridDim.x) {
-    const int s = seg_find(pre, b.nseg, item);
-    const int c = (int)(item - pre[s]);
+  const int num = *b.rbnum;
+  for (int item = blockIdx.x; item < num; item += gridDim.x) {
+    const int e = b.rblist[item];
+    const int s = e / kRbListCells, c = e % kRbListCells;
+    if (!chk(s >= 0 && s < b.nseg, 31, s, b.nseg)) continue;
     const SegDev& G = b.segs[s];
     if (write && b.sst[s].rb_over) continue;
-    const int* h = b.hist + G.hoff;  // after the scatter: the end of each cell
+    const int* h = b.hist + G.hoff;
     const long long end = h[c];
     const long long start = c > 0 ? h[c - 1] : 0;
     // (an unconditional guard: the writes below index by this range)
@@ -2331,6 +2350,71 @@ __global__ void __launch_bounds__(kRbBlock) k_rb_cells(BatchView b, int write) {
     int* oc = b.rbcnt + G.hoff;
     const int cnt = rb_cell(b, s, c, start, (int)(end - start), write != 0, write ? oc[c] : 0, sm, wsm);
     if (!write && threadIdx.x == 0) oc[c] = cnt;
+  }
+}
+
+// The particles of the cells that keep them (mode 0 and 2), streamed from the
+// sorted buffer set into the current one at their cell's scanned offset:
+// consecutive particles of a cell, consecutive positions.  Segments of due
+// runs whose plan did not overflow the capacity.
+__global__ void __launch_bounds__(kPassBlock) k_rb_copy(BatchView b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long long* pre = reinterpret_cast<long long*>(smem_raw);
+  __shared__ long long wsm[32];
+  {
+    const int per = (b.nseg + blockDim.x - 1) / blockDim.x;
+    const int s0 = threadIdx.x * per;
+    long long loc = 0;
+    for (int k = 0; k < per; ++k) {
+      const int sg = s0 + k;
+      if (sg < b.nseg) {
+        const int slot = b.segs[sg].run;
+        const bool due = run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot) &&
+                         !b.sst[sg].rb_over;
+        const long long cnt = due ? b.sst[sg].n_live : 0;
+        pre[sg] = cnt;
+        loc += cnt;
+      }
+    }
+    long long total;
+    long long run = block_excl_scan(loc, wsm, &total);
+    for (int k = 0; k < per; ++k) {
+      const int sg = s0 + k;
+      if (sg < b.nseg) {
+        const long long cnt = pre[sg];
+        pre[sg] = run;
+        run += cnt;
+      }
+    }
+    if (threadIdx.x == 0) pre[b.nseg] = total;
+    __syncthreads();
+  }
+  const long long T = pre[b.nseg];
+  if (T == 0) return;
+  const long long lo = T * (long long)blockIdx.x / gridDim.x;
+  const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
+  if (lo >= hi) return;
+  for (int s = seg_find(pre, b.nseg, lo); s < b.nseg && pre[s] < hi; ++s) {
+    const long long beg = max(lo, pre[s]) - pre[s];
+    const long long end = min(hi, pre[s + 1]) - pre[s];
+    if (beg >= end) continue;
+    const SegDev& G = b.segs[s];
+    const int out = b.sst[s].cur, in = out ^ 1;
+    const int N = b.runs[G.run].N;
+    const int* h = b.hist + G.hoff;
+    const int* oc = b.rbcnt + G.hoff;
+    const uint8_t* md = b.rbmode + G.hoff;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      if (!chk(i < G.cap, 32, i, G.cap)) continue;
+      const int c = G.cell[in][i];
+      if (!chk(c >= 0 && c < N, 33, c, N)) continue;
+      if (md[c] == 1) continue;  // listed: written by k_rb_cells
+      const long long o = (long long)oc[c] + (i - (c > 0 ? h[c - 1] : 0));
+      // (an unconditional guard, as in k_rb_cells: the writes index by o)
+      const bool ok = o >= 0 && o < G.cap;
+      chk(ok, 34, o, G.cap);
+      if (ok) rb_copy(G, in, out, i, o);
+    }
   }
 }
 
@@ -2370,10 +2454,18 @@ __global__ void __launch_bounds__(kPassBlock) k_rb_finalize(BatchView b) {
   const int slot = G.run;
   if (!run_live(b.runs[slot], b.rst[slot], MODE_REBAL, -1, slot)) return;
   const int N = b.runs[slot].N;
+  const bool over = b.sst[s].rb_over != 0;
+  unsigned long long skipped = 0;
   for (int i = threadIdx.x; i < N; i += kPassBlock) {
     b.hist[G.hoff + i] = 0;
     b.rbcnt[G.hoff + i] = 0;
+    skipped += (!over && b.rbmode[G.hoff + i] == 2) ? 1ull : 0ull;
+    b.rbmode[G.hoff + i] = 0;
   }
+  skipped = warp_sum(skipped);
+  if ((threadIdx.x & 31) == 0 && skipped)
+    atomicAdd(&b.rst[slot].ctr[G.species][C_RB_SKIPPED], skipped);
+  __syncthreads();  // every thread has read rb_over
   if (threadIdx.x == 0) {
     SegState* ss = b.sst + s;
     if (ss->rb_over) {
@@ -2649,10 +2741,16 @@ void launch_rebalance(const BatchView& b, int grid, cudaStream_t s) {
   k_scan<<<b.nseg, kPassBlock, 0, s>>>(b, MODE_REBAL);
   const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
   k_scatter<<<grid, kPassBlock, sms, s>>>(b, MODE_REBAL);
-  const size_t smr = sizeof(RbSmem) + sizeof(long long) * (size_t)(b.nseg + 1);
+  cudaMemsetAsync(b.rbnum, 0, sizeof(int), s);
+  k_rb_classify<<<dim3((unsigned)((b.nmax + kPassBlock - 1) / kPassBlock), (unsigned)b.nseg), kPassBlock, 0,
+                  s>>>(b);
+  const size_t smr = sizeof(RbSmem);
   set_smem_attr((const void*)k_rb_cells, smr);
   k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 0);
   k_rb_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
+  // (a latency-bound stream: four times the persistent grid in flight)
+  set_smem_attr((const void*)k_rb_copy, sms);
+  k_rb_copy<<<4 * grid, kPassBlock, sms, s>>>(b);
   k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 1);
   k_rb_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
   k_rb_mark<<<(b.max_slots + 127) / 128, 128, 0, s>>>(b);

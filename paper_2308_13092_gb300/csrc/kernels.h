@@ -17,6 +17,9 @@ struct BatchView {
   SegState* sst;        // device, nseg
   int* hist;            // device, sum of N over segments
   int* rbcnt;           // device, nseg * nmax: rebalancing output counts / cursors
+  uint8_t* rbmode;      // device, nseg * nmax: rebalancing cell kind (0 keep, 1 listed, 2 skipped)
+  int* rblist;          // device, nseg * nmax: the listed (segment, cell) entries
+  int* rbnum;           // device: their number
   int max_slots;
   int nseg;
   int nmax;             // largest N in the batch

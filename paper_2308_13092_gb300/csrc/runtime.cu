@@ -379,6 +379,9 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
   cudaMalloc(&d_sst_, sizeof(SegState) * nseg_);
   cudaMalloc(&d_hist_, sizeof(int) * (size_t)nseg_ * nmax_);
   cudaMalloc(&d_rbcnt_, sizeof(int) * (size_t)nseg_ * nmax_);
+  cudaMalloc(&d_rbmode_, (size_t)nseg_ * nmax_);
+  cudaMalloc(&d_rblist_, sizeof(int) * (size_t)nseg_ * nmax_);
+  cudaMalloc(&d_rbnum_, sizeof(int));
   cudaMalloc(&d_wave_slots_, sizeof(int) * max_slots_);
   cudaMalloc(&d_wave_params_, sizeof(InitParams) * max_slots_);
   level_.assign(max_slots_, 0);
@@ -396,6 +399,8 @@ Batch::Batch(int device, cudaStream_t stream, int max_slots, int spc, int nmax)
   cudaMemsetAsync(d_sst_, 0, sizeof(SegState) * nseg_, stream_);
   cudaMemsetAsync(d_hist_, 0, sizeof(int) * (size_t)nseg_ * nmax_, stream_);
   cudaMemsetAsync(d_rbcnt_, 0, sizeof(int) * (size_t)nseg_ * nmax_, stream_);
+  cudaMemsetAsync(d_rbmode_, 0, (size_t)nseg_ * nmax_, stream_);
+  cudaMemsetAsync(d_rbnum_, 0, sizeof(int), stream_);
   cudaMemcpyAsync(d_segs_, h_segs_.data(), sizeof(SegDev) * nseg_, cudaMemcpyHostToDevice, stream_);
   slot_mem_.assign(max_slots_, nullptr);
   slot_bytes_.assign(max_slots_, 0);
@@ -420,6 +425,9 @@ Batch::~Batch() {
   cudaFree(d_sst_);
   cudaFree(d_hist_);
   cudaFree(d_rbcnt_);
+  cudaFree(d_rbmode_);
+  cudaFree(d_rblist_);
+  cudaFree(d_rbnum_);
   cudaFree(d_wave_slots_);
   cudaFree(d_wave_params_);
   if (own_stream_) cudaStreamDestroy(stream_);
@@ -464,6 +472,9 @@ BatchView Batch::view() const {
   v.sst = d_sst_;
   v.hist = d_hist_;
   v.rbcnt = d_rbcnt_;
+  v.rbmode = d_rbmode_;
+  v.rblist = d_rblist_;
+  v.rbnum = d_rbnum_;
   v.max_slots = max_slots_;
   v.nseg = nseg_;
   v.nmax = nmax_;

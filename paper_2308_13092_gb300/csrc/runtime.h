@@ -199,6 +199,9 @@ class Batch {
   SegState* d_sst_ = nullptr;
   int* d_hist_ = nullptr;
   int* d_rbcnt_ = nullptr;
+  uint8_t* d_rbmode_ = nullptr;
+  int* d_rblist_ = nullptr;
+  int* d_rbnum_ = nullptr;
   std::vector<long long> level_;  // predicted level of each slot
   // runs admitted with defer, waiting for admit_wave()
   std::vector<int> wave_slots_;
