@@ -424,7 +424,7 @@ def appendix_b_block(ecpic, stream, device, steps=100_000, chunks=10):
                     "relative total-energy change every 1000/w_pe from t = 100/w_pe"}
 
 
-def served_block(ecpic, stream, device, capacity, n_req=256, rho=0.7, slots=64):
+def served_block(ecpic, stream, device, capacity, n_req=2000, rho=0.7, slots=256, n_alone=256):
     """Poisson arrivals of CCP run requests (sizes as in the batched manifest,
     5..50 RF periods at 1/10 of the steps), continuous batching vs one at a
     time; completion latency = finish - arrival.  Throughput is reported over
@@ -432,7 +432,13 @@ def served_block(ecpic, stream, device, capacity, n_req=256, rho=0.7, slots=64):
     ramp-up from an empty GPU and the drain after the last arrival) and
     sustained, over the arrival window (from the arrival of the first quarter
     of the requests to the last arrival), from the engine's particle-step
-    count sampled after every pump."""
+    count sampled after every pump.  The stream holds as many requests as
+    the served workload (2000), so that the arrival window is many request
+    lifetimes long; one at a time serves only the first ``n_alone`` of them,
+    with the same arrival times (it is overloaded at these rates, so its
+    latencies grow with the stream's length; ``n_alone`` = 0 leaves it out).
+    The engine holds up to ``slots`` runs, by default as many as the batched
+    line keeps resident."""
     reqs = I.served_stream(n_req, seed=1, rate=1.0)
     for r in reqs:
         r.config.n_steps = max(40, r.config.n_steps // 10)
@@ -442,15 +448,15 @@ def served_block(ecpic, stream, device, capacity, n_req=256, rho=0.7, slots=64):
     rate = rho * capacity / work
     arr = np.cumsum(np.random.default_rng(2).exponential(1.0 / rate, n_req))
 
-    def serve(max_slots):
+    def serve(max_slots, n):
         eng = ecpic.Engine(device=device, stream=stream.cuda_stream, max_slots=max_slots,
                            max_cells=1024, mem_budget=64 << 30)
         t0 = time.perf_counter()
-        pending = list(range(n_req))
+        pending = list(range(n))
         live = {}
         done = {}
         samples = []  # (time, particle-steps done) after every pump
-        while len(done) < n_req:
+        while len(done) < n:
             now = time.perf_counter() - t0
             while pending and arr[pending[0]] <= now:
                 i = pending.pop(0)
@@ -468,26 +474,29 @@ def served_block(ecpic, stream, device, capacity, n_req=256, rho=0.7, slots=64):
                     eng.release(tk)
         total = time.perf_counter() - t0
         eng.close()
-        lat = np.array([done[i][0] - arr[i] for i in range(n_req)])
+        lat = np.array([done[i][0] - arr[i] for i in range(n)])
         ps = sum(v[1] for v in done.values())
-        t_a, t_b = float(arr[n_req // 4]), float(arr[-1])
+        t_a, t_b = float(arr[n // 4]), float(arr[n - 1])
         win = [(t, p) for t, p in samples if t_a <= t <= t_b]
         sustained = None
         if len(win) >= 2 and win[-1][0] > win[0][0]:
             sustained = (win[-1][1] - win[0][1]) / (win[-1][0] - win[0][0])
-        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        return {"requests": n, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)),
                 "particle_steps_per_s": ps / total, "wall_s": total,
                 "sustained_particle_steps_per_s": sustained,
                 "sustained_window_s": [t_a, t_b]}
 
-    mix = serve(slots)
-    alone = serve(1)
+    mix = serve(slots, n_req)
+    alone = serve(1, min(n_alone, n_req)) if n_alone > 0 else None
     sus = mix["sustained_particle_steps_per_s"]
     return {"requests": n_req, "load": rho, "arrival_rate_per_s": rate,
             "continuous_batching": mix, "one_at_a_time": alone,
             "sustained_over_batched": None if sus is None else sus / capacity,
+            "slots": slots,
             "what": "Poisson arrivals; admitted by device memory as slots free; steps/10 of "
-                    "the full request lengths; sustained = over the arrival window"}
+                    "the full request lengths; sustained = over the arrival window; one at "
+                    "a time on the stream's first requests"}
 
 
 def e2e_block(ecpic, cfgs, stream, device, steps):
@@ -643,6 +652,11 @@ def main():
         extras["served"] = served_block(ecpic, stream, local, capacity=value / max(1, world))
         extras["served_load_0.9"] = served_block(ecpic, stream, local,
                                                  capacity=value / max(1, world), rho=0.9)
+        # the same stream with a quarter of the slots: the queue builds and
+        # the smaller resident population steps less efficiently
+        extras["served_load_0.9_slots64"] = served_block(ecpic, stream, local,
+                                                         capacity=value / max(1, world), rho=0.9,
+                                                         slots=64, n_alone=0)
         extras["appendix_b"] = appendix_b_block(ecpic, stream, local)
         # whole jobs of 5 RF periods (2000 steps), the shortest request length
         # of the served stream
@@ -684,6 +698,7 @@ def main():
                          "timing": "CUDA events recorded by the timed window's own graph "
                                    "replays after every kernel phase",
                          "pass_ms_avg": pass_ms, "field_ms_avg": field_ms,
+                         "field_us_per_run": 1e3 * field_ms / len(cfgs),
                          "collide_ms_avg": collide_ms, "sort_ms_per_step": sort_ms_step,
                          "phase_sum_ms_per_step": phase_sum,
                          "phase_sum_over_step": phase_sum / (ms / args.steps),
