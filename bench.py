@@ -67,8 +67,8 @@ SAMPLE_EVERY = 40  # energy-sample cadence of the manifest runs: 1/10 RF period
 # the kernel sources' code (comments and whitespace aside) hashes to the
 # measured version; after any change to the code the traffic is unknown
 # (null) until it is measured again.
-TRAFFIC = {"sources_sha256": "6a53c1fe1cc83a09fd9d1b04860ea77db808a9660df4525e273ca914f2a6ec4c",
-           "dram_bytes_per_particle_step": 570.373e6 / 14.3047e6}
+TRAFFIC = {"sources_sha256": "e5eeee343a1652533fba227684206c5f01ce125025a8e32c621210d9186c724c",
+           "dram_bytes_per_particle_step": 569.823e6 / 14.3047e6}
 
 
 def kernel_code(text):

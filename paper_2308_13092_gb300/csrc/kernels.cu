@@ -1906,13 +1906,45 @@ __global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b, int mode) {
   if (threadIdx.x == 0) b.sst[s].n_live = total;
 }
 
+// Counting-sort scatter (the order within a cell is not kept), one CTA
+// iteration of kScatQ particles at a time: the chunk's cells are counted in
+// shared memory (a range [clo, chi] of its run's cells), each cell present
+// reserves its slice of the destination with one global atomic per CTA
+// iteration, the records are
+// staged in shared memory in cell order, and consecutive threads then write
+// consecutive destinations of each cell, so the stores fill whole sectors.
+// The next iteration's source records are prefetched into L2.
+constexpr int kScatQ = 4 * kPassBlock;  // particles per CTA iteration
+
+size_t scatter_smem_bytes(int nseg, int nmax) {
+  return sizeof(long long) * (size_t)(nseg + 1) +
+         (size_t)kScatQ * (sizeof(unsigned long long) + 6 * sizeof(int)) +
+         3 * sizeof(int) * (size_t)(nmax + 1);
+}
+
 __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long long* pre = reinterpret_cast<long long*>(smem_raw);
+  unsigned long long* st_id = reinterpret_cast<unsigned long long*>(pre + b.nseg + 1);
+  int* st_c = reinterpret_cast<int*>(st_id + kScatQ);
+  float* st_x = reinterpret_cast<float*>(st_c + kScatQ);
+  float* st_u = st_x + kScatQ;
+  float* st_v = st_u + kScatQ;
+  float* st_w = st_v + kScatQ;
+  uint32_t* st_k = reinterpret_cast<uint32_t*>(st_w + kScatQ);
+  const int M = b.nmax + 1;
+  int* cnt = reinterpret_cast<int*>(st_k + kScatQ);  // per cell of the chunk's range
+  int* lpre = cnt + M;                               // its exclusive prefix
+  int* gbase = lpre + M;                             // its reserved destination
   __shared__ long long wsm[32];
-  // quads of four particles per thread; every field is loaded before the
-  // cursor atomics so the loads overlap
-  const long long T = seg_prefix(b, mode, -1, pre, wsm, 4);
+  __shared__ int wsi[32];
+  __shared__ int lohi[2];
+  for (int i = threadIdx.x; i < M; i += kPassBlock) cnt[i] = 0;
+  if (threadIdx.x == 0) {
+    lohi[0] = INT_MAX;
+    lohi[1] = -1;
+  }
+  const long long T = seg_prefix(b, mode, -1, pre, wsm, 4);  // ends with a barrier
   if (T == 0) return;
   const long long lo = T * (long long)blockIdx.x / gridDim.x;
   const long long hi = T * (long long)(blockIdx.x + 1) / gridDim.x;
@@ -1935,13 +1967,41 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b, int mode) {
     const float* sw = G.vz[src];
     const uint64_t* si = G.id[src];
     const uint32_t* sk = G.wt[src];  // weight multipliers (rebalancing runs)
-    for (long long base = beg + (long long)(threadIdx.x & ~31); base < end; base += kPassBlock) {
-      const long long i0 = 4 * (base + lane);
+    int32_t* dc = G.cell[dst];
+    float* dx_ = G.xi[dst];
+    float* du = G.vx[dst];
+    float* dv = G.vy[dst];
+    float* dw = G.vz[dst];
+    uint64_t* di = G.id[dst];
+    uint32_t* dk = G.wt[dst];
+    // block-uniform trip count: the barriers below need every thread
+    for (long long base = beg; base < end; base += kPassBlock) {
+      if (threadIdx.x == 0) {
+        const long long nb = base + kPassBlock;
+        if (nb < end) {
+          const long long p0 = 4 * nb;
+          const long long p1 = min(4 * min(end, nb + kPassBlock), n);
+          if (p1 > p0) {
+            const unsigned b4 = (unsigned)(((p1 - p0) * 4) & ~15ll);
+            if (b4) {
+              l2_prefetch(sc + p0, b4);
+              l2_prefetch(sx + p0, b4);
+              l2_prefetch(su + p0, b4);
+              l2_prefetch(sv + p0, b4);
+              l2_prefetch(sw + p0, b4);
+              l2_prefetch(si + p0, (unsigned)(((p1 - p0) * 8) & ~15ll));
+              if (sk) l2_prefetch(sk + p0, b4);
+            }
+          }
+        }
+      }
+      const long long q = base + threadIdx.x;
+      const long long i0 = 4 * q;
       int c[4];
       float x[4], u[4], v[4], w[4];
       uint64_t id[4];
       unsigned kq[4] = {1u, 1u, 1u, 1u};
-      if (base + lane < end && i0 + 3 < n && chk(i0 + 3 < G.cap, 27, i0, G.cap)) {
+      if (q < end && i0 + 3 < n && chk(i0 + 3 < G.cap, 27, i0, G.cap)) {
         const int4 c4 = *reinterpret_cast<const int4*>(sc + i0);
         const float4 x4 = *reinterpret_cast<const float4*>(sx + i0);
         const float4 u4 = *reinterpret_cast<const float4*>(su + i0);
@@ -1962,7 +2022,7 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b, int mode) {
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const bool in = base + lane < end && i0 + j < n;
+          const bool in = q < end && i0 + j < n && chk(i0 + j < G.cap, 27, i0 + j, G.cap);
           c[j] = in ? sc[i0 + j] : -1;
           x[j] = in ? sx[i0 + j] : 0.f;
           u[j] = in ? su[i0 + j] : 0.f;
@@ -1972,26 +2032,91 @@ __global__ void __launch_bounds__(kPassBlock) k_scatter(BatchView b, int mode) {
           if (sk && in) kq[j] = sk[i0 + j];
         }
       }
+      // the chunk's cell range (absorbed particles, cell < 0, are dropped)
+      int my_lo = INT_MAX, my_hi = -1;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int cj = c[j] < Nr ? c[j] : -1;
-        const unsigned grp = __match_any_sync(kFull, cj >= 0 ? (unsigned)cj : 0xFFFFFFFFu);
-        if (cj >= 0) {
-          const int leader = __ffs(grp) - 1;
-          int basepos = 0;
-          if (lane == leader) basepos = atomicAdd(cursor + cj, __popc(grp));
-          basepos = __shfl_sync(grp, basepos, leader);
-          const long long d = (long long)basepos + __popc(grp & lt);
-          if (!chk(d >= 0 && d < G.cap, 10, d, G.cap)) continue;
-          G.cell[dst][d] = cj;
-          G.xi[dst][d] = x[j];
-          G.vx[dst][d] = u[j];
-          G.vy[dst][d] = v[j];
-          G.vz[dst][d] = w[j];
-          G.id[dst][d] = id[j];
-          if (sk) G.wt[dst][d] = kq[j];
+        c[j] = c[j] < Nr ? c[j] : -1;
+        if (c[j] >= 0) {
+          my_lo = min(my_lo, c[j]);
+          my_hi = max(my_hi, c[j]);
         }
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        my_lo = min(my_lo, __shfl_xor_sync(kFull, my_lo, o));
+        my_hi = max(my_hi, __shfl_xor_sync(kFull, my_hi, o));
+      }
+      if (lane == 0 && my_hi >= 0) {
+        atomicMin(&lohi[0], my_lo);
+        atomicMax(&lohi[1], my_hi);
+      }
+      __syncthreads();
+      const int clo = lohi[0], chi = lohi[1];
+      const int R = chi >= clo ? chi - clo + 1 : 0;
+      // rank of each particle among the chunk's particles of its cell
+      int r[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned grp = __match_any_sync(kFull, c[j] >= 0 ? (unsigned)c[j] : 0xFFFFFFFFu);
+        if (c[j] >= 0 && chk(c[j] - clo < M, 28, c[j] - clo, M)) {
+          const int leader = __ffs(grp) - 1;
+          int b0 = 0;
+          if (lane == leader) b0 = atomicAdd(cnt + (c[j] - clo), __popc(grp));
+          b0 = __shfl_sync(grp, b0, leader);
+          r[j] = b0 + __popc(grp & lt);
+        }
+      }
+      __syncthreads();
+      // local prefix of the range's counts; each cell present reserves its
+      // destination slice
+      const int per = (R + kPassBlock - 1) / kPassBlock;
+      const int kb = min(R, (int)threadIdx.x * per), ke = min(R, kb + per);
+      int loc = 0;
+      for (int k = kb; k < ke; ++k) loc += cnt[k];
+      int m;
+      int run = block_excl_scan(loc, wsi, &m);
+      for (int k = kb; k < ke; ++k) {
+        const int ck = cnt[k];
+        lpre[k] = run;
+        run += ck;
+        gbase[k] = ck ? atomicAdd(cursor + clo + k, ck) : 0;
+      }
+      __syncthreads();
+      // stage in cell order
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (c[j] < 0) continue;
+        const int p = lpre[c[j] - clo] + r[j];
+        if (!chk(p >= 0 && p < kScatQ, 29, p, kScatQ)) continue;
+        st_c[p] = c[j];
+        st_x[p] = x[j];
+        st_u[p] = u[j];
+        st_v[p] = v[j];
+        st_w[p] = w[j];
+        st_id[p] = id[j];
+        st_k[p] = kq[j];
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < m; t += kPassBlock) {
+        const int cc = st_c[t];
+        const int k = cc - clo;
+        const long long d = (long long)gbase[k] + (t - lpre[k]);
+        if (!chk(d >= 0 && d < G.cap, 10, d, G.cap)) continue;
+        dc[d] = cc;
+        dx_[d] = st_x[t];
+        du[d] = st_u[t];
+        dv[d] = st_v[t];
+        dw[d] = st_w[t];
+        di[d] = st_id[t];
+        if (dk) dk[d] = st_k[t];
+      }
+      for (int k = threadIdx.x; k < R; k += kPassBlock) cnt[k] = 0;
+      if (threadIdx.x == 0) {
+        lohi[0] = INT_MAX;
+        lohi[1] = -1;
+      }
+      __syncthreads();
     }
   }
 }
@@ -2715,6 +2840,17 @@ void launch_phi(const BatchView& b, int slot, cudaStream_t s) {
   k_phi<<<1, kFieldBlock, sm, s>>>(b, slot);
 }
 
+// The scatter's grid: one wave of as many CTAs as fit on the device at its
+// shared-memory size (every CTA takes an equal share of the particles, so a
+// partial second wave would leave most SMs idle while it runs).
+static int scatter_grid(size_t sms) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scatter, kPassBlock, sms);
+  return (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+}
+
 void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s) {
   if (phase == 0) {
     const size_t smh = sizeof(long long) * (size_t)(b.nseg + 1) + sizeof(int) * (size_t)(b.nmax + 1);
@@ -2723,8 +2859,9 @@ void launch_sort_phase(const BatchView& b, int grid, int phase, cudaStream_t s) 
   } else if (phase == 1) {
     k_scan<<<b.nseg, kPassBlock, 0, s>>>(b, MODE_SORT);
   } else if (phase == 2) {
-    const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
-    k_scatter<<<grid, kPassBlock, sms, s>>>(b, MODE_SORT);
+    const size_t sms = scatter_smem_bytes(b.nseg, b.nmax);
+    set_smem_attr((const void*)k_scatter, sms);
+    k_scatter<<<scatter_grid(sms), kPassBlock, sms, s>>>(b, MODE_SORT);
   } else {
     k_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
   }
@@ -2739,8 +2876,9 @@ void launch_rebalance(const BatchView& b, int grid, cudaStream_t s) {
   set_smem_attr((const void*)k_hist, smh);
   k_hist<<<grid, kPassBlock, smh, s>>>(b, MODE_REBAL);
   k_scan<<<b.nseg, kPassBlock, 0, s>>>(b, MODE_REBAL);
-  const size_t sms = sizeof(long long) * (size_t)(b.nseg + 1);
-  k_scatter<<<grid, kPassBlock, sms, s>>>(b, MODE_REBAL);
+  const size_t sms = scatter_smem_bytes(b.nseg, b.nmax);
+  set_smem_attr((const void*)k_scatter, sms);
+  k_scatter<<<scatter_grid(sms), kPassBlock, sms, s>>>(b, MODE_REBAL);
   cudaMemsetAsync(b.rbnum, 0, sizeof(int), s);
   k_rb_classify<<<dim3((unsigned)((b.nmax + kPassBlock - 1) / kPassBlock), (unsigned)b.nseg), kPassBlock, 0,
                   s>>>(b);
@@ -2749,8 +2887,9 @@ void launch_rebalance(const BatchView& b, int grid, cudaStream_t s) {
   k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 0);
   k_rb_scan<<<b.nseg, kPassBlock, 0, s>>>(b);
   // (a latency-bound stream: four times the persistent grid in flight)
-  set_smem_attr((const void*)k_rb_copy, sms);
-  k_rb_copy<<<4 * grid, kPassBlock, sms, s>>>(b);
+  const size_t smc = sizeof(long long) * (size_t)(b.nseg + 1);
+  set_smem_attr((const void*)k_rb_copy, smc);
+  k_rb_copy<<<4 * grid, kPassBlock, smc, s>>>(b);
   k_rb_cells<<<grid, kRbBlock, smr, s>>>(b, 1);
   k_rb_finalize<<<b.nseg, kPassBlock, 0, s>>>(b);
   k_rb_mark<<<(b.max_slots + 127) / 128, 128, 0, s>>>(b);
