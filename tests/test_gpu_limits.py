@@ -114,3 +114,51 @@ def test_potential_error_on_stretched_grids_at_max_cells(grid):
     assert dE <= 2.0 ** -22, dE
     g.close()
     o.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_sort_at_max_cells_from_random_order(weighted):
+    """The counting sort at ECPIC_MAX_CELLS cells from the worst order it
+    meets: particles in random cell order (every CTA iteration of the
+    scatter spans most of the run's cells, so its shared-memory count range
+    is the whole grid), a count that is no multiple of four or of a CTA
+    iteration, absorbed particles to drop and ionisation births appended
+    after them.  Afterwards the live particles are ordered by cell and are
+    exactly the ones before (every field, matched by id), with the weight
+    multipliers following their particles in a rebalancing run."""
+    n = 40 * MAX_CELLS + 3
+    cfg = I.ccp("max-cells-sort", N=MAX_CELLS, n0=5e13, dt=1.0 / (400 * I.F_RF), ppc=0,
+                v0=300.0, p_mtorr=60.0, n_steps=2, seed=11, L=0.05, collisions=True,
+                n_per_species=n)
+    cfg.n_gas *= 20  # ionisation births within two steps
+    if weighted:
+        cfg.rebalance = dict(every=0, target=64, lo=32, hi=96, m0=4)
+    g = gpu_from_config(cfg, sort_every=1000)
+    rng = np.random.default_rng(12)
+    dxm = np.diff(cfg.edges).min()
+    for s, sp in enumerate(cfg.species):
+        vth = np.sqrt(I.QE * (5.0 if s == 0 else 0.5) / sp.m)
+        st = I.random_state(rng, cfg.N, n, vth, 2.0, cfg.dt, dxm, id_base=10 ** 7 * s)
+        g.set_particles(s, st["cell"], st["xi"], st["vx"], st["vy"], st["vz"], st["id"])
+        if weighted:
+            g.set_weights(s, rng.integers(1, 9, n).astype(np.uint32))
+    g.step(2)
+    g.sync()
+    d0 = g.diagnostics(profiles=False)["species"]
+    assert d0[0]["births"] > 0
+    assert d0[0]["absorbed_left"] + d0[0]["absorbed_right"] > 0
+    before = [g.get_particles(s) for s in range(2)]
+    wb = [g.get_weights(s) for s in range(2)] if weighted else None
+    g.sort_now()
+    d1 = g.diagnostics(profiles=False)["species"]
+    for s in range(2):
+        p = g.get_particles(s)
+        assert p["cell"].size == before[s]["cell"].size == d1[s]["n"] == d0[s]["n"]
+        assert np.all(np.diff(p["cell"]) >= 0)
+        ia, ib = np.argsort(before[s]["id"]), np.argsort(p["id"])
+        assert np.unique(p["id"]).size == p["id"].size
+        for k in ("cell", "xi", "vx", "vy", "vz", "id"):
+            assert np.array_equal(before[s][k][ia], p[k][ib]), k
+        if weighted:
+            assert np.array_equal(wb[s][ia], g.get_weights(s)[ib])
+    g.close()
