@@ -1843,16 +1843,24 @@ __global__ void __launch_bounds__(kPassBlock) k_hist(BatchView b, int mode) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = (base + lane < end && i0 + j < n) ? pc[i0 + j] : -1;
       }
+      // a thread's consecutive particles in one cell (most quads of sorted
+      // data) are counted together: one shared atomic per run of equal cells
+      int cur = -1, cnt = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int cj = c[j] < Nr ? c[j] : -1;
-        const unsigned grp = __match_any_sync(kFull, cj >= 0 ? (unsigned)cj : 0xFFFFFFFFu);
         if (cj >= 0) {
-          if (lane == __ffs(grp) - 1 && chk(cj <= b.nmax, 9, cj, b.nmax)) atomicAdd(H + cj, __popc(grp));
           my_lo = min(my_lo, cj);
           my_hi = max(my_hi, cj);
         }
+        if (cj != cur) {
+          if (cur >= 0 && chk(cur <= b.nmax, 9, cur, b.nmax)) atomicAdd(H + cur, cnt);
+          cur = cj;
+          cnt = 0;
+        }
+        ++cnt;
       }
+      if (cur >= 0 && chk(cur <= b.nmax, 9, cur, b.nmax)) atomicAdd(H + cur, cnt);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
