@@ -1918,10 +1918,10 @@ __global__ void __launch_bounds__(kPassBlock) k_scan(BatchView b, int mode) {
 // iteration of kScatQ particles at a time: the chunk's cells are counted in
 // shared memory (a range [clo, chi] of its run's cells), each cell present
 // reserves its slice of the destination with one global atomic per CTA
-// iteration, the records are
-// staged in shared memory in cell order, and consecutive threads then write
-// consecutive destinations of each cell, so the stores fill whole sectors.
-// The next iteration's source records are prefetched into L2.
+// iteration, the records are staged in shared memory in cell order, and
+// consecutive threads then write consecutive destinations of each cell, so
+// the stores fill whole sectors.  The next iteration's source records are
+// prefetched into L2.  Launched as one wave (scatter_grid).
 constexpr int kScatQ = 4 * kPassBlock;  // particles per CTA iteration
 
 size_t scatter_smem_bytes(int nseg, int nmax) {
